@@ -1,0 +1,190 @@
+"""CPU oracle for the TREES epoch step -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  It wraps ``oracle.c`` (plain sequential C: the
+recursive definitions of each task program and a Task Vector Machine
+simulator that follows the paper's Phase 1/2/3 epoch loop, Sec. 4.3 and 5.2)
+through ctypes.  It shares no code with the CUDA path and imports nothing
+from it.
+"""
+from __future__ import annotations
+
+import ctypes
+import fcntl
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+FIB, MERGESORT, BFS, NQUEENS, POSTORDER, PREORDER = 0, 1, 2, 3, 4, 5
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so if it is missing or stale."""
+    with open(os.path.join(_HERE, ".build.lock"), "w") as lf:
+        fcntl.flock(lf, fcntl.LOCK_EX)
+        if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+            tmp = _SO + ".tmp"
+            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", _SRC, "-o", tmp])
+            os.replace(tmp, _SO)
+    return _SO
+
+
+class Epoch(ctypes.Structure):
+    _fields_ = [("cen", ctypes.c_uint32), ("lo", ctypes.c_uint32), ("hi", ctypes.c_uint32),
+                ("valid", ctypes.c_uint32), ("forks", ctypes.c_uint32), ("joined", ctypes.c_uint32),
+                ("maps", ctypes.c_uint32)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("program", ctypes.c_int), ("fib_n", ctypes.c_uint32), ("fib_cutoff", ctypes.c_uint32),
+                ("keys", ctypes.c_void_p), ("nkeys", ctypes.c_int64), ("leaf", ctypes.c_int64),
+                ("nv", ctypes.c_int32), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("level", ctypes.c_void_p), ("src", ctypes.c_int32), ("nq_n", ctypes.c_int32),
+                ("nnodes", ctypes.c_int32), ("left", ctypes.c_void_p), ("right", ctypes.c_void_p),
+                ("visit_epoch", ctypes.c_void_p), ("max_epochs", ctypes.c_uint64)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_uint64), ("tasks", ctypes.c_uint64), ("forks", ctypes.c_uint64),
+                ("joins", ctypes.c_uint64), ("maps", ctypes.c_uint64), ("peak_slots", ctypes.c_uint64),
+                ("root_result", ctypes.c_uint64), ("final_slots", ctypes.c_uint64),
+                ("err", ctypes.c_int32)]
+
+
+def _bind(lib):
+    """Declares the C signatures on a loaded oracle library and returns it."""
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    lib.oracle_fib.restype = ctypes.c_uint64
+    lib.oracle_fib.argtypes = [ctypes.c_uint32, u64p]
+    lib.oracle_fib_task_counts.argtypes = [ctypes.c_uint32, ctypes.c_uint32, u64p, u64p]
+    lib.oracle_mergesort_u32.restype = ctypes.c_int
+    lib.oracle_mergesort_u32.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]
+    lib.oracle_bfs.restype = ctypes.c_int64
+    lib.oracle_bfs.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                               ctypes.c_void_p]
+    lib.oracle_nqueens.restype = ctypes.c_uint64
+    lib.oracle_nqueens.argtypes = [ctypes.c_int, u64p, u64p]
+    lib.oracle_tvm_run.restype = ctypes.c_int
+    lib.oracle_tvm_run.argtypes = [ctypes.POINTER(_Params), ctypes.POINTER(Epoch), ctypes.c_uint64,
+                                   ctypes.POINTER(_Stats)]
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = _bind(ctypes.CDLL(_SO))
+    return _lib
+
+
+# ------------------------------------------------------------ plain definitions
+
+def fib(n: int):
+    """Recursive Fibonacci: ``(F(n), number of calls)``."""
+    calls = ctypes.c_uint64()
+    v = _load().oracle_fib(n, ctypes.byref(calls))
+    return int(v), int(calls.value)
+
+
+def fib_task_counts(n: int, cutoff: int = 0):
+    """``(fib tasks, join tasks)`` of the fib task tree with leaves n<2 or n<=cutoff."""
+    t, j = ctypes.c_uint64(), ctypes.c_uint64()
+    _load().oracle_fib_task_counts(n, cutoff, ctypes.byref(t), ctypes.byref(j))
+    return int(t.value), int(j.value)
+
+
+def mergesort(keys: np.ndarray, leaf: int = 1024) -> np.ndarray:
+    """Top-down mergesort of uint32 keys with the method's split rule; returns a sorted copy."""
+    out = np.ascontiguousarray(keys, dtype=np.uint32).copy()
+    rc = _load().oracle_mergesort_u32(out.ctypes.data, out.shape[0], leaf)
+    if rc != 0:
+        raise RuntimeError(f"oracle_mergesort_u32 failed ({rc})")
+    return out
+
+
+def bfs(row_ptr: np.ndarray, col: np.ndarray, src: int = 0):
+    """FIFO-queue BFS: ``(level int32 array, reached count)``."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    nv = row_ptr.shape[0] - 1
+    level = np.empty(nv, dtype=np.int32)
+    reached = _load().oracle_bfs(nv, row_ptr.ctypes.data, col.ctypes.data if col.size else None, src,
+                                 level.ctypes.data)
+    return level, int(reached)
+
+
+def nqueens(n: int):
+    """Backtracking N-Queens: ``(solutions, row tasks, join tasks)``."""
+    r, j = ctypes.c_uint64(), ctypes.c_uint64()
+    v = _load().oracle_nqueens(n, ctypes.byref(r), ctypes.byref(j))
+    return int(v), int(r.value), int(j.value)
+
+
+# ------------------------------------------------------------ TVM simulator
+
+def tvm_run(program: int, *, fib_n: int = 0, fib_cutoff: int = 0, keys: np.ndarray | None = None,
+            leaf: int = 1024, row_ptr=None, col=None, src: int = 0, nq_n: int = 0, left=None, right=None,
+            max_epochs: int = 1 << 20, trace_cap: int = 1 << 16):
+    """Runs one program on the sequential TVM simulator.
+
+    Returns a dict with ``stats`` (epochs, tasks, forks, joins, maps,
+    peak_slots, root_result), ``trace`` (structured array, one row per epoch:
+    cen, lo, hi, valid, forks, joined, maps) and the program's output
+    (``keys`` sorted in place on a copy, ``level`` or ``visit_epoch``).
+    """
+    lib = _load()
+    p = _Params()
+    p.program = program
+    p.fib_n = fib_n
+    p.fib_cutoff = fib_cutoff
+    p.max_epochs = max_epochs
+    p.leaf = leaf
+    keep = []
+    out = {}
+    if program == MERGESORT:
+        k = np.ascontiguousarray(keys, dtype=np.uint32).copy()
+        keep.append(k)
+        p.keys = k.ctypes.data if k.size else None
+        p.nkeys = k.shape[0]
+        out["keys"] = k
+    if program == BFS:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        cl = np.ascontiguousarray(col, dtype=np.int32)
+        lv = np.empty(rp.shape[0] - 1, dtype=np.int32)
+        keep += [rp, cl, lv]
+        p.nv = rp.shape[0] - 1
+        p.row_ptr = rp.ctypes.data
+        p.col = cl.ctypes.data if cl.size else None
+        p.level = lv.ctypes.data
+        p.src = src
+        out["level"] = lv
+    if program == NQUEENS:
+        p.nq_n = nq_n
+    if program in (POSTORDER, PREORDER):
+        lf = np.ascontiguousarray(left, dtype=np.int32)
+        rt = np.ascontiguousarray(right, dtype=np.int32)
+        ve = np.empty(lf.shape[0], dtype=np.int32)
+        keep += [lf, rt, ve]
+        p.nnodes = lf.shape[0]
+        p.left = lf.ctypes.data if lf.size else None
+        p.right = rt.ctypes.data if rt.size else None
+        p.visit_epoch = ve.ctypes.data if ve.size else None
+        out["visit_epoch"] = ve
+    trace = (Epoch * trace_cap)()
+    st = _Stats()
+    rc = lib.oracle_tvm_run(ctypes.byref(p), trace, trace_cap, ctypes.byref(st))
+    if rc != 0:
+        raise RuntimeError(f"oracle_tvm_run failed ({rc})")
+    n = min(int(st.epochs), trace_cap)
+    dt = np.dtype([(f, np.uint32) for f, _ in Epoch._fields_])
+    arr = np.frombuffer(trace, dtype=dt, count=n).copy()
+    out["stats"] = {f: int(getattr(st, f)) for f, _ in _Stats._fields_ if f != "err"}
+    out["trace"] = arr
+    return out

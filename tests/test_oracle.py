@@ -1,0 +1,298 @@
+"""Pins the CPU oracle to facts outside itself (CPU only).
+
+Each check compares the oracle with something it does not compute the same
+way: printed values from the paper's worked example (Sec. 5.3, golden file),
+closed forms (Fibonacci identities), known counts (OEIS A000170), brute force
+on tiny inputs (permutations, Floyd-Warshall), and library routines
+(numpy sort, scipy shortest paths).
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1608_00571_b300 import gen
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def fib_fast_doubling(n):
+    """F(n) by the fast-doubling identities F(2k)=F(k)(2F(k+1)-F(k)),
+    F(2k+1)=F(k)^2+F(k+1)^2 (a different algorithm from the oracle's)."""
+    def fd(k):
+        if k == 0:
+            return 0, 1
+        a, b = fd(k // 2)
+        c = a * (2 * b - a)
+        d = a * a + b * b
+        return (d, c + d) if k % 2 else (c, d)
+    return fd(n)[0]
+
+
+def load_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([int(x) for x in line.split()])
+    return rows
+
+
+# ----------------------------------------------------------------- Fibonacci
+
+@pytest.mark.parametrize("n", list(range(0, 28)))
+def test_fib_value_and_calls(n):
+    v, calls = oracle.fib(n)
+    assert v == fib_fast_doubling(n)
+    # the naive recursion makes 2F(n+1)-1 calls
+    assert calls == 2 * fib_fast_doubling(n + 1) - 1
+
+
+def test_fib_known_values():
+    assert oracle.fib(20)[0] == 6765
+    assert oracle.fib(34)[0] == 5702887
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 10, 20, 25])
+def test_fib_tvm_closed_forms(n):
+    r = oracle.tvm_run(oracle.FIB, fib_n=n)
+    st = r["stats"]
+    F = fib_fast_doubling
+    assert st["root_result"] == F(n)
+    assert st["tasks"] == 3 * F(n + 1) - 2          # fib calls + one sum per internal call
+    assert st["joins"] == F(n + 1) - 1
+    assert st["peak_slots"] == 2 * F(n + 1) - 1     # nothing is reclaimed until the deepest level
+    assert st["epochs"] == 2 * n - 1                # n forward levels, n-1 join levels (Sec. 4.4.1)
+    assert st["final_slots"] == 0                   # TV and stacks empty together (Sec. 5.3)
+    # the fib task tree's width at each depth (brute force on the tree) is the valid count
+    # of the forward epochs
+    level = [n]
+    for d in range(n):
+        assert r["trace"][d]["valid"] == len(level)
+        assert r["trace"][d]["cen"] == d
+        level = [c for x in level if x >= 2 for c in (x - 1, x - 2)]
+    assert not level
+
+
+@pytest.mark.parametrize("n", [0, 1])
+def test_fib_tvm_leaf_root(n):
+    st = oracle.tvm_run(oracle.FIB, fib_n=n)["stats"]
+    assert (st["root_result"], st["tasks"], st["epochs"]) == (n, 1, 1)
+
+
+@pytest.mark.parametrize("n,c", [(20, 12), (25, 12), (34, 12), (15, 14), (15, 15)])
+def test_fib_cutoff_closed_forms(n, c):
+    F = fib_fast_doubling
+    r = oracle.tvm_run(oracle.FIB, fib_n=n, fib_cutoff=c)
+    st = r["stats"]
+    assert st["root_result"] == F(n)
+    if n <= c:
+        assert st["tasks"] == 1 and st["epochs"] == 1
+        return
+    # a subtree rooted at m has 2F(m-c+2)-1 calls when leaves are m <= c
+    calls = 2 * F(n - c + 2) - 1
+    assert st["tasks"] == calls + (F(n - c + 2) - 1)
+    assert oracle.fib_task_counts(n, c) == (calls, F(n - c + 2) - 1)
+    assert st["epochs"] == 2 * (n - c) + 1
+
+
+# ----------------------------------------------------------------- N-Queens
+
+def nq_brute(n):
+    """Solutions and consistent-prefix count by enumerating permutations."""
+    sols = 0
+    for p in itertools.permutations(range(n)):
+        if len({p[i] + i for i in range(n)}) == n and len({p[i] - i for i in range(n)}) == n:
+            sols += 1
+    nodes = 0
+    for r in range(n + 1):
+        for p in itertools.permutations(range(n), r):
+            if len({p[i] + i for i in range(r)}) == r and len({p[i] - i for i in range(r)}) == r:
+                nodes += 1
+    return sols, nodes
+
+
+def test_nqueens_known_counts():
+    for n, sols in load_rows("nqueens_solutions.txt"):
+        if n <= 11:
+            assert oracle.nqueens(n)[0] == sols
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7])
+def test_nqueens_brute_force(n):
+    sols, nodes = nq_brute(n)
+    v, row_tasks, _ = oracle.nqueens(n)
+    assert v == sols
+    assert row_tasks == nodes
+
+
+def test_nqueens_eight_brute_solutions():
+    sols = sum(1 for p in itertools.permutations(range(8))
+               if len({p[i] + i for i in range(8)}) == 8 and len({p[i] - i for i in range(8)}) == 8)
+    assert sols == oracle.nqueens(8)[0] == 92
+    assert oracle.nqueens(8)[1] == 2057     # the classic size of the 8-queens backtracking tree
+
+
+@pytest.mark.parametrize("n", list(range(1, 12)))
+def test_nqueens_tvm(n):
+    sols, rows, joins = oracle.nqueens(n)
+    r = oracle.tvm_run(oracle.NQUEENS, nq_n=n)
+    st = r["stats"]
+    assert st["root_result"] == sols
+    assert st["tasks"] == rows + joins
+    assert st["joins"] == joins
+    if n >= 4:
+        assert st["epochs"] == 2 * n + 1   # n+1 row levels, n join levels
+
+
+# ----------------------------------------------------------------- mergesort
+
+def leaf_count(n, leaf):
+    if n <= leaf:
+        return 1
+    m = n // 2
+    return leaf_count(m, leaf) + leaf_count(n - m, leaf)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 1023, 1024, 1025, 3000, 4096, 12345, 1 << 15])
+def test_mergesort_matches_numpy(n):
+    k = gen.keys_u32(7 + n, n)
+    assert np.array_equal(oracle.mergesort(k), np.sort(k))
+    r = oracle.tvm_run(oracle.MERGESORT, keys=k)
+    assert np.array_equal(r["keys"], np.sort(k))
+    leaves = leaf_count(n, 1024)
+    st = r["stats"]
+    assert st["tasks"] == 2 * leaves - 1 + (leaves - 1)
+    assert st["maps"] == (leaves if n > 0 else 0) + (leaves - 1)
+
+
+def test_mergesort_duplicates():
+    rng = np.random.default_rng(3)
+    k = rng.integers(0, 5, size=5000).astype(np.uint32)
+    assert np.array_equal(oracle.mergesort(k, leaf=7), np.sort(k))
+    assert np.array_equal(oracle.tvm_run(oracle.MERGESORT, keys=k, leaf=7)["keys"], np.sort(k))
+
+
+@pytest.mark.parametrize("leaf", [1, 2, 3])
+def test_mergesort_brute_force_small(leaf):
+    for n in range(0, 7):
+        for vals in itertools.product(range(3), repeat=n) if n <= 5 else [tuple(range(n))[::-1]]:
+            k = np.array(vals, dtype=np.uint32)
+            want = np.array(sorted(vals), dtype=np.uint32)
+            assert np.array_equal(oracle.mergesort(k, leaf=leaf), want)
+            assert np.array_equal(oracle.tvm_run(oracle.MERGESORT, keys=k, leaf=leaf)["keys"], want)
+
+
+@pytest.mark.parametrize("log_leaves", [0, 1, 4, 6])
+def test_mergesort_epochs_power_of_two(log_leaves):
+    n = 1024 << log_leaves
+    st = oracle.tvm_run(oracle.MERGESORT, keys=gen.keys_u32(1, n))["stats"]
+    assert st["epochs"] == 2 * log_leaves + 1
+    assert st["tasks"] == (2 << log_leaves) - 1 + (1 << log_leaves) - 1
+
+
+# ----------------------------------------------------------------- BFS
+
+def random_graph(nv, p, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.random((nv, nv)) < p
+    a = np.triu(a, 1)
+    a = a | a.T
+    row_ptr = np.zeros(nv + 1, dtype=np.int32)
+    row_ptr[1:] = np.cumsum(a.sum(1))
+    col = np.concatenate([np.nonzero(a[i])[0] for i in range(nv)] + [np.zeros(0, int)]).astype(np.int32)
+    return a, row_ptr, col
+
+
+def floyd_warshall_hops(a):
+    nv = a.shape[0]
+    inf = 10 ** 9
+    d = np.where(a, 1, inf).astype(np.int64)
+    np.fill_diagonal(d, 0)
+    for k in range(nv):
+        d = np.minimum(d, d[:, k:k + 1] + d[k:k + 1, :])
+    return np.where(d >= inf, -1, d)
+
+
+@pytest.mark.parametrize("nv,p,seed", [(1, 0.0, 0), (5, 0.0, 1), (12, 0.2, 2), (40, 0.05, 3),
+                                       (64, 0.03, 4), (64, 0.3, 5)])
+def test_bfs_floyd_warshall(nv, p, seed):
+    a, row_ptr, col = random_graph(nv, p, seed)
+    d = floyd_warshall_hops(a)
+    for src in {0, nv - 1}:
+        level, reached = oracle.bfs(row_ptr, col, src)
+        assert np.array_equal(level, d[src])
+        assert reached == int((d[src] >= 0).sum())
+        r = oracle.tvm_run(oracle.BFS, row_ptr=row_ptr, col=col, src=src)
+        assert np.array_equal(r["level"], d[src])
+        st = r["stats"]
+        assert st["tasks"] == reached
+        assert st["epochs"] == int(d[src].max()) + 1
+        # epoch k runs exactly the vertices at distance k
+        for t in r["trace"]:
+            assert t["valid"] == int((d[src] == t["cen"]).sum())
+
+
+def test_bfs_rmat_scipy():
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import shortest_path
+    row_ptr, col, info = gen.rmat(10, 16, seed=2)
+    nv = info["nv"]
+    m = csr_matrix((np.ones(col.shape[0]), col, row_ptr), shape=(nv, nv))
+    d = shortest_path(m, unweighted=True, indices=[0])[0]
+    want = np.where(np.isinf(d), -1, d).astype(np.int32)
+    level, reached = oracle.bfs(row_ptr, col, 0)
+    assert np.array_equal(level, want)
+    r = oracle.tvm_run(oracle.BFS, row_ptr=row_ptr, col=col, src=0)
+    assert np.array_equal(r["level"], want)
+    assert r["stats"]["tasks"] == reached
+    assert r["stats"]["epochs"] == int(want.max()) + 1
+
+
+# ----------------------------------------------------------------- Fig. 3 worked example
+
+@pytest.mark.parametrize("null_under", ["B", "C"])
+def test_fig3_postorder_trace(null_under):
+    # A=0 with children B=1, C=2; three leaves D, E, F below B and C with one NULL slot.
+    if null_under == "B":
+        left = np.array([1, 3, 4, -1, -1, -1]); right = np.array([2, -1, 5, -1, -1, -1])
+    else:
+        left = np.array([1, 3, 5, -1, -1, -1]); right = np.array([2, 4, -1, -1, -1, -1])
+    r = oracle.tvm_run(oracle.POSTORDER, left=left, right=right)
+    rows = load_rows("fig3_postorder_trace.txt")
+    tr = r["trace"]
+    assert len(tr) == len(rows)
+    assert r["stats"]["final_slots"] == 0
+    for (e, cen, lo, hi, valid, forks, joined), t in zip(rows, tr):
+        assert (t["cen"], t["lo"], t["hi"], t["valid"], t["forks"], t["joined"]) == \
+            (cen, lo, hi, valid, forks, joined), e
+    # postorder: every node is visited after its children
+    ve = r["visit_epoch"]
+    for v in range(6):
+        for c in (left[v], right[v]):
+            if c >= 0:
+                assert ve[v] > ve[c]
+
+
+def test_traversal_orders_random_tree():
+    left, right = gen.binary_tree(11, 300)
+    post = oracle.tvm_run(oracle.POSTORDER, left=left, right=right)["visit_epoch"]
+    pre = oracle.tvm_run(oracle.PREORDER, left=left, right=right)["visit_epoch"]
+    depth = np.full(300, -1)
+    depth[0] = 0
+    stack = [0]
+    while stack:
+        v = stack.pop()
+        for c in (left[v], right[v]):
+            if c >= 0:
+                depth[c] = depth[v] + 1
+                stack.append(c)
+    assert (depth >= 0).all()
+    assert np.array_equal(pre, depth)                 # preorder visits at its forward epoch
+    for v in range(300):
+        for c in (left[v], right[v]):
+            if c >= 0:
+                assert post[v] > post[c]
