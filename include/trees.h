@@ -1,0 +1,199 @@
+/*
+ * trees.h -- C ABI of libtrees, a B300 (sm_103a) implementation of the TREES
+ * epoch step: the Task Vector Machine of Sec. 4 run by a GPU-resident
+ * scheduler.  Every task in the current epoch runs in parallel (Sec. 4.3.2);
+ * forks take task-vector slots through a cooperative block scan and one
+ * atomic per block (Sec. 5.2.3); joins rewrite the task's own slot as a
+ * continuation for a later epoch (Sec. 4.3.2); the whole GPU synchronises
+ * once between epochs (work-together Tenet 1, Sec. 3).
+ *
+ * Conventions
+ *  - Every call returns an int status: TREES_OK (0) or one TREES_ERR_* code.
+ *    Device-side failures (a full task vector, an epoch limit, a barrier
+ *    wait that ran out) are sticky flags that the run sets instead of
+ *    trapping; trees_sync() returns them.
+ *  - Pointers named dev_* / device pointers are CUDA device memory owned by
+ *    the caller (e.g. a torch tensor's data_ptr()); host pointers are plain
+ *    host memory.  The library never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Runs are asynchronous and stream ordered; one context runs one
+ *    job (or one batch) at a time, so calls on a context must be ordered on
+ *    one stream or separated by trees_sync().
+ *  - Capacities are counted in task-vector slots (one slot = one TV entry).
+ */
+#ifndef TREES_H
+#define TREES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define TREES_OK 0
+#define TREES_ERR_CAPACITY 1     /* a fork or map found the task vector / map list full */
+#define TREES_ERR_EPOCH_LIMIT 2  /* the run reached config.max_epochs */
+#define TREES_ERR_TIMEOUT 3      /* a grid barrier wait exceeded config.timeout_ns */
+#define TREES_ERR_INVALID_ARG 4  /* bad argument; nothing was launched */
+#define TREES_ERR_CUDA 5         /* a CUDA runtime call failed */
+#define TREES_ERR_ADMISSION 6    /* serving: a job can never fit the configured memory */
+#define TREES_ERR_STACK 7        /* the epoch-range stack overflowed */
+#define TREES_ERR_BUSY 8         /* the context is still running a job */
+
+/* ------------------------------------------------------------ task types
+ * Sec. 5.1.2 footnote 2: a TV entry stores one integer, epoch*NTT + type,
+ * with type in 1..NTT and 0 meaning "no task".  NTT = TREES_NUM_TASK_TYPES. */
+#define TREES_TASK_FIB 1         /* fib(n): fork n-1, n-2, join FIB_SUM; leaf n<2 or n<=cutoff */
+#define TREES_TASK_FIB_SUM 2     /* join: sum of the two children */
+#define TREES_TASK_MS_SPLIT 3    /* mergesort split [lo,hi): leaf -> map leaf sort */
+#define TREES_TASK_MS_MERGE 4    /* join: map merge of the two sorted halves */
+#define TREES_TASK_NQ_ROW 5      /* N-Queens row: fork one child per safe column, join NQ_SUM */
+#define TREES_TASK_NQ_SUM 6      /* join: sum of the children's counts */
+#define TREES_TASK_BFS_VISIT 7   /* BFS vertex: map over its adjacency, claimed neighbours fork */
+#define TREES_TASK_PO 8          /* postorder(node) of Fig. 2 */
+#define TREES_TASK_PO_AFTER 9    /* visitAfter(node) of Fig. 2 (join) */
+#define TREES_TASK_PRE 10        /* preorder(node) of Fig. 2 */
+#define TREES_NUM_TASK_TYPES 10
+
+/* ------------------------------------------------------------ programs */
+#define TREES_PROG_FIB 1
+#define TREES_PROG_MERGESORT 2
+#define TREES_PROG_NQUEENS 3
+#define TREES_PROG_BFS 4
+#define TREES_PROG_POSTORDER 5
+#define TREES_PROG_PREORDER 6
+
+/* ------------------------------------------------------------ schedulers */
+#define TREES_SCHED_PERSISTENT 0 /* one cooperative launch; one grid barrier per epoch */
+#define TREES_SCHED_GRAPH 1      /* CUDA graph: epoch, map and Phase-3 kernels in a conditional WHILE node */
+#define TREES_SCHED_HOSTLOOP 2   /* the paper's host loop: one launch and one device->host read per epoch (Sec. 5.2.4) */
+
+typedef struct {
+    int32_t block_size;      /* threads per block: 256, 512 or 1024 (default 512) */
+    int32_t blocks_per_sm;   /* persistent grid = SMs * this; 0 = as many as fit */
+    int32_t scheduler;       /* TREES_SCHED_* */
+    int32_t trace;           /* 1 = record the per-epoch trace (trees_trace) */
+    uint32_t max_epochs;     /* 0 = 1<<20 */
+    uint32_t trace_cap;      /* trace entries kept; 0 = 65536 */
+    uint64_t timeout_ns;     /* grid-barrier wait limit; 0 = 2 s */
+    uint64_t map_capacity;   /* map descriptors and map tiles per epoch; 0 = task-vector capacity */
+    int32_t inject_stall_epoch; /* test hook, -1 = off: in that epoch the last block leaves
+                                   without arriving at the barrier, so the others time out */
+    int32_t reserved;
+} trees_config_t;
+
+/* Fills *cfg with the defaults above. */
+void trees_default_config(trees_config_t *cfg);
+
+/* ------------------------------------------------------------ context */
+typedef struct trees_ctx trees_ctx;
+
+/* Device bytes a context with `capacity_slots` TV slots needs (TV columns,
+ * map lists, trace, control block).  Returns 0 for invalid arguments. */
+size_t trees_bytes_for(size_t capacity_slots, const trees_config_t *cfg);
+
+/* Creates a context on the current CUDA device that owns a task vector of
+ * capacity_slots entries (allocated with cudaMalloc).  cfg may be NULL
+ * (defaults).  capacity_slots must be in [1, 2^32-1].  Errors: INVALID_ARG,
+ * CUDA (allocation failed). */
+int trees_create(size_t capacity_slots, const trees_config_t *cfg, trees_ctx **out);
+
+/* Same, but carves everything out of a caller-owned device buffer of `bytes`
+ * bytes (256-byte aligned), e.g. a torch tensor; capacity is the largest that
+ * fits.  The buffer must outlive the context. */
+int trees_create_on(void *dev_buf, size_t bytes, const trees_config_t *cfg, trees_ctx **out);
+
+/* Releases everything the context allocated (not caller buffers). */
+void trees_destroy(trees_ctx *ctx);
+
+/* Task-vector capacity of the context, in slots. */
+size_t trees_capacity(const trees_ctx *ctx);
+
+/* Launch geometry the context uses: blocks in the persistent grid, threads
+ * per block, SM count. */
+int trees_geometry(const trees_ctx *ctx, int32_t *grid_blocks, int32_t *block_size, int32_t *sms);
+
+/* ------------------------------------------------------------ one job */
+typedef struct {
+    int32_t program;          /* TREES_PROG_* */
+    uint32_t n;               /* fib: n; N-Queens: board size (1..16); mergesort: number of keys;
+                                 BFS: source vertex; traversal: number of nodes */
+    uint32_t cutoff;          /* fib: a call with n <= cutoff is a leaf computed in its task (0 = none) */
+    uint32_t leaf;            /* mergesort: leaf size, 1..1024 (0 = 1024) */
+    uint32_t *keys;           /* mergesort: device keys, sorted in place */
+    uint32_t *scratch;        /* mergesort: device buffer of n keys (NULL = the context's own) */
+    const int32_t *row_ptr;   /* BFS: device CSR row offsets [nv+1] */
+    const int32_t *col;       /* BFS: device CSR columns */
+    int32_t *level;           /* BFS: device output [nv], -1 = unreachable */
+    int32_t nv;               /* BFS: vertex count */
+    const int32_t *left;      /* traversal: device child arrays [n], -1 = nil; node 0 is the root */
+    const int32_t *right;
+    int32_t *visit_epoch;     /* traversal: device output [n], index of the epoch that visited the node */
+} trees_job_t;
+
+/* Sec. 5.2.1 initialisation + the epoch loop: writes the job's root task
+ * into TV entry 0 for epoch 0 and runs epochs until the range stack is empty.
+ * Asynchronous on `stream` for the persistent and graph schedulers; the host
+ * loop scheduler returns when the run is over.  Errors before launch:
+ * INVALID_ARG (bad job), BUSY, CUDA. */
+int trees_run(trees_ctx *ctx, const trees_job_t *job, void *stream);
+
+/* Waits for the context's last run and returns its status (TREES_OK or the
+ * first device-side error). */
+int trees_sync(trees_ctx *ctx);
+
+/* Reads the result word of a TV slot after trees_sync (slot 0 = the root's
+ * emitted value: fib(n), the N-Queens count).  Errors: INVALID_ARG. */
+int trees_result(trees_ctx *ctx, uint32_t slot, uint64_t *out);
+
+typedef struct {
+    uint64_t epochs;        /* epochs executed (Sec. 4.4.1: the critical path) */
+    uint64_t tasks;         /* valid task executions, joins included (the work) */
+    uint64_t forks;         /* TV slots handed out by forks */
+    uint64_t joins;         /* join operations */
+    uint64_t maps;          /* map operations */
+    uint64_t peak_slots;    /* highest nextFreeCore reached */
+    uint64_t final_slots;   /* nextFreeCore at halt (0 = the TV emptied, Sec. 5.3) */
+    uint64_t ns;            /* device time of the epoch loop (globaltimer) */
+    int32_t status;         /* TREES_OK or the device-side error */
+    int32_t error_epoch;    /* epoch in which the error was raised */
+} trees_stats_t;
+
+/* Statistics of the last run (call after trees_sync). */
+int trees_stats(trees_ctx *ctx, trees_stats_t *out);
+
+typedef struct {
+    uint32_t cen;     /* current epoch number (the popped join-stack value) */
+    uint32_t lo, hi;  /* NDRange [lo, hi) launched */
+    uint32_t valid;   /* entries whose code matched CEN */
+    uint32_t forks;   /* nextFreeCore - oldNextFreeCore */
+    uint32_t joined;  /* joinScheduled */
+    uint32_t maps;    /* map operations scheduled */
+    uint32_t pad;
+    uint64_t t_ns;    /* globaltimer at the end of the epoch */
+} trees_epoch_t;
+
+/* Copies up to `cap` per-epoch records of the last run (config.trace = 1)
+ * into host memory `out`; *n receives the number copied. */
+int trees_trace(trees_ctx *ctx, trees_epoch_t *out, size_t cap, size_t *n);
+
+/* Convenience forms of trees_run. */
+int trees_fib(trees_ctx *ctx, uint32_t n, uint32_t cutoff, void *stream);
+int trees_nqueens(trees_ctx *ctx, uint32_t n, void *stream);
+int trees_mergesort_u32(trees_ctx *ctx, uint32_t *dev_keys, uint32_t *dev_scratch, uint32_t n, void *stream);
+int trees_bfs(trees_ctx *ctx, const int32_t *dev_row_ptr, const int32_t *dev_col, int32_t nv, int32_t src,
+              int32_t *dev_level, void *stream);
+
+/* ------------------------------------------------------------ measurement */
+
+/* The critical-path floor: a persistent kernel with the context's grid that
+ * does nothing but `iters` of the scheduler's grid barrier.  Writes the
+ * device time per barrier in microseconds. */
+int trees_barrier_floor(trees_ctx *ctx, uint32_t iters, void *stream, double *us_per_barrier);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TREES_H */

@@ -1,0 +1,1001 @@
+// libtrees: the TREES epoch step on one B300 (sm_103a), behind the C ABI of
+// include/trees.h.
+//
+// Three schedulers drive the same Phase-2 tile code (trees_programs.cuh):
+//  - persistent: one cooperative launch.  Every block keeps its own copy of
+//    the epoch-range stack (the join stack + NDRange stack of Sec. 5.2) in
+//    shared memory and applies Phase 3 (Sec. 5.2.4) and Phase 1 (Sec. 5.2.2)
+//    itself from the same global counters, so an epoch costs one grid
+//    barrier (two when maps were scheduled).
+//  - graph: a CUDA graph whose conditional WHILE node runs the epoch
+//    kernel, the map kernel and a one-thread Phase-3 kernel per epoch.
+//  - hostloop: the paper's own arrangement (Sec. 5.2.2-5.2.4): the host pops
+//    the stacks, launches one kernel over the NDRange, reads nextFreeCore /
+//    joinScheduled / mapScheduled back, and launches the map kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "trees.h"
+#include "trees_dev.cuh"
+#include "trees_programs.cuh"
+
+using namespace trees;
+
+namespace {
+
+constexpr int NBLK_STATS = 8192;  // per-block statistics slots (blk_stats)
+
+// ------------------------------------------------------------------ kernels
+
+template <int BS>
+__device__ __forceinline__ void block_add_stats(unsigned long long *blk, const Acc &acc, Smem<BS> &sm) {
+    // block-reduce the per-thread counters, then one add per counter per block
+    const uint32_t v = __reduce_add_sync(0xffffffffu, acc.valid);
+    const uint32_t j = __reduce_add_sync(0xffffffffu, acc.joins);
+    const uint32_t m = __reduce_add_sync(0xffffffffu, acc.maps);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sm.bc64[0] = 0;
+        sm.bc64[1] = 0;
+        sm.bc64[2] = 0;
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sm.bc64[0], (unsigned long long)v);
+        atomicAdd(&sm.bc64[1], (unsigned long long)j);
+        atomicAdd(&sm.bc64[2], (unsigned long long)m);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long *b = blk + 4ull * (blockIdx.x % NBLK_STATS);
+        atomicAdd(b + 0, sm.bc64[0]);
+        atomicAdd(b + 1, sm.bc64[1]);
+        atomicAdd(b + 2, sm.bc64[2]);
+    }
+}
+
+template <int BS>
+__device__ __forceinline__ void trace_valid_add(const Conf &c, uint32_t e, uint32_t v, Smem<BS> &sm) {
+    if (!c.trace_on || e >= c.trace_cap) return;
+    const uint32_t w = __reduce_add_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(&c.trace_valid[e], w);
+}
+
+// Zeroes the control block and writes the root task into TV entry 0 for
+// epoch 0 (Sec. 5.2.1).
+__global__ void k_setup(Ctl *ctl, Conf c, uint32_t type, uint32_t a0, uint32_t a1) {
+    unsigned int *w = reinterpret_cast<unsigned int *>(ctl);
+    for (uint32_t i = threadIdx.x; i < sizeof(Ctl) / 4; i += blockDim.x) w[i] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        c.code[0] = enc(0u, type);
+        c.a0[0] = a0;
+        c.a1[0] = a1;
+        c.link[0] = 0u;
+        c.result[0] = 0ull;
+        ctl->g_cen = 0u;
+        ctl->g_lo = 0u;
+        ctl->g_hi = 1u;
+        ctl->g_base = 1u;
+        ctl->g_next = 1u;
+        ctl->g_e = 0u;
+        ctl->g_sp = 0u;
+        ctl->g_stop = 0u;
+        ctl->peak = 1u;
+        ctl->t_start = globaltimer();
+    }
+}
+
+__global__ void k_bfs_init(int32_t *level, int32_t nv, int32_t src) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x)
+        level[v] = (v == src) ? 0 : -1;
+}
+
+// The persistent scheduler: the whole epoch loop in one cooperative launch.
+template <int BS>
+__global__ void __launch_bounds__(BS) k_persistent(Ctl *ctl, Conf c, unsigned long long *blk) {
+    __shared__ Smem<BS> sm;
+    uint32_t bar = 0;
+    Acc acc = {0u, 0u, 0u};
+    if (threadIdx.x == 0) {
+        sm.sp = 1;
+        sm.stk[0] = Range{0u, 0u, 1u};
+        sm.next = 1u;
+    }
+    unsigned long long forks_total = 0;
+    uint32_t peak = 1u;
+    uint32_t e = 0;
+    for (;; ++e) {
+        // Phase 1: pop (CEN, NDRange); oldNextFreeCore = nextFreeCore
+        if (threadIdx.x == 0) {
+            int stop = 0;
+            if (sm.sp == 0) {
+                stop = 1;
+            } else if (e >= c.max_epochs) {
+                stop = 2;
+                set_err(ctl, TREES_ERR_EPOCH_LIMIT, e);
+            } else {
+                const Range r = sm.stk[--sm.sp];
+                sm.cen = r.cen;
+                sm.lo = r.lo;
+                sm.hi = r.hi;
+                sm.base = sm.next;
+            }
+            sm.stop = stop;
+            if (!stop && blockIdx.x == 0) {  // clear the counters epoch e+1 will use
+                const uint32_t q = (e + 1u) % 3u;
+                ctl->cnt[q] = 0u;
+                ctl->join[q] = 0u;
+                ctl->mt_ctr[q] = 0ull;
+                ctl->me_ctr[q] = 0ull;
+            }
+        }
+        __syncthreads();
+        if (sm.stop) break;
+        const uint32_t cen = sm.cen, lo = sm.lo, hi = sm.hi, base = sm.base, ep = e % 3u;
+        // Phase 2: every entry of [lo, hi)
+        const uint32_t v0 = acc.valid;
+        for (unsigned long long t0 = (unsigned long long)lo + (unsigned long long)blockIdx.x * BS; t0 < hi;
+             t0 += (unsigned long long)gridDim.x * BS) {
+            const unsigned long long s = t0 + threadIdx.x;
+            epoch_tile<BS>(c, ctl, sm, (uint32_t)s, s < hi, cen, base, ep, e, acc);
+        }
+        trace_valid_add<BS>(c, e, acc.valid - v0, sm);
+        if ((int32_t)e == c.stall_epoch && blockIdx.x == gridDim.x - 1) return;  // test hook: never arrives
+        if (!grid_sync<BS>(ctl, &bar, c.timeout_ns, sm)) break;
+        const unsigned long long mt = vload(&ctl->mt_ctr[ep]), me = vload(&ctl->me_ctr[ep]);
+        if (mt | me) {  // the map operations of this epoch run before the next one (Sec. 5.2.4)
+            map_phase<BS>(c, ctl, sm, ep, e, cen, base, mt, me);
+            if (!grid_sync<BS>(ctl, &bar, c.timeout_ns, sm)) break;
+        }
+        // Phase 3: push the join range, then the fork range; or give the range back
+        if (threadIdx.x == 0) {
+            const uint32_t f = vload(&ctl->cnt[ep]), jf = vload(&ctl->join[ep]);
+            int ok = 1;
+            if (jf) {
+                if (sm.sp < STK_CAP) sm.stk[sm.sp++] = Range{cen, lo, hi};
+                else ok = 0;
+            }
+            if (f) {
+                if (sm.sp < STK_CAP) sm.stk[sm.sp++] = Range{cen + 1u, base, base + f};
+                else ok = 0;
+                sm.next = base + f;
+            } else if (!jf) {
+                sm.next = lo;  // neither forks nor joins: nextFreeCore decreases (Sec. 5.3)
+            }
+            if (!ok) {
+                if (blockIdx.x == 0) set_err(ctl, TREES_ERR_STACK, e);
+                sm.sp = 0;
+            }
+            if (blockIdx.x == 0) {
+                forks_total += f;
+                peak = max(peak, base + f);
+                if (c.trace_on && e < c.trace_cap) {
+                    trees_epoch_t r;
+                    r.cen = cen;
+                    r.lo = lo;
+                    r.hi = hi;
+                    r.valid = 0u;
+                    r.forks = f;
+                    r.joined = jf;
+                    r.maps = (uint32_t)(mt >> 40) + (uint32_t)(me >> 40);
+                    r.pad = 0u;
+                    r.t_ns = globaltimer();
+                    c.trace[e] = r;
+                }
+            }
+        }
+    }
+    block_add_stats<BS>(blk, acc, sm);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->epochs = e;
+        ctl->peak = peak;
+        ctl->final_next = sm.next;
+        ctl->forks = forks_total;
+        ctl->t_end = globaltimer();
+    }
+}
+
+// Phase 2 of one epoch as its own kernel (graph and host-loop schedulers).
+// from_ctl = 1: the epoch comes from the control block (graph); 0: from the
+// arguments (host loop, grid sized to the NDRange as in Sec. 5.1.1).
+template <int BS>
+__global__ void __launch_bounds__(BS) k_epoch(Ctl *ctl, Conf c, unsigned long long *blk, int from_ctl, uint32_t a_cen,
+                                              uint32_t a_lo, uint32_t a_hi, uint32_t a_base, uint32_t a_e) {
+    __shared__ Smem<BS> sm;
+    if (threadIdx.x == 0) {
+        sm.stop = vload(&ctl->err) != 0 || (from_ctl && vload(&ctl->g_stop) != 0u);
+        if (from_ctl) {
+            sm.cen = vload(&ctl->g_cen);
+            sm.lo = vload(&ctl->g_lo);
+            sm.hi = vload(&ctl->g_hi);
+            sm.base = vload(&ctl->g_base);
+            sm.next = vload(&ctl->g_e);
+        } else {
+            sm.cen = a_cen;
+            sm.lo = a_lo;
+            sm.hi = a_hi;
+            sm.base = a_base;
+            sm.next = a_e;
+        }
+    }
+    __syncthreads();
+    if (sm.stop) return;
+    const uint32_t cen = sm.cen, lo = sm.lo, hi = sm.hi, base = sm.base, e = sm.next, ep = e % 3u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint32_t q = (e + 1u) % 3u;
+        ctl->cnt[q] = 0u;
+        ctl->join[q] = 0u;
+        ctl->mt_ctr[q] = 0ull;
+        ctl->me_ctr[q] = 0ull;
+    }
+    Acc acc = {0u, 0u, 0u};
+    for (unsigned long long t0 = (unsigned long long)lo + (unsigned long long)blockIdx.x * BS; t0 < hi;
+         t0 += (unsigned long long)gridDim.x * BS) {
+        const unsigned long long s = t0 + threadIdx.x;
+        epoch_tile<BS>(c, ctl, sm, (uint32_t)s, s < hi, cen, base, ep, e, acc);
+    }
+    trace_valid_add<BS>(c, e, acc.valid, sm);
+    block_add_stats<BS>(blk, acc, sm);
+}
+
+// The map operations scheduled in one epoch, as their own kernel.
+template <int BS>
+__global__ void __launch_bounds__(BS) k_map(Ctl *ctl, Conf c, int from_ctl, uint32_t a_cen, uint32_t a_base,
+                                            uint32_t a_e) {
+    __shared__ Smem<BS> sm;
+    if (threadIdx.x == 0) {
+        sm.stop = vload(&ctl->err) != 0 || (from_ctl && vload(&ctl->g_stop) != 0u);
+        sm.cen = from_ctl ? vload(&ctl->g_cen) : a_cen;
+        sm.base = from_ctl ? vload(&ctl->g_base) : a_base;
+        sm.next = from_ctl ? vload(&ctl->g_e) : a_e;
+    }
+    __syncthreads();
+    if (sm.stop) return;
+    const uint32_t cen = sm.cen, base = sm.base, e = sm.next, ep = e % 3u;
+    const unsigned long long mt = vload(&ctl->mt_ctr[ep]), me = vload(&ctl->me_ctr[ep]);
+    if (!(mt | me)) return;
+    map_phase<BS>(c, ctl, sm, ep, e, cen, base, mt, me);
+}
+
+// Phase 3 + Phase 1 of the graph scheduler (one thread): updates the
+// device-resident stacks and ends the WHILE loop when they are empty.
+__global__ void k_phase3(Ctl *ctl, Conf c, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0) return;
+    uint32_t cont = 1u;
+    if (ctl->g_stop) {
+        cont = 0u;
+    } else {
+        const uint32_t e = ctl->g_e, ep = e % 3u;
+        const uint32_t cen = ctl->g_cen, lo = ctl->g_lo, hi = ctl->g_hi, base = ctl->g_base;
+        const uint32_t f = ctl->cnt[ep], jf = ctl->join[ep];
+        const unsigned long long mt = ctl->mt_ctr[ep], me = ctl->me_ctr[ep];
+        uint32_t sp = ctl->g_sp, next = base;
+        int ok = 1;
+        if (jf) {
+            if (sp < c.gstack_cap) c.gstack[sp++] = Range{cen, lo, hi};
+            else ok = 0;
+        }
+        if (f) {
+            if (sp < c.gstack_cap) c.gstack[sp++] = Range{cen + 1u, base, base + f};
+            else ok = 0;
+            next = base + f;
+        } else if (!jf) {
+            next = lo;
+        }
+        ctl->forks += f;
+        ctl->peak = max(ctl->peak, base + f);
+        if (c.trace_on && e < c.trace_cap) {
+            trees_epoch_t r;
+            r.cen = cen;
+            r.lo = lo;
+            r.hi = hi;
+            r.valid = 0u;
+            r.forks = f;
+            r.joined = jf;
+            r.maps = (uint32_t)(mt >> 40) + (uint32_t)(me >> 40);
+            r.pad = 0u;
+            r.t_ns = globaltimer();
+            c.trace[e] = r;
+        }
+        const uint32_t ne = e + 1u;
+        ctl->g_e = ne;
+        ctl->g_next = next;
+        if (!ok) set_err(ctl, TREES_ERR_STACK, e);
+        if (ctl->err || !ok) {
+            cont = 0u;
+        } else if (sp == 0u) {
+            cont = 0u;
+        } else if (ne >= c.max_epochs) {
+            set_err(ctl, TREES_ERR_EPOCH_LIMIT, ne);
+            cont = 0u;
+        } else {
+            const Range r = c.gstack[--sp];
+            ctl->g_cen = r.cen;
+            ctl->g_lo = r.lo;
+            ctl->g_hi = r.hi;
+            ctl->g_base = next;
+        }
+        ctl->g_sp = sp;
+        if (!cont) {
+            ctl->g_stop = 1u;
+            ctl->epochs = ne;
+            ctl->final_next = next;
+            ctl->t_end = globaltimer();
+        }
+    }
+    if (ctl->err && !ctl->g_stop) {
+        ctl->g_stop = 1u;
+        ctl->epochs = ctl->g_e;
+        ctl->t_end = globaltimer();
+        cont = 0u;
+    }
+    cudaGraphSetConditional(h, cont);
+}
+
+// The critical-path floor: only grid barriers, same grid as k_persistent.
+template <int BS>
+__global__ void __launch_bounds__(BS) k_floor(Ctl *ctl, uint32_t iters, unsigned long long timeout_ns) {
+    __shared__ Smem<BS> sm;
+    uint32_t bar = 0;
+    for (uint32_t i = 0; i < iters; ++i)
+        if (!grid_sync<BS>(ctl, &bar, timeout_ns, sm)) break;
+}
+
+// ------------------------------------------------------------------ host side
+
+struct Kern {
+    const void *persistent, *epoch, *map, *floor;
+};
+
+template <int BS>
+Kern kern_for() {
+    return Kern{(const void *)k_persistent<BS>, (const void *)k_epoch<BS>, (const void *)k_map<BS>,
+                (const void *)k_floor<BS>};
+}
+
+bool kern_by_bs(int bs, Kern *k) {
+    switch (bs) {
+    case 256: *k = kern_for<256>(); return true;
+    case 512: *k = kern_for<512>(); return true;
+    case 1024: *k = kern_for<1024>(); return true;
+    default: return false;
+    }
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    size_t off_dev, off_code, off_a0, off_a1, off_link, off_result;
+    size_t off_mt[7], off_me[4], off_trace, off_tvalid, off_gstack, off_blk, total;
+};
+
+Layout make_layout(size_t cap, size_t mcap, size_t trace_cap, size_t gstack_cap) {
+    Layout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o = align_up(o + bytes, 256);
+        return r;
+    };
+    L.off_dev = take(sizeof(Dev));
+    L.off_code = take(cap * 4);
+    L.off_a0 = take(cap * 4);
+    L.off_a1 = take(cap * 4);
+    L.off_link = take(cap * 4);
+    L.off_result = take(cap * 8);
+    for (int i = 0; i < 7; ++i) L.off_mt[i] = take(mcap * 4);
+    for (int i = 0; i < 4; ++i) L.off_me[i] = take(mcap * 4);
+    L.off_trace = take(trace_cap * sizeof(trees_epoch_t));
+    L.off_tvalid = take(trace_cap * 4);
+    L.off_gstack = take(gstack_cap * sizeof(Range));
+    L.off_blk = take((size_t)NBLK_STATS * 4 * 8);
+    L.total = o;
+    return L;
+}
+
+void normalize(trees_config_t *c) {
+    if (c->block_size == 0) c->block_size = 512;
+    if (c->max_epochs == 0) c->max_epochs = 1u << 20;
+    if (c->trace_cap == 0) c->trace_cap = 65536;
+    if (c->timeout_ns == 0) c->timeout_ns = 2000000000ull;
+}
+
+}  // namespace
+
+struct trees_ctx {
+    int device = 0, sms = 0;
+    trees_config_t cfg{};
+    char *mem = nullptr;
+    size_t bytes = 0;
+    bool owns = false;
+    Layout L{};
+    Ctl *ctl = nullptr;
+    Conf conf{};
+    unsigned long long *blk = nullptr;
+    uint32_t cap = 0, mcap = 0;
+    int grid = 0, bs = 0;
+    Kern kern{};
+    cudaStream_t last_stream = nullptr;
+    uint32_t *own_scratch = nullptr;
+    size_t own_scratch_n = 0;
+    // graph scheduler
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraphNode_t gnode_epoch = nullptr, gnode_map = nullptr, gnode_p3 = nullptr;
+    cudaGraphConditionalHandle gh = 0;
+    // host-loop scheduler
+    std::vector<trees_epoch_t> host_trace;
+    int last_sched = TREES_SCHED_PERSISTENT;
+    int host_status = TREES_OK;
+    Ctl *pinned_ctl = nullptr;
+};
+
+extern "C" {
+
+void trees_default_config(trees_config_t *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->block_size = 512;
+    cfg->blocks_per_sm = 0;
+    cfg->scheduler = TREES_SCHED_PERSISTENT;
+    cfg->trace = 0;
+    cfg->max_epochs = 1u << 20;
+    cfg->trace_cap = 65536;
+    cfg->timeout_ns = 2000000000ull;
+    cfg->map_capacity = 0;
+    cfg->inject_stall_epoch = -1;
+}
+
+static size_t bytes_for_cfg(size_t cap, const trees_config_t &c) {
+    const size_t mcap = c.map_capacity ? (size_t)c.map_capacity : cap;
+    return make_layout(cap, mcap, c.trace_cap, STK_CAP).total;
+}
+
+size_t trees_bytes_for(size_t capacity_slots, const trees_config_t *cfg) {
+    trees_config_t c;
+    if (cfg) c = *cfg;
+    else trees_default_config(&c);
+    normalize(&c);
+    if (capacity_slots == 0 || capacity_slots > 0xFFFFFFFFull) return 0;
+    return bytes_for_cfg(capacity_slots, c);
+}
+
+static int finish_create(trees_ctx *x) {
+    if (cudaGetDevice(&x->device) != cudaSuccess) return TREES_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, x->device) != cudaSuccess)
+        return TREES_ERR_CUDA;
+    if (!kern_by_bs(x->cfg.block_size, &x->kern)) return TREES_ERR_INVALID_ARG;
+    x->bs = x->cfg.block_size;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, x->kern.persistent, x->bs, 0) != cudaSuccess || occ < 1)
+        return TREES_ERR_CUDA;
+    int per_sm = x->cfg.blocks_per_sm > 0 ? std::min(x->cfg.blocks_per_sm, occ) : occ;
+    x->grid = x->sms * per_sm;
+    char *m = x->mem;
+    const Layout &L = x->L;
+    x->ctl = reinterpret_cast<Ctl *>(m + L.off_dev);
+    Conf &c = x->conf;
+    std::memset(&c, 0, sizeof(c));
+    c.code = reinterpret_cast<uint32_t *>(m + L.off_code);
+    c.a0 = reinterpret_cast<uint32_t *>(m + L.off_a0);
+    c.a1 = reinterpret_cast<uint32_t *>(m + L.off_a1);
+    c.link = reinterpret_cast<uint32_t *>(m + L.off_link);
+    c.result = reinterpret_cast<unsigned long long *>(m + L.off_result);
+    c.cap = x->cap;
+    uint32_t **mt[7] = {&c.mt_kind, &c.mt_a, &c.mt_b, &c.mt_c, &c.mt_job, &c.mt_tilebase, &c.mt_tiledesc};
+    for (int i = 0; i < 7; ++i) *mt[i] = reinterpret_cast<uint32_t *>(m + L.off_mt[i]);
+    uint32_t **me[4] = {&c.me_v, &c.me_base, &c.me_job, &c.me_tfd};
+    for (int i = 0; i < 4; ++i) *me[i] = reinterpret_cast<uint32_t *>(m + L.off_me[i]);
+    c.mcap = x->mcap;
+    c.trace = reinterpret_cast<trees_epoch_t *>(m + L.off_trace);
+    c.trace_valid = reinterpret_cast<uint32_t *>(m + L.off_tvalid);
+    c.trace_cap = x->cfg.trace_cap;
+    c.trace_on = x->cfg.trace;
+    c.max_epochs = x->cfg.max_epochs;
+    c.stall_epoch = x->cfg.inject_stall_epoch;
+    c.timeout_ns = x->cfg.timeout_ns;
+    c.gstack = reinterpret_cast<Range *>(m + L.off_gstack);
+    c.gstack_cap = STK_CAP;
+    x->blk = reinterpret_cast<unsigned long long *>(m + L.off_blk);
+    if (cudaMallocHost(&x->pinned_ctl, sizeof(Ctl)) != cudaSuccess) return TREES_ERR_CUDA;
+    if (cudaMemset(x->ctl, 0, sizeof(Ctl)) != cudaSuccess) return TREES_ERR_CUDA;
+    return TREES_OK;
+}
+
+static int validate_cfg(const trees_config_t *cfg, trees_config_t *out) {
+    if (cfg) *out = *cfg;
+    else trees_default_config(out);
+    normalize(out);
+    if (out->block_size != 256 && out->block_size != 512 && out->block_size != 1024) return TREES_ERR_INVALID_ARG;
+    if (out->scheduler < TREES_SCHED_PERSISTENT || out->scheduler > TREES_SCHED_HOSTLOOP) return TREES_ERR_INVALID_ARG;
+    if (out->blocks_per_sm < 0) return TREES_ERR_INVALID_ARG;
+    return TREES_OK;
+}
+
+int trees_create(size_t capacity_slots, const trees_config_t *cfg, trees_ctx **out) {
+    if (!out || capacity_slots == 0 || capacity_slots > 0xFFFFFFFFull) return TREES_ERR_INVALID_ARG;
+    *out = nullptr;
+    trees_ctx *x = new (std::nothrow) trees_ctx();
+    if (!x) return TREES_ERR_INVALID_ARG;
+    int rc = validate_cfg(cfg, &x->cfg);
+    if (rc) {
+        delete x;
+        return rc;
+    }
+    x->cap = (uint32_t)capacity_slots;
+    const uint64_t mc = x->cfg.map_capacity ? x->cfg.map_capacity : capacity_slots;
+    if (mc > 0xFFFFFFFFull) {
+        delete x;
+        return TREES_ERR_INVALID_ARG;
+    }
+    x->mcap = (uint32_t)mc;
+    x->L = make_layout(x->cap, x->mcap, x->cfg.trace_cap, STK_CAP);
+    if (cudaMalloc(&x->mem, x->L.total) != cudaSuccess) {
+        cudaGetLastError();
+        delete x;
+        return TREES_ERR_CUDA;
+    }
+    x->owns = true;
+    x->bytes = x->L.total;
+    rc = finish_create(x);
+    if (rc) {
+        trees_destroy(x);
+        return rc;
+    }
+    *out = x;
+    return TREES_OK;
+}
+
+int trees_create_on(void *dev_buf, size_t bytes, const trees_config_t *cfg, trees_ctx **out) {
+    if (!out || !dev_buf || ((uintptr_t)dev_buf & 255u)) return TREES_ERR_INVALID_ARG;
+    *out = nullptr;
+    trees_ctx *x = new (std::nothrow) trees_ctx();
+    if (!x) return TREES_ERR_INVALID_ARG;
+    int rc = validate_cfg(cfg, &x->cfg);
+    if (rc) {
+        delete x;
+        return rc;
+    }
+    // the largest capacity whose layout fits (binary search on slots)
+    size_t lo = 0, hi = 0xFFFFFFFFull;
+    while (lo < hi) {
+        const size_t mid = lo + (hi - lo + 1) / 2;
+        if (bytes_for_cfg(mid, x->cfg) <= bytes) lo = mid;
+        else hi = mid - 1;
+    }
+    if (lo == 0) {
+        delete x;
+        return TREES_ERR_INVALID_ARG;
+    }
+    x->cap = (uint32_t)lo;
+    x->mcap = x->cfg.map_capacity ? (uint32_t)std::min<uint64_t>(x->cfg.map_capacity, 0xFFFFFFFFull) : x->cap;
+    x->L = make_layout(x->cap, x->mcap, x->cfg.trace_cap, STK_CAP);
+    x->mem = static_cast<char *>(dev_buf);
+    x->owns = false;
+    x->bytes = bytes;
+    rc = finish_create(x);
+    if (rc) {
+        trees_destroy(x);
+        return rc;
+    }
+    *out = x;
+    return TREES_OK;
+}
+
+void trees_destroy(trees_ctx *x) {
+    if (!x) return;
+    if (x->gexec) cudaGraphExecDestroy(x->gexec);
+    if (x->graph) cudaGraphDestroy(x->graph);
+    if (x->own_scratch) cudaFree(x->own_scratch);
+    if (x->pinned_ctl) cudaFreeHost(x->pinned_ctl);
+    if (x->owns && x->mem) cudaFree(x->mem);
+    delete x;
+}
+
+size_t trees_capacity(const trees_ctx *x) { return x ? x->cap : 0; }
+
+int trees_geometry(const trees_ctx *x, int32_t *grid_blocks, int32_t *block_size, int32_t *sms) {
+    if (!x) return TREES_ERR_INVALID_ARG;
+    if (grid_blocks) *grid_blocks = x->grid;
+    if (block_size) *block_size = x->bs;
+    if (sms) *sms = x->sms;
+    return TREES_OK;
+}
+
+// Builds the graph of the graph scheduler once per context: a conditional
+// WHILE node whose body is epoch kernel -> map kernel -> Phase-3 kernel.
+static int build_graph(trees_ctx *x) {
+    if (x->gexec) return TREES_OK;
+    if (cudaGraphCreate(&x->graph, 0) != cudaSuccess) return TREES_ERR_CUDA;
+    if (cudaGraphConditionalHandleCreate(&x->gh, x->graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        return TREES_ERR_CUDA;
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = x->gh;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    if (cudaGraphAddNode(&cnode, x->graph, nullptr, nullptr, 0, &cp) != cudaSuccess) return TREES_ERR_CUDA;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+
+    static int from_ctl = 1;
+    static uint32_t zero = 0;
+    void *ep_args[] = {&x->ctl, &x->conf, &x->blk, &from_ctl, &zero, &zero, &zero, &zero, &zero};
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.func = const_cast<void *>(x->kern.epoch);
+    kp.gridDim = dim3(x->grid);
+    kp.blockDim = dim3(x->bs);
+    kp.kernelParams = ep_args;
+    if (cudaGraphAddKernelNode(&x->gnode_epoch, body, nullptr, 0, &kp) != cudaSuccess) return TREES_ERR_CUDA;
+    void *map_args[] = {&x->ctl, &x->conf, &from_ctl, &zero, &zero, &zero};
+    kp.func = const_cast<void *>(x->kern.map);
+    kp.kernelParams = map_args;
+    if (cudaGraphAddKernelNode(&x->gnode_map, body, &x->gnode_epoch, 1, &kp) != cudaSuccess) return TREES_ERR_CUDA;
+    void *p3_args[] = {&x->ctl, &x->conf, &x->gh};
+    kp.func = (void *)k_phase3;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = p3_args;
+    if (cudaGraphAddKernelNode(&x->gnode_p3, body, &x->gnode_map, 1, &kp) != cudaSuccess) return TREES_ERR_CUDA;
+    if (cudaGraphInstantiate(&x->gexec, x->graph, 0) != cudaSuccess) return TREES_ERR_CUDA;
+    return TREES_OK;
+}
+
+// Refreshes the Conf argument of the graph's kernels (the job changes per run).
+static int update_graph_args(trees_ctx *x) {
+    static int from_ctl = 1;
+    static uint32_t zero = 0;
+    void *ep_args[] = {&x->ctl, &x->conf, &x->blk, &from_ctl, &zero, &zero, &zero, &zero, &zero};
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.func = const_cast<void *>(x->kern.epoch);
+    kp.gridDim = dim3(x->grid);
+    kp.blockDim = dim3(x->bs);
+    kp.kernelParams = ep_args;
+    if (cudaGraphExecKernelNodeSetParams(x->gexec, x->gnode_epoch, &kp) != cudaSuccess) return TREES_ERR_CUDA;
+    void *map_args[] = {&x->ctl, &x->conf, &from_ctl, &zero, &zero, &zero};
+    kp.func = const_cast<void *>(x->kern.map);
+    kp.kernelParams = map_args;
+    if (cudaGraphExecKernelNodeSetParams(x->gexec, x->gnode_map, &kp) != cudaSuccess) return TREES_ERR_CUDA;
+    void *p3_args[] = {&x->ctl, &x->conf, &x->gh};
+    kp.func = (void *)k_phase3;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = p3_args;
+    if (cudaGraphExecKernelNodeSetParams(x->gexec, x->gnode_p3, &kp) != cudaSuccess) return TREES_ERR_CUDA;
+    return TREES_OK;
+}
+
+// The paper's host loop (Sec. 5.2.2-5.2.4), one launch and one read-back per epoch.
+static int run_hostloop(trees_ctx *x, cudaStream_t st) {
+    struct R {
+        uint32_t cen, lo, hi;
+    };
+    std::vector<R> stk;
+    x->host_trace.clear();
+    uint32_t cen = 0, lo = 0, hi = 1, base = 1, e = 0, next = 1, peak = 1;
+    unsigned long long forks = 0;
+    int status = TREES_OK;
+    Ctl *h = x->pinned_ctl;
+    for (;;) {
+        const uint32_t ep = e % 3u;
+        const uint32_t nb = (hi - lo + x->bs - 1) / x->bs;
+        void *args[] = {&x->ctl, &x->conf, &x->blk, nullptr, &cen, &lo, &hi, &base, &e};
+        int from_ctl = 0;
+        args[3] = &from_ctl;
+        if (cudaLaunchKernel(x->kern.epoch, dim3(nb), dim3(x->bs), args, 0, st) != cudaSuccess) return TREES_ERR_CUDA;
+        if (cudaMemcpyAsync(h, x->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess) return TREES_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return TREES_ERR_CUDA;
+        if (h->err) {
+            status = h->err;
+            break;
+        }
+        const unsigned long long mt = h->mt_ctr[ep], me = h->me_ctr[ep];
+        if (mt | me) {  // mapScheduled: run the map kernel before the next epoch
+            void *margs[] = {&x->ctl, &x->conf, &from_ctl, &cen, &base, &e};
+            if (cudaLaunchKernel(x->kern.map, dim3(x->grid), dim3(x->bs), margs, 0, st) != cudaSuccess)
+                return TREES_ERR_CUDA;
+            if (cudaMemcpyAsync(h, x->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                return TREES_ERR_CUDA;
+            if (cudaStreamSynchronize(st) != cudaSuccess) return TREES_ERR_CUDA;
+            if (h->err) {
+                status = h->err;
+                break;
+            }
+        }
+        const uint32_t f = h->cnt[ep], jf = h->join[ep];
+        if (jf) stk.push_back(R{cen, lo, hi});
+        if (f) {
+            stk.push_back(R{cen + 1u, base, base + f});
+            next = base + f;
+        } else if (!jf) {
+            next = lo;
+        }
+        forks += f;
+        peak = std::max(peak, base + f);
+        trees_epoch_t r;
+        std::memset(&r, 0, sizeof(r));
+        r.cen = cen;
+        r.lo = lo;
+        r.hi = hi;
+        r.forks = f;
+        r.joined = jf;
+        r.maps = (uint32_t)(mt >> 40) + (uint32_t)(me >> 40);
+        if (x->cfg.trace && e < x->cfg.trace_cap) x->host_trace.push_back(r);
+        ++e;
+        if (stk.size() > STK_CAP) {
+            status = TREES_ERR_STACK;
+            break;
+        }
+        if (stk.empty()) break;
+        if (e >= x->cfg.max_epochs) {
+            status = TREES_ERR_EPOCH_LIMIT;
+            break;
+        }
+        const R r2 = stk.back();
+        stk.pop_back();
+        cen = r2.cen;
+        lo = r2.lo;
+        hi = r2.hi;
+        base = next;
+    }
+    // record the run's scheduler-side statistics where trees_stats reads them
+    Ctl upd;
+    if (cudaMemcpy(&upd, x->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return TREES_ERR_CUDA;
+    upd.epochs = e;
+    upd.peak = peak;
+    upd.final_next = next;
+    upd.forks = forks;
+    if (status != TREES_OK && upd.err == 0) {
+        upd.err = status;
+        upd.err_epoch = e;
+    }
+    if (cudaMemcpy(x->ctl, &upd, sizeof(Ctl), cudaMemcpyHostToDevice) != cudaSuccess) return TREES_ERR_CUDA;
+    return status;
+}
+
+int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
+    if (!x || !job) return TREES_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    RunParams &rp = x->conf.rp;
+    std::memset(&rp, 0, sizeof(rp));
+    rp.program = job->program;
+    rp.n = job->n;
+    rp.cutoff = job->cutoff;
+    rp.leaf = job->leaf ? job->leaf : LEAF_MAX;
+    uint32_t type = 0, a0 = 0, a1 = 0;
+    switch (job->program) {
+    case TREES_PROG_FIB:
+        if (job->n > 93 || job->cutoff > 30) return TREES_ERR_INVALID_ARG;
+        type = TREES_TASK_FIB;
+        a0 = job->n;
+        break;
+    case TREES_PROG_NQUEENS:
+        if (job->n < 1 || job->n > 16) return TREES_ERR_INVALID_ARG;
+        type = TREES_TASK_NQ_ROW;
+        break;
+    case TREES_PROG_MERGESORT:
+        if (rp.leaf > (uint32_t)LEAF_MAX || (job->n && !job->keys)) return TREES_ERR_INVALID_ARG;
+        rp.keys = job->keys;
+        rp.scratch = job->scratch;
+        if (!rp.scratch && job->n) {
+            if (x->own_scratch_n < job->n) {
+                if (x->own_scratch) cudaFree(x->own_scratch);
+                x->own_scratch = nullptr;
+                x->own_scratch_n = 0;
+                if (cudaMalloc(&x->own_scratch, (size_t)job->n * 4) != cudaSuccess) return TREES_ERR_CUDA;
+                x->own_scratch_n = job->n;
+            }
+            rp.scratch = x->own_scratch;
+        }
+        type = TREES_TASK_MS_SPLIT;
+        a0 = 0;
+        a1 = job->n;
+        break;
+    case TREES_PROG_BFS:
+        if (!job->row_ptr || !job->level || job->nv < 1 || (int32_t)job->n < 0 || (int32_t)job->n >= job->nv)
+            return TREES_ERR_INVALID_ARG;
+        rp.row_ptr = job->row_ptr;
+        rp.col = job->col;
+        rp.level = job->level;
+        rp.nv = job->nv;
+        type = TREES_TASK_BFS_VISIT;
+        a0 = job->n;
+        break;
+    case TREES_PROG_POSTORDER:
+    case TREES_PROG_PREORDER:
+        if (job->n && (!job->left || !job->right || !job->visit_epoch)) return TREES_ERR_INVALID_ARG;
+        rp.left = job->left;
+        rp.right = job->right;
+        rp.visit_epoch = job->visit_epoch;
+        type = job->program == TREES_PROG_POSTORDER ? TREES_TASK_PO : TREES_TASK_PRE;
+        a0 = job->n ? 0u : 0xFFFFFFFFu;
+        break;
+    default:
+        return TREES_ERR_INVALID_ARG;
+    }
+    x->last_stream = st;
+    x->last_sched = x->cfg.scheduler;
+    if (cudaMemsetAsync(x->blk, 0, (size_t)NBLK_STATS * 4 * 8, st) != cudaSuccess) return TREES_ERR_CUDA;
+    if (x->cfg.trace && cudaMemsetAsync(x->conf.trace_valid, 0, (size_t)x->cfg.trace_cap * 4, st) != cudaSuccess)
+        return TREES_ERR_CUDA;
+    k_setup<<<1, 256, 0, st>>>(x->ctl, x->conf, type, a0, a1);
+    if (job->program == TREES_PROG_BFS) {
+        const int nb = std::min<int64_t>((job->nv + 255) / 256, 65536);
+        k_bfs_init<<<nb, 256, 0, st>>>(job->level, job->nv, (int32_t)job->n);
+    }
+    if (job->program == TREES_PROG_POSTORDER || job->program == TREES_PROG_PREORDER) {
+        if (job->n && cudaMemsetAsync(job->visit_epoch, 0xFF, (size_t)job->n * 4, st) != cudaSuccess)
+            return TREES_ERR_CUDA;
+    }
+    if (cudaGetLastError() != cudaSuccess) return TREES_ERR_CUDA;
+    switch (x->cfg.scheduler) {
+    case TREES_SCHED_PERSISTENT: {
+        void *args[] = {&x->ctl, &x->conf, &x->blk};
+        if (cudaLaunchCooperativeKernel(x->kern.persistent, dim3(x->grid), dim3(x->bs), args, 0, st) != cudaSuccess) {
+            cudaGetLastError();
+            return TREES_ERR_CUDA;
+        }
+        return TREES_OK;
+    }
+    case TREES_SCHED_GRAPH: {
+        int rc = build_graph(x);
+        if (rc) return rc;
+        rc = update_graph_args(x);
+        if (rc) return rc;
+        if (cudaGraphLaunch(x->gexec, st) != cudaSuccess) return TREES_ERR_CUDA;
+        return TREES_OK;
+    }
+    case TREES_SCHED_HOSTLOOP: {
+        const int rc = run_hostloop(x, st);
+        x->host_status = rc;
+        return (rc == TREES_ERR_CUDA || rc == TREES_ERR_INVALID_ARG) ? rc : TREES_OK;
+    }
+    }
+    return TREES_ERR_INVALID_ARG;
+}
+
+int trees_sync(trees_ctx *x) {
+    if (!x) return TREES_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(x->last_stream) != cudaSuccess) return TREES_ERR_CUDA;
+    int err = 0;
+    if (cudaMemcpy(&err, &x->ctl->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TREES_ERR_CUDA;
+    return err;
+}
+
+int trees_result(trees_ctx *x, uint32_t slot, uint64_t *out) {
+    if (!x || !out || slot >= x->cap) return TREES_ERR_INVALID_ARG;
+    unsigned long long v = 0;
+    if (cudaMemcpy(&v, x->conf.result + slot, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return TREES_ERR_CUDA;
+    *out = v;
+    return TREES_OK;
+}
+
+int trees_stats(trees_ctx *x, trees_stats_t *out) {
+    if (!x || !out) return TREES_ERR_INVALID_ARG;
+    Ctl h;
+    if (cudaMemcpy(&h, x->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return TREES_ERR_CUDA;
+    std::vector<unsigned long long> blk((size_t)NBLK_STATS * 4);
+    if (cudaMemcpy(blk.data(), x->blk, blk.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return TREES_ERR_CUDA;
+    unsigned long long tasks = 0, joins = 0, maps = 0;
+    for (int b = 0; b < NBLK_STATS; ++b) {
+        tasks += blk[4 * b + 0];
+        joins += blk[4 * b + 1];
+        maps += blk[4 * b + 2];
+    }
+    out->epochs = h.epochs;
+    out->tasks = tasks;
+    out->forks = h.forks;
+    out->joins = joins;
+    out->maps = maps;
+    out->peak_slots = h.peak;
+    out->final_slots = h.final_next;
+    out->ns = h.t_end > h.t_start ? h.t_end - h.t_start : 0;
+    out->status = h.err;
+    out->error_epoch = (int32_t)h.err_epoch;
+    return TREES_OK;
+}
+
+int trees_trace(trees_ctx *x, trees_epoch_t *out, size_t cap, size_t *n) {
+    if (!x || (!out && cap) || !n) return TREES_ERR_INVALID_ARG;
+    Ctl h;
+    if (cudaMemcpy(&h, x->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return TREES_ERR_CUDA;
+    size_t m = std::min<size_t>({cap, (size_t)h.epochs, (size_t)x->cfg.trace_cap});
+    if (!x->cfg.trace) m = 0;
+    std::vector<uint32_t> valid(m);
+    if (m) {
+        if (x->last_sched == TREES_SCHED_HOSTLOOP) {
+            m = std::min(m, x->host_trace.size());
+            std::memcpy(out, x->host_trace.data(), m * sizeof(trees_epoch_t));
+        } else if (cudaMemcpy(out, x->conf.trace, m * sizeof(trees_epoch_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            return TREES_ERR_CUDA;
+        }
+        if (cudaMemcpy(valid.data(), x->conf.trace_valid, m * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return TREES_ERR_CUDA;
+        for (size_t i = 0; i < m; ++i) out[i].valid = valid[i];
+    }
+    *n = m;
+    return TREES_OK;
+}
+
+int trees_fib(trees_ctx *x, uint32_t n, uint32_t cutoff, void *stream) {
+    trees_job_t j;
+    std::memset(&j, 0, sizeof(j));
+    j.program = TREES_PROG_FIB;
+    j.n = n;
+    j.cutoff = cutoff;
+    return trees_run(x, &j, stream);
+}
+
+int trees_nqueens(trees_ctx *x, uint32_t n, void *stream) {
+    trees_job_t j;
+    std::memset(&j, 0, sizeof(j));
+    j.program = TREES_PROG_NQUEENS;
+    j.n = n;
+    return trees_run(x, &j, stream);
+}
+
+int trees_mergesort_u32(trees_ctx *x, uint32_t *keys, uint32_t *scratch, uint32_t n, void *stream) {
+    trees_job_t j;
+    std::memset(&j, 0, sizeof(j));
+    j.program = TREES_PROG_MERGESORT;
+    j.n = n;
+    j.keys = keys;
+    j.scratch = scratch;
+    return trees_run(x, &j, stream);
+}
+
+int trees_bfs(trees_ctx *x, const int32_t *row_ptr, const int32_t *col, int32_t nv, int32_t src, int32_t *level,
+              void *stream) {
+    trees_job_t j;
+    std::memset(&j, 0, sizeof(j));
+    j.program = TREES_PROG_BFS;
+    j.n = (uint32_t)src;
+    j.row_ptr = row_ptr;
+    j.col = col;
+    j.nv = nv;
+    j.level = level;
+    return trees_run(x, &j, stream);
+}
+
+int trees_barrier_floor(trees_ctx *x, uint32_t iters, void *stream, double *us) {
+    if (!x || !us || iters == 0) return TREES_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return TREES_ERR_CUDA;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return TREES_ERR_CUDA;
+    }
+    int rc = TREES_OK;
+    unsigned long long to = x->cfg.timeout_ns;
+    void *args[] = {&x->ctl, &iters, &to};
+    if (cudaMemsetAsync(x->ctl, 0, sizeof(Ctl), st) != cudaSuccess ||
+        cudaEventRecord(a, st) != cudaSuccess ||
+        cudaLaunchCooperativeKernel(x->kern.floor, dim3(x->grid), dim3(x->bs), args, 0, st) != cudaSuccess ||
+        cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
+        cudaGetLastError();
+        rc = TREES_ERR_CUDA;
+    }
+    if (!rc) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        *us = 1000.0 * ms / iters;
+        int err = 0;
+        cudaMemcpy(&err, &x->ctl->err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (err) rc = err;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return rc;
+}
+
+}  // extern "C"

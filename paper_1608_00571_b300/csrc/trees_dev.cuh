@@ -1,0 +1,280 @@
+// Device-side internals of libtrees: the task vector layout, the control
+// block, the timed grid barrier and the block-wide scans the cooperative
+// allocator is built from.
+//
+// Layout (Sec. 5.1.2, re-designed for coalescing on sm_103a): the task vector
+// is a structure of arrays in HBM -- one u32 `code` column (epoch*NTT + type,
+// footnote 2 of Sec. 5.1.2; 0 = no task), two u32 argument columns, a u32
+// `link` column (first child slot of a join) and a u64 `result` column (the
+// value an `emit` stores, Sec. 4.3.2).  A warp touching 32 consecutive slots
+// reads or writes one 128-byte line per column.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "trees.h"
+
+namespace trees {
+
+constexpr uint32_t NTT = TREES_NUM_TASK_TYPES;  // NumTaskTypes of footnote 2, Sec. 5.1.2
+constexpr int STK_CAP = 512;                    // epoch-range stack entries per job
+constexpr int LEAF_MAX = 1024;                  // largest leaf a block sorts in shared memory
+constexpr uint32_t MERGE_TILE = 4096;           // outputs of one merge-path tile
+constexpr uint32_t EXPAND_TILE = 4096;          // adjacency entries of one BFS expansion tile
+constexpr unsigned long long CTR_LOW_MASK = (1ull << 40) - 1;  // map counters: (descs << 40) | units
+
+enum MapKind : uint32_t { MAP_LEAF_SORT = 1, MAP_MERGE = 2 };
+
+struct Range {
+    uint32_t cen, lo, hi;  // epoch number and NDRange [lo, hi) (Sec. 5.1.2)
+};
+
+// The job a single-job run executes (copied into the control block per run).
+struct RunParams {
+    int32_t program;
+    uint32_t n, cutoff, leaf;
+    uint32_t *keys, *scratch;
+    const int32_t *row_ptr, *col;
+    int32_t *level;
+    int32_t nv;
+    const int32_t *left, *right;
+    int32_t *visit_epoch;
+};
+
+// Read-only during a run: where everything lives.
+struct Conf {
+    uint32_t *code, *a0, *a1, *link;
+    unsigned long long *result;
+    uint32_t cap;
+    // tiled map list: one descriptor per map operation, `units` tiles each
+    uint32_t *mt_kind, *mt_a, *mt_b, *mt_c, *mt_job, *mt_tilebase, *mt_tiledesc;
+    // element map list (BFS expansion): one descriptor per vertex, one unit per edge
+    uint32_t *me_v, *me_base, *me_job, *me_tfd;
+    uint32_t mcap;
+    trees_epoch_t *trace;
+    uint32_t *trace_valid;
+    uint32_t trace_cap;
+    int32_t trace_on;
+    uint32_t max_epochs;
+    int32_t stall_epoch;
+    unsigned long long timeout_ns;
+    Range *gstack;
+    uint32_t gstack_cap;
+    RunParams rp;
+};
+
+// Mutable control block.  The per-epoch counters are triple-buffered by
+// epoch index: epoch e allocates from slot e%3, block 0 clears slot (e+1)%3
+// during epoch e (its last readers finished before the barrier that opened
+// epoch e), so one grid barrier per epoch is enough.
+struct Ctl {
+    unsigned int bar_count;          // monotonic arrival counter of the grid barrier
+    unsigned int pad0[63];
+    unsigned int cnt[3];             // forks this epoch (nextFreeCore - oldNextFreeCore)
+    unsigned int join[3];            // joinScheduled
+    unsigned long long mt_ctr[3];    // tiled maps: (descriptors << 40) | tiles
+    unsigned long long me_ctr[3];    // element maps: (descriptors << 40) | elements
+    int err;                         // first device-side error (sticky)
+    unsigned int err_epoch;
+    unsigned long long tasks, joins, maps, forks;
+    unsigned long long t_start, t_end;
+    unsigned int epochs, peak, final_next, pad1;
+    // scheduler state for the graph and host-loop schedulers
+    unsigned int g_cen, g_lo, g_hi, g_base, g_e, g_next, g_sp, g_stop;
+};
+
+struct Dev {
+    Ctl ctl;
+    Conf conf;
+};
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ uint32_t task_type(uint32_t code, uint32_t cen) {
+    // active iff code in [cen*NTT + 1, (cen+1)*NTT]  (footnote 2, Sec. 5.1.2)
+    const uint32_t d = code - (cen * NTT + 1u);
+    return d < NTT ? d + 1u : 0u;
+}
+
+__device__ __forceinline__ uint32_t enc(uint32_t epoch, uint32_t type) { return epoch * NTT + type; }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned int *p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ T vload(const T *p) {
+    return *(const volatile T *)p;
+}
+
+__device__ __forceinline__ void set_err(Ctl *ctl, int code, uint32_t epoch) {
+    if (atomicCAS(&ctl->err, 0, code) == 0) ctl->err_epoch = epoch;
+}
+
+// ------------------------------------------------------------------ shared memory
+
+template <int BS>
+struct Smem {
+    static constexpr int NW = BS / 32;
+    unsigned int w32[NW];
+    unsigned int wflag[NW];
+    unsigned long long w64a[NW];
+    unsigned long long w64b[NW];
+    unsigned int flags;
+    unsigned int bc32[4];
+    unsigned long long bc64[4];
+    int bar_ok;
+    // replicated epoch-range stack and scheduler state (persistent scheduler)
+    Range stk[STK_CAP];
+    int sp;
+    uint32_t next, cen, lo, hi, base;
+    int stop;
+    union {
+        uint32_t sortk[LEAF_MAX];
+        struct {
+            uint32_t in[MERGE_TILE];
+            uint32_t out[MERGE_TILE];
+            uint32_t split[2];
+        } mg;
+        struct {
+            uint32_t base[EXPAND_TILE + 2];
+            uint32_t v[EXPAND_TILE + 2];
+        } ex;
+        struct {
+            uint32_t toff[BS];   // tile offset of each tiled map request, by request rank
+            uint32_t di[BS];     // its descriptor index
+        } rq;
+    } u;
+};
+
+// ------------------------------------------------------------------ scans
+
+__device__ __forceinline__ uint32_t warp_incl_u32(uint32_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_incl_u64(unsigned long long x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Exclusive block scan of v; *total gets the block sum, *any the block-wide OR
+// of pred.  Two __syncthreads; the caller must __syncthreads before the next
+// scan reuses the shared words.
+template <int BS>
+__device__ __forceinline__ uint32_t block_scan_u32(uint32_t v, int pred, uint32_t *total, int *any, Smem<BS> &sm) {
+    constexpr int NW = BS / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t inc = warp_incl_u32(v);
+    const unsigned int bal = __ballot_sync(0xffffffffu, pred);
+    if (lane == 31) sm.w32[wid] = inc;
+    if (lane == 0) sm.wflag[wid] = bal != 0u;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < NW ? sm.w32[lane] : 0u;
+        const unsigned int f = __ballot_sync(0xffffffffu, lane < NW ? sm.wflag[lane] : 0u);
+        w = warp_incl_u32(w);
+        if (lane < NW) sm.w32[lane] = w;
+        if (lane == 0) sm.flags = f != 0u;
+    }
+    __syncthreads();
+    *total = sm.w32[NW - 1];
+    *any = (int)sm.flags;
+    return (wid ? sm.w32[wid - 1] : 0u) + inc - v;
+}
+
+// Exclusive block scan of two u64 values at once.
+template <int BS>
+__device__ __forceinline__ void block_scan_u64x2(unsigned long long a, unsigned long long b, unsigned long long *ea,
+                                                 unsigned long long *eb, unsigned long long *ta,
+                                                 unsigned long long *tb, Smem<BS> &sm) {
+    constexpr int NW = BS / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned long long ia = warp_incl_u64(a), ib = warp_incl_u64(b);
+    if (lane == 31) {
+        sm.w64a[wid] = ia;
+        sm.w64b[wid] = ib;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long x = lane < NW ? sm.w64a[lane] : 0ull;
+        unsigned long long y = lane < NW ? sm.w64b[lane] : 0ull;
+        x = warp_incl_u64(x);
+        y = warp_incl_u64(y);
+        if (lane < NW) {
+            sm.w64a[lane] = x;
+            sm.w64b[lane] = y;
+        }
+    }
+    __syncthreads();
+    *ta = sm.w64a[NW - 1];
+    *tb = sm.w64b[NW - 1];
+    *ea = (wid ? sm.w64a[wid - 1] : 0ull) + ia - a;
+    *eb = (wid ? sm.w64b[wid - 1] : 0ull) + ib - b;
+}
+
+// ------------------------------------------------------------------ grid barrier
+
+// One grid-wide barrier (Tenet 1's bulk synchronisation).  Thread 0 of each
+// block adds 1 to a monotonic counter with release semantics and spins with
+// acquire loads until the counter reaches (barrier index) * gridDim.x.  The
+// spin is bounded by timeout_ns of globaltimer: past it the block records
+// TREES_ERR_TIMEOUT and returns false instead of waiting forever.
+template <int BS>
+__device__ __forceinline__ bool grid_sync(Ctl *ctl, uint32_t *bar_idx, unsigned long long timeout_ns, Smem<BS> &sm) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t idx = ++(*bar_idx);
+        const unsigned int target = idx * gridDim.x;
+        fence_acq_rel();
+        red_release_add(&ctl->bar_count, 1u);
+        int ok = 1;
+        uint32_t spins = 0;
+        uint64_t t0 = 0;
+        while ((int)(ld_acquire(&ctl->bar_count) - target) < 0) {
+            if ((++spins & 63u) == 0u) {
+                const uint64_t now = globaltimer();
+                if (t0 == 0) {
+                    t0 = now;
+                } else if (now - t0 > timeout_ns) {
+                    set_err(ctl, TREES_ERR_TIMEOUT, idx);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        fence_acq_rel();
+        // one block-uniform decision: stop on a timeout or on any error raised before the barrier
+        sm.bar_ok = ok && vload(&ctl->err) == 0;
+    }
+    __syncthreads();
+    return sm.bar_ok != 0;
+}
+
+}  // namespace trees
