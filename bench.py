@@ -1,0 +1,451 @@
+#!/usr/bin/env python
+"""Benchmark of the TREES epoch step on B300.
+
+One step = one complete run of the fib(34) task tree (no sequential cutoff)
+through the persistent scheduler: every epoch of the task vector, forks,
+joins and the per-epoch grid barrier, from the root task to the empty stack.
+The JSON line reports tasks/s (valid task executions, joins included) with
+microseconds per epoch, the roofline of the persistent kernel, the clocks seen,
+an end-to-end figure through the C ABI with host-side input/output, and the
+CPU oracle timed on this host.  Secondary workloads (fib(34) with a leaf
+cutoff of 12, mergesort of 2^26 keys, BFS on R-MAT scale 22) and the
+V1/V-infinity fit of T_P = V1*T1/P + Vinf*Tinf ride along in the same line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--quick]
+
+Multi-GPU: the run shards nothing (one task tree per GPU), so N>1 runs N
+independent replicas (weak scaling) with no collective on the data path.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tasks/sec & µs/epoch (fib, sort, BFS); batched jobs/sec, p99 latency vs plain"
+FIB_N = 34
+FLUSH_BYTES = 256 << 20  # > 126 MB L2
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--quick", action="store_true", help="headline only (no secondary workloads / fit)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1608_00571_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel_key)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "20", "-i", str(dev)], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.tmp.flush()
+        with open(self.tmp.name) as f:
+            rows = [r.split(",") for r in f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for i, nm in enumerate(names):
+                if r[5 + i].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ algorithmic bytes
+
+def fib_alg_bytes(stats, trace):
+    """Minimum TV traffic of the fib task tree with the SoA layout (u32 code,
+    u32 arg, u32 link, u64 result): an internal fib task reads code+arg (8 B),
+    writes two children (16 B) and rewrites itself as a join (code+link, 8 B);
+    a leaf reads 8 B and emits (result 8 B + code 4 B); a sum join reads
+    code+link (8 B) and two child results (16 B) and emits (12 B); a dead entry
+    launched in a join epoch is read once (4 B)."""
+    joins = stats["joins"]
+    fib_tasks = stats["tasks"] - joins
+    leaves = fib_tasks - joins
+    dead = sum(t["hi"] - t["lo"] - t["valid"] for t in trace)
+    return 32 * joins + 20 * leaves + 36 * joins + 4 * dead
+
+
+def sort_alg_bytes(n, leaf=1024):
+    """Each key is read and written once per level: the leaf sort plus one
+    merge per level of the split tree."""
+    levels = 0
+    m = n
+    while m > leaf:
+        m = (m + 1) // 2
+        levels += 1
+    return (levels + 1) * 2 * 4 * n
+
+
+def bfs_alg_bytes(row_ptr, level):
+    """Adjacency (4 B) and one level probe (4 B) per scanned edge, plus per
+    reached vertex its row offsets (8 B), level write (4 B), TV entry written
+    and read (16 B), retirement (4 B) and its map descriptor written and read
+    (16 B)."""
+    import numpy as np
+    reached = level >= 0
+    deg = np.diff(row_ptr)
+    edges = int(deg[reached].sum())
+    nreach = int(reached.sum())
+    return 8 * edges + 48 * nreach, edges
+
+
+# ------------------------------------------------------------ runners
+
+def timed_runs(T, torch, ctx, job, steps, warmup, stream, flush=None, setup=None):
+    """Runs `job` warmup+steps times; returns per-step device ms (CUDA events
+    on the launching stream), flushing L2 between steps."""
+    times = []
+    for i in range(warmup + steps):
+        if setup is not None:
+            setup()
+        if flush is not None:
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        T.trees_run(ctx, job, stream)
+        b.record(stream)
+        st = T.trees_sync(ctx)
+        if st != T.TREES_OK:
+            raise RuntimeError(f"run failed with status {st}")
+        b.synchronize()
+        if i >= warmup:
+            times.append(a.elapsed_time(b))
+    return times
+
+
+def vfit(T, torch, stream, sms):
+    """Least-squares fit of T_P = V1*T1/P + Vinf*Tinf over fib n = 16..34,
+    cutoffs {0, 8, 12} and grids of P = SMs/4, SMs/2, SMs (one 1024-thread
+    block per SM used)."""
+    import numpy as np
+    rows, ys = [], []
+    for frac in (4, 2, 1):
+        P = max(1, sms // frac)
+        ctx = T.trees_create(20_000_000, T.trees_default_config(block_size=1024, grid_blocks=P))
+        try:
+            for cutoff in (0, 8, 12):
+                for n in range(16, 35, 2):
+                    if cutoff and n <= cutoff + 2:
+                        continue
+                    job = T.make_job(T.TREES_PROG_FIB, n=n, cutoff=cutoff)
+                    t = min(timed_runs(T, torch, ctx, job, 3, 1, stream))
+                    st = T.trees_stats(ctx)
+                    rows.append([st["tasks"] / P, st["epochs"]])
+                    ys.append(t * 1000.0)  # us
+        finally:
+            T.trees_destroy(ctx)
+    A, y = np.array(rows, dtype=float), np.array(ys)
+    coef, *_ = np.linalg.lstsq(A, y, rcond=None)
+    pred = A @ coef
+    r2 = 1.0 - float(((y - pred) ** 2).sum() / ((y - y.mean()) ** 2).sum())
+    return {"V1_us_per_task_per_SM": float(coef[0]), "Vinf_us_per_epoch": float(coef[1]), "r2": r2,
+            "points": len(ys), "P": "SMs used (1024-thread blocks, one per SM): 37, 74, 148"}
+
+
+def cpu_baseline(seconds):
+    """The oracle's TVM simulator on fib(34), one host core, repeated for about
+    `seconds` seconds."""
+    import oracle
+    t0 = time.perf_counter()
+    runs, tasks = 0, 0
+    while True:
+        r = oracle.tvm_run(oracle.FIB, fib_n=FIB_N)
+        tasks += r["stats"]["tasks"]
+        runs += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": tasks / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+            "sample": f"{runs} full runs of the sequential TVM simulator on fib({FIB_N}) "
+                      f"({tasks} task executions, {dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    times, tasks = [], 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.tvm_run(oracle.FIB, fib_n=FIB_N)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            tasks = r["stats"]["tasks"]
+    total = sum(times)
+    value = args.steps * tasks / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "tasks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64",
+            "data": "synthetic", "config": {"workload": f"fib({FIB_N}) uint64 task tree, no sequential cutoff",
+                                            "n": FIB_N, "cutoff": 0},
+            "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed runs of the sequential TVM simulator on fib({FIB_N})"},
+            "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    import paper_1608_00571_b300 as T
+    from paper_1608_00571_b300 import build as tbuild
+    from paper_1608_00571_b300 import gen
+
+    tbuild.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", init_method="env://")
+    stream = torch.cuda.current_stream()
+    hbm_peak, peak_kind = measured_peaks()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    # ---------------- headline: fib(34), persistent scheduler
+    cfg = T.trees_default_config(block_size=1024)
+    ctx = T.trees_create(20_000_000, cfg)
+    grid, bs, sms = T.trees_geometry(ctx)
+    job = T.make_job(T.TREES_PROG_FIB, n=FIB_N)
+    timed_runs(T, torch, ctx, job, 0, args.warmup, stream, flush)
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    times = timed_runs(T, torch, ctx, job, args.steps, 0, stream, flush)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    stats = T.trees_stats(ctx)
+    result = T.trees_result(ctx, 0)
+    assert result == 5702887, result
+    total_ms = sum(times)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    tasks = stats["tasks"]
+    ms_step = total_ms / args.steps
+    value = world * args.steps * tasks / (total_ms / 1000.0)
+    us_epoch = 1000.0 * ms_step / stats["epochs"]
+    floor_us = T.trees_barrier_floor(ctx, 20000, stream)
+    T.trees_destroy(ctx)
+
+    # per-epoch trace (counts are deterministic) for the algorithmic bytes
+    tctx = T.trees_create(20_000_000, T.trees_default_config(block_size=1024, trace=1))
+    T.trees_run(tctx, job, stream)
+    assert T.trees_sync(tctx) == T.TREES_OK
+    trace = T.trees_trace(tctx)
+    T.trees_destroy(tctx)
+    alg = fib_alg_bytes(stats, trace)
+    achieved = alg / (ms_step / 1000.0) / 1e9
+    traffic = ncu_traffic("fib34_persistent")
+
+    # ---------------- end to end through the C ABI: host input, host result
+    ectx = T.trees_create(20_000_000, cfg)
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        T.trees_fib(ectx, FIB_N, 0, stream)  # the root task travels host->device in the launch
+        st = T.trees_sync(ectx)
+        r = T.trees_result(ectx, 0)          # device->host read of the result
+        dt = time.perf_counter() - t0
+        assert st == T.TREES_OK and r == 5702887
+        if i >= args.warmup:
+            e2e_times.append(dt)
+    T.trees_destroy(ectx)
+    e2e_value = world * args.steps * tasks / sum(e2e_times)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "tasks/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
+        "config": {"workload": f"fib({FIB_N}) uint64 task tree, no sequential cutoff", "n": FIB_N, "cutoff": 0,
+                   "scheduler": "persistent", "block_size": bs, "grid_blocks": grid, "sms": sms,
+                   "l2": "flushed between steps (256 MiB device write)"},
+        "us_per_epoch": us_epoch, "epochs": stats["epochs"], "tasks_per_step": tasks,
+        "barrier_floor_us": floor_us, "epoch_over_floor": us_epoch / floor_us,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)",
+                     "algorithmic_bytes_per_launch": alg, "kernel": "k_persistent<1024>"},
+        "clocks": clk, "wall_s_timed_region": wall,
+        "e2e": {"value": e2e_value, "unit": "tasks/s", "h2d_bytes_per_step": 12, "d2h_bytes_per_step": 8},
+        "gpu_launches": 2 * args.steps,
+    }
+
+    if not args.quick:
+        workloads = {}
+        # fib(34) with a leaf cutoff of 12
+        c2 = T.trees_create(20_000_000, cfg)
+        j2 = T.make_job(T.TREES_PROG_FIB, n=FIB_N, cutoff=12)
+        t2 = timed_runs(T, torch, c2, j2, 10, 2, stream, flush)
+        s2 = T.trees_stats(c2)
+        assert T.trees_result(c2, 0) == 5702887
+        T.trees_destroy(c2)
+        m2 = statistics.mean(t2)
+        workloads["fib34_cutoff12"] = {"ms": m2, "tasks": s2["tasks"], "epochs": s2["epochs"],
+                                       "tasks_per_s": s2["tasks"] / (m2 / 1000), "us_per_epoch": 1000 * m2 / s2["epochs"],
+                                       "bound": "alu (leaves run the naive recursion in-thread)"}
+        # mergesort of 2^26 uint32 keys
+        n = 1 << 26
+        keys = gen.keys_u32(1, n)
+        src = torch.from_numpy(keys.view(np.int32)).cuda()
+        kd = torch.empty_like(src)
+        sc = torch.empty_like(src)
+        c3 = T.trees_create(1 << 18, cfg)
+        j3 = T.make_job(T.TREES_PROG_MERGESORT, n=n, keys=kd, scratch=sc)
+        t3 = timed_runs(T, torch, c3, j3, 5, 1, stream, None, setup=lambda: kd.copy_(src))
+        s3 = T.trees_stats(c3)
+        T.trees_destroy(c3)
+        ok3 = bool(np.array_equal(kd.cpu().numpy().view(np.uint32), np.sort(keys)))
+        m3 = statistics.mean(t3)
+        ab3 = sort_alg_bytes(n)
+        workloads["mergesort_2^26"] = {"ms": m3, "tasks": s3["tasks"], "epochs": s3["epochs"],
+                                       "tasks_per_s": s3["tasks"] / (m3 / 1000), "us_per_epoch": 1000 * m3 / s3["epochs"],
+                                       "keys_per_s": n / (m3 / 1000), "sorted_equal_numpy": ok3,
+                                       "roofline": {"bound": "hbm", "achieved": ab3 / (m3 / 1000) / 1e9,
+                                                    "peak": hbm_peak, "unit": "GB/s",
+                                                    "frac": ab3 / (m3 / 1000) / 1e9 / hbm_peak,
+                                                    "algorithmic_bytes": ab3}}
+        del src, kd, sc
+        # BFS on R-MAT scale 22
+        row_ptr, col, info = gen.rmat(22, 16, seed=2)
+        rp = torch.from_numpy(row_ptr).cuda()
+        cl = torch.from_numpy(col).cuda()
+        lv = torch.empty(row_ptr.size - 1, dtype=torch.int32, device="cuda")
+        c4 = T.trees_create(1 << 23, cfg)
+        j4 = T.make_job(T.TREES_PROG_BFS, n=0, row_ptr=rp, col=cl, level=lv, nv=row_ptr.size - 1)
+        t4 = timed_runs(T, torch, c4, j4, 5, 1, stream, flush)
+        s4 = T.trees_stats(c4)
+        T.trees_destroy(c4)
+        import oracle
+        level = lv.cpu().numpy()
+        ok4 = bool(np.array_equal(level, oracle.bfs(row_ptr, col, 0)[0]))
+        m4 = statistics.mean(t4)
+        ab4, edges = bfs_alg_bytes(row_ptr, level)
+        workloads["bfs_rmat22"] = {"ms": m4, "tasks": s4["tasks"], "epochs": s4["epochs"],
+                                   "tasks_per_s": s4["tasks"] / (m4 / 1000), "us_per_epoch": 1000 * m4 / s4["epochs"],
+                                   "edges_scanned": edges, "teps": edges / (m4 / 1000), "levels_equal_oracle": ok4,
+                                   "graph": {k: info[k] for k in ("nv", "m", "generated")},
+                                   "roofline": {"bound": "hbm", "achieved": ab4 / (m4 / 1000) / 1e9, "peak": hbm_peak,
+                                                "unit": "GB/s", "frac": ab4 / (m4 / 1000) / 1e9 / hbm_peak,
+                                                "algorithmic_bytes": ab4}}
+        del rp, cl, lv
+        line["workloads"] = workloads
+        # graph-relaunch and host-loop schedulers on the headline workload
+        sch = {}
+        for name, sid in (("graph", T.TREES_SCHED_GRAPH), ("hostloop", T.TREES_SCHED_HOSTLOOP)):
+            cx = T.trees_create(20_000_000, T.trees_default_config(block_size=1024, scheduler=sid))
+            tt = timed_runs(T, torch, cx, job, 5, 1, stream, flush)
+            T.trees_destroy(cx)
+            mm = statistics.mean(tt)
+            sch[name] = {"ms": mm, "us_per_epoch": 1000 * mm / stats["epochs"], "tasks_per_s": tasks / (mm / 1000)}
+        sch["persistent"] = {"ms": ms_step, "us_per_epoch": us_epoch, "tasks_per_s": tasks / (ms_step / 1000)}
+        line["schedulers"] = sch
+        line["vfit"] = vfit(T, torch, stream, sms)
+
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

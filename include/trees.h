@@ -81,7 +81,7 @@ typedef struct {
     uint64_t map_capacity;   /* map descriptors and map tiles per epoch; 0 = task-vector capacity */
     int32_t inject_stall_epoch; /* test hook, -1 = off: in that epoch the last block leaves
                                    without arriving at the barrier, so the others time out */
-    int32_t reserved;
+    int32_t grid_blocks;     /* persistent grid size; 0 = SMs * blocks_per_sm (capped at co-residency) */
 } trees_config_t;
 
 /* Fills *cfg with the defaults above. */

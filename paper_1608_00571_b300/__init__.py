@@ -52,7 +52,7 @@ class trees_config_t(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("scheduler", ctypes.c_int32),
                 ("trace", ctypes.c_int32), ("max_epochs", ctypes.c_uint32), ("trace_cap", ctypes.c_uint32),
                 ("timeout_ns", ctypes.c_uint64), ("map_capacity", ctypes.c_uint64),
-                ("inject_stall_epoch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("inject_stall_epoch", ctypes.c_int32), ("grid_blocks", ctypes.c_int32)]
 
 
 class trees_job_t(ctypes.Structure):

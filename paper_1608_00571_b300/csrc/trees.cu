@@ -478,6 +478,7 @@ static int finish_create(trees_ctx *x) {
         return TREES_ERR_CUDA;
     int per_sm = x->cfg.blocks_per_sm > 0 ? std::min(x->cfg.blocks_per_sm, occ) : occ;
     x->grid = x->sms * per_sm;
+    if (x->cfg.grid_blocks > 0) x->grid = std::min(x->cfg.grid_blocks, x->sms * occ);
     char *m = x->mem;
     const Layout &L = x->L;
     x->ctl = reinterpret_cast<Ctl *>(m + L.off_dev);
@@ -515,7 +516,7 @@ static int validate_cfg(const trees_config_t *cfg, trees_config_t *out) {
     normalize(out);
     if (out->block_size != 256 && out->block_size != 512 && out->block_size != 1024) return TREES_ERR_INVALID_ARG;
     if (out->scheduler < TREES_SCHED_PERSISTENT || out->scheduler > TREES_SCHED_HOSTLOOP) return TREES_ERR_INVALID_ARG;
-    if (out->blocks_per_sm < 0) return TREES_ERR_INVALID_ARG;
+    if (out->blocks_per_sm < 0 || out->grid_blocks < 0) return TREES_ERR_INVALID_ARG;
     return TREES_OK;
 }
 
