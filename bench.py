@@ -42,7 +42,53 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="headline only (no secondary workloads / fit)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
+    ap.add_argument("--profile-case", default=None,
+                    help="PROGRAM:SIZE[:BLOCK] -- run one small case twice and exit (for ncu): "
+                         "fib:N, sort:LOG2KEYS, bfs:RMAT_SCALE")
     return ap.parse_args()
+
+
+def profile_case(spec):
+    """One small workload run twice (a warm-up and the captured launch)."""
+    import numpy as np
+    import torch
+    import paper_1608_00571_b300 as T
+    from paper_1608_00571_b300 import gen
+    parts = spec.split(":")
+    prog, size = parts[0], int(parts[1])
+    bs = int(parts[2]) if len(parts) > 2 else 1024
+    torch.cuda.set_device(0)
+    s = torch.cuda.current_stream()
+    keep = []
+    if prog == "fib":
+        a, b = 0, 1
+        for _ in range(size + 1):
+            a, b = b, a + b
+        ctx = T.trees_create(2 * a + 1024, T.trees_default_config(block_size=bs, map_capacity=1))
+        job = T.make_job(T.TREES_PROG_FIB, n=size)
+    elif prog == "sort":
+        n = 1 << size
+        kd = torch.from_numpy(gen.keys_u32(1, n).view(np.int32)).cuda()
+        sc = torch.empty_like(kd)
+        keep += [kd, sc]
+        ctx = T.trees_create(max(4 * n // 1024, 1024), T.trees_default_config(block_size=bs))
+        job = T.make_job(T.TREES_PROG_MERGESORT, n=n, keys=kd, scratch=sc)
+    elif prog == "bfs":
+        row_ptr, col, _ = gen.rmat(size, 16, seed=2)
+        rp, cl = torch.from_numpy(row_ptr).cuda(), torch.from_numpy(col).cuda()
+        lv = torch.empty(row_ptr.size - 1, dtype=torch.int32, device="cuda")
+        keep += [rp, cl, lv]
+        ctx = T.trees_create(row_ptr.size + 1024, T.trees_default_config(block_size=bs))
+        job = T.make_job(T.TREES_PROG_BFS, n=0, row_ptr=rp, col=cl, level=lv, nv=row_ptr.size - 1)
+    else:
+        raise SystemExit(f"unknown profile case {spec}")
+    for _ in range(2):
+        T.trees_run(ctx, job, s)
+        st = T.trees_sync(ctx)
+        if st != T.TREES_OK:
+            raise SystemExit(f"status {st}")
+    print(prog, size, T.trees_stats(ctx))
+    T.trees_destroy(ctx)
 
 
 def dist_env():
@@ -272,6 +318,9 @@ def run_reference(args, rank, world):
 def main():
     args = parse_args()
     rank, world, local = dist_env()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
