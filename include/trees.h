@@ -193,6 +193,32 @@ int trees_bfs(trees_ctx *ctx, const int32_t *dev_row_ptr, const int32_t *dev_col
  * device time per barrier in microseconds. */
 int trees_barrier_floor(trees_ctx *ctx, uint32_t iters, void *stream, double *us_per_barrier);
 
+/* ------------------------------------------------------------ allocation-free entry point
+ * The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory when they run a job: code recorded into a CUDA
+ * stream capture that must not allocate, hosts whose GPU memory budget is
+ * fixed at start-up, and plug-ins whose host application owns the allocator.
+ *
+ * trees_fib_noalloc runs fib(n) (leaf when n < 2 or n <= cutoff) with the
+ * persistent scheduler, with its task vector, control block and statistics
+ * in one static device array of 26 MiB that is part of the library (every GPU
+ * that loads libtrees holds it until the process exits).  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *  - Limit: 1,048,576 task-vector slots, i.e. trees of at most that many
+ *    tasks at their peak (fib(n) needs 2F(n+1)-1: n <= 28 without cutoff).
+ *    Larger jobs return TREES_ERR_CAPACITY before anything is launched.
+ *  - Outputs: *dev_result (device uint64) receives fib(n); *dev_status
+ *    (device int32) receives TREES_OK or the run's device-side error.  Both
+ *    are written asynchronously on `stream`.
+ *  - The first call on a device looks up the array's device address and the
+ *    launch geometry for that device (the device must be current); make that
+ *    first call before any stream capture.
+ *  - All calls share the array and it keeps the previous call's contents (the
+ *    control block is cleared at each call).  Calls whose GPU work overlaps
+ *    race on it: order them on one stream or with events.
+ * Errors: INVALID_ARG (null output, n > 93, cutoff > 30), CAPACITY, CUDA. */
+int trees_fib_noalloc(uint32_t n, uint32_t cutoff, uint64_t *dev_result, int32_t *dev_status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -105,6 +105,7 @@ _SIGNATURES = [
     ("trees_mergesort_u32", ctypes.c_int, [_ctxp, _vp, _vp, ctypes.c_uint32, _vp]),
     ("trees_bfs", ctypes.c_int, [_ctxp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
     ("trees_barrier_floor", ctypes.c_int, [_ctxp, ctypes.c_uint32, _vp, ctypes.POINTER(ctypes.c_double)]),
+    ("trees_fib_noalloc", ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, _vp, _vp, _vp]),
 ]
 
 
@@ -255,6 +256,14 @@ def trees_barrier_floor(ctx, iters: int = 1000, stream=None) -> float:
     us = ctypes.c_double()
     _check("trees_barrier_floor", lib().trees_barrier_floor(ctx, iters, _stream(stream), ctypes.byref(us)))
     return float(us.value)
+
+
+def trees_fib_noalloc(n: int, cutoff: int, dev_result, dev_status, stream=None) -> int:
+    """fib(n) without any device allocation (static 26 MiB task vector inside
+    the library, at most 2^20 slots); results land in the caller's device
+    buffers ``dev_result`` (uint64) and ``dev_status`` (int32).  Returns the
+    host-side status; raises only through the caller's own checks."""
+    return int(lib().trees_fib_noalloc(n, cutoff, _ptr(dev_result), _ptr(dev_status), _stream(stream)))
 
 
 def exported_symbols():

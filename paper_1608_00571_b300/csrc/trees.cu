@@ -1000,3 +1000,120 @@ int trees_barrier_floor(trees_ctx *x, uint32_t iters, void *stream, double *us) 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free fib entry point
+//
+// Some callers cannot allocate device memory at call time: code running
+// under a CUDA stream capture that must not allocate, real-time or embedded
+// hosts whose memory budget is fixed at start-up, and plugins whose host
+// application owns the allocator.  trees_fib_noalloc serves them: it runs the
+// persistent epoch kernel with its task vector, control block and statistics
+// carved out of one file-scope device array below, so it never calls
+// cudaMalloc, cudaFree or any allocating routine.  The array (NOALLOC_BYTES)
+// is part of the library image: every GPU that loads libtrees keeps it until
+// the process exits.  All calls share it and it keeps the previous call's
+// contents; the control block and statistics are cleared at the start of
+// each call.  Two calls whose work overlaps on the GPU race on the array, so
+// a caller must order them (one stream, or a stream/event dependency).
+
+namespace {
+
+constexpr size_t NOALLOC_CAP = 1u << 20;        // task-vector slots: fib(n) needs 2F(n+1)-1
+constexpr size_t NOALLOC_BYTES = 26u << 20;     // 26 MiB: TV columns (24 MiB) + control block, lists, stats
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+struct NoallocDevice {
+    bool ready = false;
+    char *base = nullptr;  // device address of g_noalloc_scratch on this device
+    int grid = 0, sms = 0;
+};
+NoallocDevice g_noalloc_dev[64];
+
+// Once per device, with that device current: find the device address of the
+// static array (host code only sees a host-side stand-in for the symbol) and
+// the cooperative grid size.
+int noalloc_setup(int dev, NoallocDevice *d) {
+    if (d->ready) return TREES_OK;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        return TREES_ERR_CUDA;
+    }
+    int sms = 0, occ = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TREES_ERR_CUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k_persistent<1024>, 1024, 0) !=
+            cudaSuccess || occ < 1)
+        return TREES_ERR_CUDA;
+    if (make_layout(NOALLOC_CAP, 1, 1, STK_CAP).total > NOALLOC_BYTES) return TREES_ERR_CUDA;
+    d->base = static_cast<char *>(p);
+    d->sms = sms;
+    d->grid = sms * occ;
+    d->ready = true;
+    return TREES_OK;
+}
+
+}  // namespace
+
+extern "C" int trees_fib_noalloc(uint32_t n, uint32_t cutoff, uint64_t *dev_result, int32_t *dev_status,
+                                 void *stream) {
+    if (!dev_result || !dev_status || n > 93 || cutoff > 30) return TREES_ERR_INVALID_ARG;
+    // slots the task tree needs at its peak: every node of the tree, where a
+    // node of size k is a leaf when k < 2 or k <= cutoff (saturating count)
+    uint64_t nk2 = 1, nk1 = 1, need = 1;
+    for (uint32_t k = 0; k <= n; ++k) {
+        need = (k < 2 || k <= cutoff) ? 1 : std::min<uint64_t>(1 + nk1 + nk2, NOALLOC_CAP + 1);
+        nk2 = nk1;
+        nk1 = need;
+    }
+    if (need > NOALLOC_CAP) return TREES_ERR_CAPACITY;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TREES_ERR_CUDA;
+    NoallocDevice *d = &g_noalloc_dev[dev];
+    const int rc = noalloc_setup(dev, d);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Layout L = make_layout(NOALLOC_CAP, 1, 1, STK_CAP);
+    char *m0 = d->base;
+    Ctl *ctl = reinterpret_cast<Ctl *>(m0 + L.off_dev);
+    Conf c;
+    std::memset(&c, 0, sizeof(c));
+    c.code = reinterpret_cast<uint32_t *>(m0 + L.off_code);
+    c.a0 = reinterpret_cast<uint32_t *>(m0 + L.off_a0);
+    c.a1 = reinterpret_cast<uint32_t *>(m0 + L.off_a1);
+    c.link = reinterpret_cast<uint32_t *>(m0 + L.off_link);
+    c.result = reinterpret_cast<unsigned long long *>(m0 + L.off_result);
+    c.cap = (uint32_t)NOALLOC_CAP;
+    uint32_t **mt[7] = {&c.mt_kind, &c.mt_a, &c.mt_b, &c.mt_c, &c.mt_job, &c.mt_tilebase, &c.mt_tiledesc};
+    for (int i = 0; i < 7; ++i) *mt[i] = reinterpret_cast<uint32_t *>(m0 + L.off_mt[i]);
+    uint32_t **me[4] = {&c.me_v, &c.me_base, &c.me_job, &c.me_tfd};
+    for (int i = 0; i < 4; ++i) *me[i] = reinterpret_cast<uint32_t *>(m0 + L.off_me[i]);
+    c.mcap = 1;
+    c.trace = reinterpret_cast<trees_epoch_t *>(m0 + L.off_trace);
+    c.trace_valid = reinterpret_cast<uint32_t *>(m0 + L.off_tvalid);
+    c.trace_cap = 1;
+    c.trace_on = 0;
+    c.max_epochs = 1u << 20;
+    c.stall_epoch = -1;
+    c.timeout_ns = 2000000000ull;
+    c.gstack = reinterpret_cast<Range *>(m0 + L.off_gstack);
+    c.gstack_cap = STK_CAP;
+    c.rp.program = TREES_PROG_FIB;
+    c.rp.n = n;
+    c.rp.cutoff = cutoff;
+    c.rp.leaf = LEAF_MAX;
+    unsigned long long *blk = reinterpret_cast<unsigned long long *>(m0 + L.off_blk);
+    if (cudaMemsetAsync(blk, 0, (size_t)NBLK_STATS * 4 * 8, st) != cudaSuccess) return TREES_ERR_CUDA;
+    k_setup<<<1, 256, 0, st>>>(ctl, c, TREES_TASK_FIB, n, 0u);
+    if (cudaGetLastError() != cudaSuccess) return TREES_ERR_CUDA;
+    void *args[] = {&ctl, &c, &blk};
+    if (cudaLaunchCooperativeKernel((const void *)k_persistent<1024>, dim3(d->grid), dim3(1024), args, 0, st) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return TREES_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(dev_result, c.result, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dev_status, &ctl->err, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return TREES_ERR_CUDA;
+    return TREES_OK;
+}
