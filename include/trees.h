@@ -193,6 +193,79 @@ int trees_bfs(trees_ctx *ctx, const int32_t *dev_row_ptr, const int32_t *dev_col
  * device time per barrier in microseconds. */
 int trees_barrier_floor(trees_ctx *ctx, uint32_t iters, void *stream, double *us_per_barrier);
 
+/* ------------------------------------------------------------ batches and serving
+ * Many independent task trees share one persistent launch (work-together
+ * Tenet 1, Sec. 3, applied across jobs): each job owns a segment of the task
+ * vector and its own epoch state; a global step runs the current epoch of
+ * every live job.  Batched jobs may be fib, N-Queens, mergesort (caller
+ * scratch required) or a traversal; BFS runs only through trees_run. */
+typedef struct {
+    uint64_t id;            /* job index (batch) or submission id (server) */
+    uint64_t result;        /* the root's emitted value (fib, N-Queens); 0 otherwise */
+    uint64_t tasks;         /* valid task executions of this job */
+    uint64_t joins;
+    uint64_t maps;
+    uint64_t ns;            /* device time from admission to completion */
+    uint32_t epochs;        /* this job's epochs */
+    uint32_t peak_slots;    /* highest slot used in its segment, + 1 */
+    int32_t status;         /* TREES_OK or the job's own error (CAPACITY when its segment was too small) */
+    int32_t pad;
+} trees_job_result_t;
+
+/* Task-vector slots a job needs at its peak.  *exact (may be NULL) is set to
+ * 1 when the count is exact (fib, mergesort, traversal upper bound, BFS) and
+ * 0 when it is an estimate (N-Queens: the backtracking tree is not known
+ * before it is explored; a job that outgrows it ends with CAPACITY). */
+uint64_t trees_job_slots(const trees_job_t *job, int32_t *exact);
+
+/* Runs njobs jobs in one persistent launch on the context's task vector.
+ * seg_slots[i] (host array; NULL = trees_job_slots) reserves each job's
+ * segment; their sum must fit the context (else ADMISSION).  Asynchronous on
+ * `stream`.  Errors before launch: INVALID_ARG (a job that cannot be batched),
+ * ADMISSION, CUDA. */
+int trees_batch_run(trees_ctx *ctx, const trees_job_t *jobs, const uint64_t *seg_slots, int32_t njobs, void *stream);
+
+/* Waits for the batch and copies one record per job into out[0..njobs)
+ * (host memory), in job order; *steps (may be NULL) receives the number of
+ * global steps.  Returns the batch-wide status (TIMEOUT, CUDA) or TREES_OK;
+ * per-job errors are in out[i].status. */
+int trees_batch_results(trees_ctx *ctx, trees_job_result_t *out, int32_t njobs, uint32_t *steps);
+
+typedef struct trees_server trees_server;
+
+/* A continuous-batching server on the current device: a task-vector pool of
+ * pool_slots slots, up to max_jobs jobs resident at once, and launches of at
+ * most steps_per_launch global steps.  Job state stays on the device between
+ * launches; jobs that arrive while others run are admitted at the next
+ * launch when a table entry and a segment of their size are free (first
+ * fit, in arrival order). */
+int trees_server_create(size_t pool_slots, int32_t max_jobs, int32_t steps_per_launch, const trees_config_t *cfg,
+                        trees_server **out);
+void trees_server_destroy(trees_server *srv);
+
+/* Queues a job (host call, no device work).  seg_slots = 0 uses
+ * trees_job_slots.  ADMISSION if the job can never fit the pool. */
+int trees_server_submit(trees_server *srv, const trees_job_t *job, uint64_t seg_slots, uint64_t *id);
+
+/* Admits queued jobs, runs one launch and collects the jobs that finished.
+ * Synchronous (returns when the launch is over). */
+int trees_server_step(trees_server *srv, void *stream);
+
+/* Moves up to cap finished jobs into out (host); *n receives how many. */
+int trees_server_poll(trees_server *srv, trees_job_result_t *out, int32_t cap, int32_t *n);
+
+/* Jobs waiting for admission, jobs resident on the device, launches so far. */
+int trees_server_stats(trees_server *srv, int32_t *queued, int32_t *running, uint64_t *launches);
+
+/* Replays a trace in real time: job i arrives arrival_s[i] seconds after the
+ * start (non-decreasing).  plain = 0 serves through the continuous batch;
+ * plain = 1 runs one job per launch in arrival order (trees_run).  Writes each
+ * job's latency (completion - arrival, seconds) and record.  seg_slots may be
+ * NULL.  Returns TREES_OK or the first launch-level error. */
+int trees_server_replay(trees_server *srv, const trees_job_t *jobs, const uint64_t *seg_slots,
+                        const double *arrival_s, int32_t n, int32_t plain, double *latency_s,
+                        trees_job_result_t *results, void *stream);
+
 /* ------------------------------------------------------------ allocation-free entry point
  * The paper has no counterpart to this call; it exists for callers that may
  * not allocate device memory when they run a job: code recorded into a CUDA

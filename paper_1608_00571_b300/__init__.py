@@ -79,6 +79,16 @@ class trees_epoch_t(ctypes.Structure):
                 ("maps", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("t_ns", ctypes.c_uint64)]
 
 
+class trees_job_result_t(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("result", ctypes.c_uint64), ("tasks", ctypes.c_uint64),
+                ("joins", ctypes.c_uint64), ("maps", ctypes.c_uint64), ("ns", ctypes.c_uint64),
+                ("epochs", ctypes.c_uint32), ("peak_slots", ctypes.c_uint32), ("status", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "pad"}
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _ctxp = ctypes.c_void_p
@@ -106,6 +116,25 @@ _SIGNATURES = [
     ("trees_bfs", ctypes.c_int, [_ctxp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
     ("trees_barrier_floor", ctypes.c_int, [_ctxp, ctypes.c_uint32, _vp, ctypes.POINTER(ctypes.c_double)]),
     ("trees_fib_noalloc", ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, _vp, _vp, _vp]),
+    ("trees_job_slots", ctypes.c_uint64, [ctypes.POINTER(trees_job_t), ctypes.POINTER(ctypes.c_int32)]),
+    ("trees_batch_run", ctypes.c_int, [_ctxp, ctypes.POINTER(trees_job_t), ctypes.POINTER(ctypes.c_uint64),
+                                       ctypes.c_int32, _vp]),
+    ("trees_batch_results", ctypes.c_int, [_ctxp, ctypes.POINTER(trees_job_result_t), ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_uint32)]),
+    ("trees_server_create", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.POINTER(trees_config_t), ctypes.POINTER(_vp)]),
+    ("trees_server_destroy", None, [_vp]),
+    ("trees_server_submit", ctypes.c_int, [_vp, ctypes.POINTER(trees_job_t), ctypes.c_uint64,
+                                           ctypes.POINTER(ctypes.c_uint64)]),
+    ("trees_server_step", ctypes.c_int, [_vp, _vp]),
+    ("trees_server_poll", ctypes.c_int, [_vp, ctypes.POINTER(trees_job_result_t), ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_int32)]),
+    ("trees_server_stats", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    ("trees_server_replay", ctypes.c_int, [_vp, ctypes.POINTER(trees_job_t), ctypes.POINTER(ctypes.c_uint64),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(trees_job_result_t),
+                                           _vp]),
 ]
 
 
@@ -264,6 +293,91 @@ def trees_fib_noalloc(n: int, cutoff: int, dev_result, dev_status, stream=None) 
     buffers ``dev_result`` (uint64) and ``dev_status`` (int32).  Returns the
     host-side status; raises only through the caller's own checks."""
     return int(lib().trees_fib_noalloc(n, cutoff, _ptr(dev_result), _ptr(dev_status), _stream(stream)))
+
+
+def trees_job_slots(job: trees_job_t):
+    """``(slots, exact)``: peak task-vector need of a job."""
+    ex = ctypes.c_int32()
+    v = lib().trees_job_slots(ctypes.byref(job), ctypes.byref(ex))
+    return int(v), bool(ex.value)
+
+
+def _job_array(jobs):
+    arr = (trees_job_t * len(jobs))()
+    for i, j in enumerate(jobs):
+        arr[i] = j
+    return arr
+
+
+def _u64_array(vals):
+    if vals is None:
+        return None
+    arr = (ctypes.c_uint64 * len(vals))()
+    for i, v in enumerate(vals):
+        arr[i] = int(v)
+    return arr
+
+
+def trees_batch_run(ctx, jobs, seg_slots=None, stream=None) -> int:
+    arr = _job_array(jobs)
+    segs = _u64_array(seg_slots)
+    return _check("trees_batch_run", lib().trees_batch_run(ctx, arr, segs, len(jobs), _stream(stream)))
+
+
+def trees_batch_results(ctx, njobs: int):
+    """``(status, [per-job dict], steps)``."""
+    out = (trees_job_result_t * njobs)()
+    steps = ctypes.c_uint32()
+    rc = lib().trees_batch_results(ctx, out, njobs, ctypes.byref(steps))
+    if rc in (TREES_ERR_INVALID_ARG, TREES_ERR_CUDA):
+        raise TreesError("trees_batch_results", rc)
+    return rc, [out[i].as_dict() for i in range(njobs)], int(steps.value)
+
+
+def trees_server_create(pool_slots: int, max_jobs: int, steps_per_launch: int, cfg: trees_config_t | None = None):
+    h = _vp()
+    _check("trees_server_create", lib().trees_server_create(pool_slots, max_jobs, steps_per_launch,
+                                                            ctypes.byref(cfg) if cfg else None, ctypes.byref(h)))
+    return h
+
+
+def trees_server_destroy(srv) -> None:
+    lib().trees_server_destroy(srv)
+
+
+def trees_server_submit(srv, job: trees_job_t, seg_slots: int = 0) -> int:
+    i = ctypes.c_uint64()
+    _check("trees_server_submit", lib().trees_server_submit(srv, ctypes.byref(job), seg_slots, ctypes.byref(i)))
+    return int(i.value)
+
+
+def trees_server_step(srv, stream=None) -> int:
+    return _check("trees_server_step", lib().trees_server_step(srv, _stream(stream)))
+
+
+def trees_server_poll(srv, cap: int = 4096):
+    out = (trees_job_result_t * cap)()
+    n = ctypes.c_int32()
+    _check("trees_server_poll", lib().trees_server_poll(srv, out, cap, ctypes.byref(n)))
+    return [out[i].as_dict() for i in range(n.value)]
+
+
+def trees_server_stats(srv):
+    q, r, L = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_uint64()
+    _check("trees_server_stats", lib().trees_server_stats(srv, ctypes.byref(q), ctypes.byref(r), ctypes.byref(L)))
+    return int(q.value), int(r.value), int(L.value)
+
+
+def trees_server_replay(srv, jobs, arrival_s, seg_slots=None, plain: bool = False, stream=None):
+    """``(latency seconds list, [per-job dict])`` of a real-time replay."""
+    n = len(jobs)
+    arr = _job_array(jobs)
+    arrivals = (ctypes.c_double * n)(*[float(a) for a in arrival_s])
+    lat = (ctypes.c_double * n)()
+    res = (trees_job_result_t * n)()
+    _check("trees_server_replay", lib().trees_server_replay(srv, arr, _u64_array(seg_slots), arrivals, n,
+                                                            1 if plain else 0, lat, res, _stream(stream)))
+    return [float(lat[i]) for i in range(n)], [res[i].as_dict() for i in range(n)]
 
 
 def exported_symbols():

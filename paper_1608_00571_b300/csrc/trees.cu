@@ -24,6 +24,12 @@
 #include "trees.h"
 #include "trees_dev.cuh"
 #include "trees_programs.cuh"
+#include "trees_batch.cuh"
+
+#include <chrono>
+#include <deque>
+#include <map>
+#include <thread>
 
 using namespace trees;
 
@@ -435,6 +441,13 @@ struct trees_ctx {
     int last_sched = TREES_SCHED_PERSISTENT;
     int host_status = TREES_OK;
     Ctl *pinned_ctl = nullptr;
+    // batched runs
+    Job *d_jobs = nullptr;
+    uint32_t *d_joff = nullptr;
+    BatchDone *d_done = nullptr;
+    BatchCtl *d_bc = nullptr;
+    Job *h_jobs = nullptr;
+    int32_t batch_cap = 0, batch_n = 0;
 };
 
 extern "C" {
@@ -596,6 +609,11 @@ void trees_destroy(trees_ctx *x) {
     if (x->graph) cudaGraphDestroy(x->graph);
     if (x->own_scratch) cudaFree(x->own_scratch);
     if (x->pinned_ctl) cudaFreeHost(x->pinned_ctl);
+    if (x->d_jobs) cudaFree(x->d_jobs);
+    if (x->d_joff) cudaFree(x->d_joff);
+    if (x->d_done) cudaFree(x->d_done);
+    if (x->d_bc) cudaFree(x->d_bc);
+    if (x->h_jobs) cudaFreeHost(x->h_jobs);
     if (x->owns && x->mem) cudaFree(x->mem);
     delete x;
 }
@@ -1115,5 +1133,521 @@ extern "C" int trees_fib_noalloc(uint32_t n, uint32_t cutoff, uint64_t *dev_resu
     if (cudaMemcpyAsync(dev_result, c.result, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(dev_status, &ctl->err, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return TREES_ERR_CUDA;
+    return TREES_OK;
+}
+
+// ------------------------------------------------------------------ batches and serving (host)
+
+namespace {
+
+// Peak task-vector need of one job (see trees_job_slots).
+uint64_t job_slots(const trees_job_t *j, int32_t *exact) {
+    int32_t ex = 1;
+    uint64_t need = 1;
+    switch (j->program) {
+    case TREES_PROG_FIB: {  // every node of the fib tree is resident at the peak
+        uint64_t nk2 = 1, nk1 = 1;
+        for (uint32_t k = 0; k <= j->n; ++k) {
+            need = (k < 2 || k <= j->cutoff) ? 1 : std::min<uint64_t>(1 + nk1 + nk2, 1ull << 40);
+            nk2 = nk1;
+            nk1 = need;
+        }
+        break;
+    }
+    case TREES_PROG_MERGESORT: {  // every split node of the tree
+        const uint64_t leaf = j->leaf ? j->leaf : LEAF_MAX;
+        std::map<uint64_t, uint64_t> memo;
+        struct F {
+            static uint64_t go(uint64_t m, uint64_t leaf, std::map<uint64_t, uint64_t> &memo) {
+                if (m <= leaf) return 1;
+                auto it = memo.find(m);
+                if (it != memo.end()) return it->second;
+                const uint64_t h = m / 2, r = 1 + go(h, leaf, memo) + go(m - h, leaf, memo);
+                memo[m] = r;
+                return r;
+            }
+        };
+        need = F::go(j->n, leaf, memo);
+        break;
+    }
+    case TREES_PROG_NQUEENS: {  // estimate 4 * 3^(n-1); a job that outgrows it ends with CAPACITY
+        ex = 0;
+        need = 4;
+        for (uint32_t k = 1; k < j->n && need < (1ull << 40); ++k) need *= 3;
+        break;
+    }
+    case TREES_PROG_POSTORDER:
+    case TREES_PROG_PREORDER:
+        need = 2ull * j->n + 1;  // every node and every nil child
+        break;
+    case TREES_PROG_BFS:
+        need = (uint64_t)std::max(j->nv, 1);
+        break;
+    default:
+        need = 0;
+        ex = 0;
+    }
+    if (exact) *exact = ex;
+    return need;
+}
+
+// Validates a job for batched execution and fills its table record.
+int make_job_record(const trees_job_t *j, uint32_t seg_base, uint32_t seg_cap, uint64_t id, Job *r) {
+    std::memset(r, 0, sizeof(Job));
+    RunParams &rp = r->rp;
+    rp.program = j->program;
+    rp.n = j->n;
+    rp.cutoff = j->cutoff;
+    rp.leaf = j->leaf ? j->leaf : LEAF_MAX;
+    switch (j->program) {
+    case TREES_PROG_FIB:
+        if (j->n > 93 || j->cutoff > 30) return TREES_ERR_INVALID_ARG;
+        r->type0 = TREES_TASK_FIB;
+        r->a00 = j->n;
+        break;
+    case TREES_PROG_NQUEENS:
+        if (j->n < 1 || j->n > 16) return TREES_ERR_INVALID_ARG;
+        r->type0 = TREES_TASK_NQ_ROW;
+        break;
+    case TREES_PROG_MERGESORT:
+        if (rp.leaf > (uint32_t)LEAF_MAX || (j->n && (!j->keys || !j->scratch))) return TREES_ERR_INVALID_ARG;
+        rp.keys = j->keys;
+        rp.scratch = j->scratch;
+        r->type0 = TREES_TASK_MS_SPLIT;
+        r->a10 = j->n;
+        break;
+    case TREES_PROG_POSTORDER:
+    case TREES_PROG_PREORDER:
+        if (j->n && (!j->left || !j->right || !j->visit_epoch)) return TREES_ERR_INVALID_ARG;
+        rp.left = j->left;
+        rp.right = j->right;
+        rp.visit_epoch = j->visit_epoch;
+        r->type0 = j->program == TREES_PROG_POSTORDER ? TREES_TASK_PO : TREES_TASK_PRE;
+        r->a00 = j->n ? 0u : 0xFFFFFFFFu;
+        break;
+    default:
+        return TREES_ERR_INVALID_ARG;  // BFS runs through trees_run only
+    }
+    r->seg_base = seg_base;
+    r->seg_cap = seg_cap;
+    r->state = JOB_NEW;
+    r->id = id;
+    return TREES_OK;
+}
+
+template <int BS>
+const void *batch_kernel() {
+    return (const void *)k_batch<BS>;
+}
+
+const void *batch_kernel_for(int bs) {
+    switch (bs) {
+    case 256: return batch_kernel<256>();
+    case 512: return batch_kernel<512>();
+    default: return batch_kernel<1024>();
+    }
+}
+
+int batch_grid(trees_ctx *x, const void *kern) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, x->bs, 0) != cudaSuccess || occ < 1) return 0;
+    const int per_sm = x->cfg.blocks_per_sm > 0 ? std::min(x->cfg.blocks_per_sm, occ) : occ;
+    int g = x->sms * per_sm;
+    if (x->cfg.grid_blocks > 0) g = std::min(x->cfg.grid_blocks, x->sms * occ);
+    return g;
+}
+
+int ensure_batch_buffers(trees_ctx *x, int32_t n) {
+    if (x->batch_cap >= n) return TREES_OK;
+    if (x->d_jobs) cudaFree(x->d_jobs);
+    if (x->d_joff) cudaFree(x->d_joff);
+    if (x->d_done) cudaFree(x->d_done);
+    if (x->d_bc) cudaFree(x->d_bc);
+    if (x->h_jobs) cudaFreeHost(x->h_jobs);
+    x->d_jobs = nullptr;
+    x->d_joff = nullptr;
+    x->d_done = nullptr;
+    x->d_bc = nullptr;
+    x->h_jobs = nullptr;
+    x->batch_cap = 0;
+    if (cudaMalloc(&x->d_jobs, sizeof(Job) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&x->d_joff, sizeof(uint32_t) * ((size_t)n + 1)) != cudaSuccess ||
+        cudaMalloc(&x->d_done, sizeof(BatchDone) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&x->d_bc, sizeof(BatchCtl)) != cudaSuccess ||
+        cudaMallocHost(&x->h_jobs, sizeof(Job) * (size_t)n) != cudaSuccess) {
+        cudaGetLastError();
+        return TREES_ERR_CUDA;
+    }
+    x->batch_cap = n;
+    return TREES_OK;
+}
+
+int launch_batch(trees_ctx *x, BatchCtl *d_bc, Job *d_jobs, uint32_t *d_joff, BatchDone *d_done, uint32_t max_steps,
+                 cudaStream_t st) {
+    const void *kern = batch_kernel_for(x->bs);
+    const int grid = batch_grid(x, kern);
+    if (grid < 1) return TREES_ERR_CUDA;
+    if (cudaMemsetAsync(x->ctl, 0, sizeof(Ctl), st) != cudaSuccess) return TREES_ERR_CUDA;
+    void *args[] = {&x->ctl, &x->conf, &d_bc, &d_jobs, &d_joff, &d_done, &max_steps, &x->blk};
+    if (cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(x->bs), args, 0, st) != cudaSuccess) {
+        cudaGetLastError();
+        return TREES_ERR_CUDA;
+    }
+    return TREES_OK;
+}
+
+void fill_result(const BatchDone &d, trees_job_result_t *o) {
+    o->id = d.id;
+    o->result = d.result;
+    o->tasks = d.tasks;
+    o->joins = d.joins;
+    o->maps = d.maps;
+    o->ns = d.ns;
+    o->epochs = d.epochs;
+    o->peak_slots = d.peak;
+    o->status = d.status;
+    o->pad = 0;
+}
+
+}  // namespace
+
+extern "C" uint64_t trees_job_slots(const trees_job_t *job, int32_t *exact) {
+    if (!job) {
+        if (exact) *exact = 0;
+        return 0;
+    }
+    return job_slots(job, exact);
+}
+
+extern "C" int trees_batch_run(trees_ctx *x, const trees_job_t *jobs, const uint64_t *seg_slots, int32_t njobs,
+                               void *stream) {
+    if (!x || !jobs || njobs <= 0) return TREES_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure_batch_buffers(x, njobs);
+    if (rc) return rc;
+    uint64_t base = 0;
+    for (int32_t i = 0; i < njobs; ++i) {
+        const uint64_t want = seg_slots ? seg_slots[i] : job_slots(&jobs[i], nullptr);
+        if (want == 0 || want > 0xFFFFFFFFull) return TREES_ERR_INVALID_ARG;
+        if (base + want > x->cap) return TREES_ERR_ADMISSION;
+        rc = make_job_record(&jobs[i], (uint32_t)base, (uint32_t)want, (uint64_t)i, &x->h_jobs[i]);
+        if (rc) return rc;
+        base += want;
+    }
+    BatchCtl hb;
+    std::memset(&hb, 0, sizeof(hb));
+    hb.njobs = (unsigned int)njobs;
+    hb.max_epochs = x->cfg.max_epochs;
+    if (cudaMemcpyAsync(x->d_jobs, x->h_jobs, sizeof(Job) * (size_t)njobs, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(x->d_bc, &hb, sizeof(hb), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return TREES_ERR_CUDA;
+    x->last_stream = st;
+    x->batch_n = njobs;
+    // the host copies above read pageable/pinned host memory; keep hb alive until issued
+    if (cudaStreamSynchronize(st) != cudaSuccess) return TREES_ERR_CUDA;
+    return launch_batch(x, x->d_bc, x->d_jobs, x->d_joff, x->d_done, 0xFFFFFFFFu, st);
+}
+
+extern "C" int trees_batch_results(trees_ctx *x, trees_job_result_t *out, int32_t njobs, uint32_t *steps) {
+    if (!x || !out || njobs != x->batch_n) return TREES_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(x->last_stream) != cudaSuccess) return TREES_ERR_CUDA;
+    BatchCtl hb;
+    int err = 0;
+    if (cudaMemcpy(&hb, x->d_bc, sizeof(hb), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&err, &x->ctl->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TREES_ERR_CUDA;
+    std::vector<BatchDone> d(hb.done_count);
+    if (hb.done_count && cudaMemcpy(d.data(), x->d_done, sizeof(BatchDone) * hb.done_count,
+                                    cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TREES_ERR_CUDA;
+    for (int32_t i = 0; i < njobs; ++i) {
+        std::memset(&out[i], 0, sizeof(out[i]));
+        out[i].id = (uint64_t)i;
+        out[i].status = err ? err : TREES_ERR_EPOCH_LIMIT;  // overwritten by the job's completion record
+    }
+    for (const BatchDone &r : d)
+        if (r.job < (uint32_t)njobs) fill_result(r, &out[r.job]);
+    if (steps) *steps = hb.steps;
+    return err;
+}
+
+// ------------------------------------------------------------------ server
+
+struct trees_server {
+    trees_ctx *ctx = nullptr;
+    int32_t max_jobs = 0, steps = 0;
+    Job *d_jobs = nullptr, *d_stage = nullptr, *h_stage = nullptr;
+    uint32_t *d_joff = nullptr, *d_entries = nullptr, *h_entries = nullptr;
+    BatchDone *d_done = nullptr, *h_done = nullptr;
+    BatchCtl *d_bc = nullptr, *h_bc = nullptr;
+    struct Pending {
+        trees_job_t job;
+        uint64_t slots, id;
+    };
+    std::deque<Pending> queue;
+    std::vector<int32_t> free_entries;
+    std::vector<uint8_t> used;
+    std::vector<std::pair<uint32_t, uint32_t>> seg;  // per entry: base, length
+    std::map<uint32_t, uint32_t> free_seg;           // base -> length
+    std::vector<trees_job_result_t> finished;
+    uint32_t hw = 0;
+    int32_t running = 0;
+    uint64_t next_id = 0, launches = 0;
+};
+
+namespace {
+
+bool seg_alloc(trees_server *s, uint32_t len, uint32_t *base) {
+    for (auto it = s->free_seg.begin(); it != s->free_seg.end(); ++it) {
+        if (it->second >= len) {
+            *base = it->first;
+            const uint32_t rest = it->second - len, nb = it->first + len;
+            s->free_seg.erase(it);
+            if (rest) s->free_seg[nb] = rest;
+            return true;
+        }
+    }
+    return false;
+}
+
+void seg_free(trees_server *s, uint32_t base, uint32_t len) {
+    auto it = s->free_seg.emplace(base, len).first;
+    auto nx = std::next(it);
+    if (nx != s->free_seg.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        s->free_seg.erase(nx);
+    }
+    if (it != s->free_seg.begin()) {
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            s->free_seg.erase(it);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int trees_server_create(size_t pool_slots, int32_t max_jobs, int32_t steps_per_launch,
+                                   const trees_config_t *cfg, trees_server **out) {
+    if (!out || max_jobs <= 0 || steps_per_launch <= 0) return TREES_ERR_INVALID_ARG;
+    *out = nullptr;
+    trees_server *s = new (std::nothrow) trees_server();
+    if (!s) return TREES_ERR_INVALID_ARG;
+    int rc = trees_create(pool_slots, cfg, &s->ctx);
+    if (rc) {
+        delete s;
+        return rc;
+    }
+    s->max_jobs = max_jobs;
+    s->steps = steps_per_launch;
+    const size_t n = (size_t)max_jobs;
+    if (cudaMalloc(&s->d_jobs, sizeof(Job) * n) != cudaSuccess || cudaMalloc(&s->d_stage, sizeof(Job) * n) != cudaSuccess ||
+        cudaMalloc(&s->d_joff, sizeof(uint32_t) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&s->d_entries, sizeof(uint32_t) * n) != cudaSuccess ||
+        cudaMalloc(&s->d_done, sizeof(BatchDone) * n) != cudaSuccess ||
+        cudaMalloc(&s->d_bc, sizeof(BatchCtl)) != cudaSuccess ||
+        cudaMallocHost(&s->h_stage, sizeof(Job) * n) != cudaSuccess ||
+        cudaMallocHost(&s->h_entries, sizeof(uint32_t) * n) != cudaSuccess ||
+        cudaMallocHost(&s->h_done, sizeof(BatchDone) * n) != cudaSuccess ||
+        cudaMallocHost(&s->h_bc, sizeof(BatchCtl)) != cudaSuccess ||
+        cudaMemset(s->d_jobs, 0, sizeof(Job) * n) != cudaSuccess) {
+        cudaGetLastError();
+        trees_server_destroy(s);
+        return TREES_ERR_CUDA;
+    }
+    s->used.assign(n, 0);
+    s->seg.assign(n, {0u, 0u});
+    for (int32_t i = max_jobs - 1; i >= 0; --i) s->free_entries.push_back(i);
+    s->free_seg[0] = (uint32_t)s->ctx->cap;
+    *out = s;
+    return TREES_OK;
+}
+
+extern "C" void trees_server_destroy(trees_server *s) {
+    if (!s) return;
+    if (s->d_jobs) cudaFree(s->d_jobs);
+    if (s->d_stage) cudaFree(s->d_stage);
+    if (s->d_joff) cudaFree(s->d_joff);
+    if (s->d_entries) cudaFree(s->d_entries);
+    if (s->d_done) cudaFree(s->d_done);
+    if (s->d_bc) cudaFree(s->d_bc);
+    if (s->h_stage) cudaFreeHost(s->h_stage);
+    if (s->h_entries) cudaFreeHost(s->h_entries);
+    if (s->h_done) cudaFreeHost(s->h_done);
+    if (s->h_bc) cudaFreeHost(s->h_bc);
+    if (s->ctx) trees_destroy(s->ctx);
+    delete s;
+}
+
+extern "C" int trees_server_submit(trees_server *s, const trees_job_t *job, uint64_t seg_slots, uint64_t *id) {
+    if (!s || !job) return TREES_ERR_INVALID_ARG;
+    const uint64_t want = seg_slots ? seg_slots : job_slots(job, nullptr);
+    if (want == 0 || want > 0xFFFFFFFFull) return TREES_ERR_INVALID_ARG;
+    if (want > s->ctx->cap) return TREES_ERR_ADMISSION;
+    Job probe;
+    const int rc = make_job_record(job, 0u, 1u, 0u, &probe);
+    if (rc) return rc;
+    trees_server::Pending p;
+    p.job = *job;
+    p.slots = want;
+    p.id = s->next_id++;
+    s->queue.push_back(p);
+    if (id) *id = p.id;
+    return TREES_OK;
+}
+
+extern "C" int trees_server_step(trees_server *s, void *stream) {
+    if (!s) return TREES_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // admission: in arrival order, while an entry and a segment are free
+    uint32_t na = 0;
+    while (!s->queue.empty() && !s->free_entries.empty()) {
+        const trees_server::Pending &p = s->queue.front();
+        uint32_t base = 0;
+        if (!seg_alloc(s, (uint32_t)p.slots, &base)) break;
+        const int32_t e = s->free_entries.back();
+        s->free_entries.pop_back();
+        make_job_record(&p.job, base, (uint32_t)p.slots, p.id, &s->h_stage[na]);
+        s->h_entries[na] = (uint32_t)e;
+        s->used[e] = 1;
+        s->seg[e] = {base, (uint32_t)p.slots};
+        s->hw = std::max(s->hw, (uint32_t)e + 1u);
+        ++na;
+        ++s->running;
+        s->queue.pop_front();
+    }
+    if (na) {
+        if (cudaMemcpyAsync(s->d_stage, s->h_stage, sizeof(Job) * na, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(s->d_entries, s->h_entries, sizeof(uint32_t) * na, cudaMemcpyHostToDevice, st) !=
+                cudaSuccess)
+            return TREES_ERR_CUDA;
+        k_admit<<<std::min<uint32_t>(na, 1024u), 256, 0, st>>>(s->d_jobs, s->d_stage, s->d_entries, na);
+        if (cudaGetLastError() != cudaSuccess) return TREES_ERR_CUDA;
+    }
+    if (s->running == 0) return TREES_OK;
+    std::memset(s->h_bc, 0, sizeof(BatchCtl));
+    s->h_bc->njobs = s->hw;
+    s->h_bc->max_epochs = s->ctx->cfg.max_epochs;
+    if (cudaMemcpyAsync(s->d_bc, s->h_bc, sizeof(BatchCtl), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return TREES_ERR_CUDA;
+    int rc = launch_batch(s->ctx, s->d_bc, s->d_jobs, s->d_joff, s->d_done, (uint32_t)s->steps, st);
+    if (rc) return rc;
+    ++s->launches;
+    if (cudaMemcpyAsync(s->h_bc, s->d_bc, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return TREES_ERR_CUDA;
+    int err = 0;
+    if (cudaMemcpy(&err, &s->ctx->ctl->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TREES_ERR_CUDA;
+    const uint32_t nd = s->h_bc->done_count;
+    if (nd) {
+        if (cudaMemcpyAsync(s->h_done, s->d_done, sizeof(BatchDone) * nd, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return TREES_ERR_CUDA;
+        for (uint32_t i = 0; i < nd; ++i) {
+            const BatchDone &d = s->h_done[i];
+            trees_job_result_t r;
+            fill_result(d, &r);
+            s->finished.push_back(r);
+            const int32_t e = (int32_t)d.job;
+            if (e >= 0 && e < s->max_jobs && s->used[e]) {
+                s->used[e] = 0;
+                seg_free(s, s->seg[e].first, s->seg[e].second);
+                s->free_entries.push_back(e);
+                --s->running;
+            }
+        }
+        while (s->hw > 0 && !s->used[s->hw - 1]) --s->hw;
+    }
+    return err;
+}
+
+extern "C" int trees_server_poll(trees_server *s, trees_job_result_t *out, int32_t cap, int32_t *n) {
+    if (!s || !n || (cap > 0 && !out)) return TREES_ERR_INVALID_ARG;
+    const int32_t m = std::min<int32_t>(cap, (int32_t)s->finished.size());
+    for (int32_t i = 0; i < m; ++i) out[i] = s->finished[i];
+    s->finished.erase(s->finished.begin(), s->finished.begin() + m);
+    *n = m;
+    return TREES_OK;
+}
+
+extern "C" int trees_server_stats(trees_server *s, int32_t *queued, int32_t *running, uint64_t *launches) {
+    if (!s) return TREES_ERR_INVALID_ARG;
+    if (queued) *queued = (int32_t)s->queue.size();
+    if (running) *running = s->running;
+    if (launches) *launches = s->launches;
+    return TREES_OK;
+}
+
+extern "C" int trees_server_replay(trees_server *s, const trees_job_t *jobs, const uint64_t *seg_slots,
+                                   const double *arrival_s, int32_t n, int32_t plain, double *latency_s,
+                                   trees_job_result_t *results, void *stream) {
+    if (!s || !jobs || !arrival_s || !latency_s || !results || n <= 0) return TREES_ERR_INVALID_ARG;
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    auto elapsed = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
+    auto wait_until = [&](double t) {
+        while (elapsed() < t) {
+            const double d = t - elapsed();
+            if (d > 200e-6) std::this_thread::sleep_for(std::chrono::duration<double>(d - 100e-6));
+        }
+    };
+    if (plain) {  // one job per launch, first come first served
+        for (int32_t i = 0; i < n; ++i) {
+            wait_until(arrival_s[i]);
+            int rc = trees_run(s->ctx, &jobs[i], stream);
+            if (rc) return rc;
+            const int status = trees_sync(s->ctx);
+            const double t = elapsed();
+            trees_stats_t st;
+            trees_stats(s->ctx, &st);
+            uint64_t v = 0;
+            trees_result(s->ctx, 0, &v);
+            trees_job_result_t &r = results[i];
+            std::memset(&r, 0, sizeof(r));
+            r.id = (uint64_t)i;
+            r.result = (jobs[i].program == TREES_PROG_FIB || jobs[i].program == TREES_PROG_NQUEENS) ? v : 0;
+            r.tasks = st.tasks;
+            r.joins = st.joins;
+            r.maps = st.maps;
+            r.ns = st.ns;
+            r.epochs = (uint32_t)st.epochs;
+            r.peak_slots = (uint32_t)st.peak_slots;
+            r.status = status;
+            latency_s[i] = t - arrival_s[i];
+        }
+        return TREES_OK;
+    }
+    std::vector<int32_t> index_of_id;
+    const uint64_t id0 = s->next_id;
+    int32_t next = 0, done = 0;
+    std::vector<trees_job_result_t> got((size_t)std::max(1, s->max_jobs));
+    while (done < n) {
+        while (next < n && arrival_s[next] <= elapsed()) {
+            uint64_t id = 0;
+            const int rc = trees_server_submit(s, &jobs[next], seg_slots ? seg_slots[next] : 0, &id);
+            if (rc) return rc;
+            ++next;
+        }
+        int32_t q = 0, r = 0;
+        trees_server_stats(s, &q, &r, nullptr);
+        if (q + r == 0) {
+            if (next < n) wait_until(arrival_s[next]);
+            continue;
+        }
+        const int rc = trees_server_step(s, stream);
+        if (rc) return rc;
+        const double t = elapsed();
+        int32_t m = 0;
+        trees_server_poll(s, got.data(), (int32_t)got.size(), &m);
+        for (int32_t k = 0; k < m; ++k) {
+            const int64_t i = (int64_t)(got[k].id - id0);
+            if (i < 0 || i >= n) continue;
+            results[i] = got[k];
+            results[i].id = (uint64_t)i;
+            latency_s[i] = t - arrival_s[i];
+            ++done;
+        }
+    }
     return TREES_OK;
 }

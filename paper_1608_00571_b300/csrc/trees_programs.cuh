@@ -55,13 +55,13 @@ __device__ __forceinline__ uint32_t nq_free(uint32_t a0, uint32_t a1, uint32_t n
 }
 
 // Step 1 of a task: read it, emit if it is a leaf, count forks, request maps.
-__device__ __forceinline__ void plan_task(const Conf &c, Plan &p, uint32_t cen, uint32_t e) {
+__device__ __forceinline__ void plan_task(const Conf &c, const RunParams &rp, Plan &p, uint32_t cen, uint32_t e) {
     const uint32_t s = p.s;
     switch (p.type) {
     case TREES_TASK_FIB: {
         const uint32_t n = c.a0[s];
         p.a0 = n;
-        if (n < 2u || n <= c.rp.cutoff) {
+        if (n < 2u || n <= rp.cutoff) {
             c.result[s] = n < 2u ? (unsigned long long)n : fib_leaf(n);
             c.code[s] = 0u;  // emit: the entry is dead (Sec. 4.3.2)
         } else {
@@ -79,7 +79,7 @@ __device__ __forceinline__ void plan_task(const Conf &c, Plan &p, uint32_t cen, 
         const uint32_t lo = c.a0[s], hi = c.a1[s];
         p.a0 = lo;
         p.a1 = hi;
-        if (hi - lo <= c.rp.leaf) {
+        if (hi - lo <= rp.leaf) {
             if (hi > lo) {
                 p.mkind = MAP_LEAF_SORT;
                 p.ma = lo;
@@ -104,7 +104,7 @@ __device__ __forceinline__ void plan_task(const Conf &c, Plan &p, uint32_t cen, 
         break;
     }
     case TREES_TASK_NQ_ROW: {
-        const uint32_t a0 = c.a0[s], a1 = c.a1[s], n = c.rp.n;
+        const uint32_t a0 = c.a0[s], a1 = c.a1[s], n = rp.n;
         p.a0 = a0;
         p.a1 = a1;
         if ((a0 >> 16) == n) {
@@ -122,7 +122,7 @@ __device__ __forceinline__ void plan_task(const Conf &c, Plan &p, uint32_t cen, 
         break;
     }
     case TREES_TASK_NQ_SUM: {
-        const uint32_t k = (uint32_t)__popc(nq_free(c.a0[s], c.a1[s], c.rp.n));
+        const uint32_t k = (uint32_t)__popc(nq_free(c.a0[s], c.a1[s], rp.n));
         const uint32_t l = c.link[s];
         unsigned long long sum = 0;
         for (uint32_t i = 0; i < k; ++i) sum += c.result[l + i];
@@ -132,7 +132,7 @@ __device__ __forceinline__ void plan_task(const Conf &c, Plan &p, uint32_t cen, 
     }
     case TREES_TASK_BFS_VISIT: {
         const uint32_t v = c.a0[s];
-        const int32_t rb = __ldg(c.rp.row_ptr + v), re = __ldg(c.rp.row_ptr + v + 1);
+        const int32_t rb = __ldg(rp.row_ptr + v), re = __ldg(rp.row_ptr + v + 1);
         if (re > rb) {
             p.xv = (uint32_t)rb;
             p.xn = (uint32_t)(re - rb);
@@ -148,7 +148,7 @@ __device__ __forceinline__ void plan_task(const Conf &c, Plan &p, uint32_t cen, 
         break;
     }
     case TREES_TASK_PO_AFTER: {
-        c.rp.visit_epoch[c.a0[s]] = (int32_t)e;
+        rp.visit_epoch[c.a0[s]] = (int32_t)e;
         c.code[s] = 0u;
         break;
     }
@@ -157,7 +157,7 @@ __device__ __forceinline__ void plan_task(const Conf &c, Plan &p, uint32_t cen, 
         p.a0 = node;
         c.code[s] = 0u;
         if ((int32_t)node >= 0) {
-            c.rp.visit_epoch[node] = (int32_t)e;
+            rp.visit_epoch[node] = (int32_t)e;
             p.nfork = 2u;
         }
         break;
@@ -169,7 +169,8 @@ __device__ __forceinline__ void plan_task(const Conf &c, Plan &p, uint32_t cen, 
 
 // Step 2: write the children into [child, child + nfork) for epoch CEN+1 and
 // turn the task into its join continuation.  Returns 1 if it joined.
-__device__ __forceinline__ uint32_t commit_task(const Conf &c, const Plan &p, uint32_t cen, uint32_t child) {
+__device__ __forceinline__ uint32_t commit_task(const Conf &c, const RunParams &rp, const Plan &p, uint32_t cen,
+                                                 uint32_t child) {
     const uint32_t s = p.s;
     const uint32_t fe = enc(cen + 1u, 0u);
     switch (p.type) {
@@ -194,7 +195,7 @@ __device__ __forceinline__ uint32_t commit_task(const Conf &c, const Plan &p, ui
         return 1u;
     }
     case TREES_TASK_NQ_ROW: {
-        const uint32_t n = c.rp.n, mask = (1u << n) - 1u;
+        const uint32_t n = rp.n, mask = (1u << n) - 1u;
         const uint32_t r = p.a0 >> 16, cols = p.a0 & 0xFFFFu, d1 = p.a1 & 0xFFFFu, d2 = p.a1 >> 16;
         uint32_t fr = nq_free(p.a0, p.a1, n);
         uint32_t slot = child;
@@ -213,9 +214,9 @@ __device__ __forceinline__ uint32_t commit_task(const Conf &c, const Plan &p, ui
     case TREES_TASK_PO: {
         const int32_t node = (int32_t)p.a0;
         c.code[child] = fe + TREES_TASK_PO;
-        c.a0[child] = (uint32_t)__ldg(c.rp.right + node);
+        c.a0[child] = (uint32_t)__ldg(rp.right + node);
         c.code[child + 1] = fe + TREES_TASK_PO;
-        c.a0[child + 1] = (uint32_t)__ldg(c.rp.left + node);
+        c.a0[child + 1] = (uint32_t)__ldg(rp.left + node);
         c.link[s] = child;
         c.code[s] = enc(cen, TREES_TASK_PO_AFTER);
         return 1u;
@@ -223,9 +224,9 @@ __device__ __forceinline__ uint32_t commit_task(const Conf &c, const Plan &p, ui
     case TREES_TASK_PRE: {
         const int32_t node = (int32_t)p.a0;
         c.code[child] = fe + TREES_TASK_PRE;
-        c.a0[child] = (uint32_t)__ldg(c.rp.right + node);
+        c.a0[child] = (uint32_t)__ldg(rp.right + node);
         c.code[child + 1] = fe + TREES_TASK_PRE;
-        c.a0[child + 1] = (uint32_t)__ldg(c.rp.left + node);
+        c.a0[child + 1] = (uint32_t)__ldg(rp.left + node);
         return 0u;
     }
     default:
@@ -320,7 +321,7 @@ __device__ __forceinline__ void epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm
     if (inr) p.type = task_type(c.code[s], cen);  // invalid or stale entries exit at once (Sec. 5.3)
     if (p.type) {
         acc.valid++;
-        plan_task(c, p, cen, e);
+        plan_task(c, c.rp, p, cen, e);
     }
     uint32_t ftot;
     int anymap;
@@ -335,7 +336,7 @@ __device__ __forceinline__ void epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm
         }
         __syncthreads();
         uint32_t joined = 0u;
-        if (!sm.bc32[1] && p.nfork) joined = commit_task(c, p, cen, base + sm.bc32[0] + foff);
+        if (!sm.bc32[1] && p.nfork) joined = commit_task(c, c.rp, p, cen, base + sm.bc32[0] + foff);
         acc.joins += joined;
         if (__any_sync(0xffffffffu, joined) && (threadIdx.x & 31) == 0) ctl->join[ep] = 1u;  // joinScheduled
     }
@@ -498,7 +499,8 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
 // tiled list (leaf sorts, merge tiles) followed by the expansion tiles.
 template <int BS>
 __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, uint32_t e, uint32_t cen, uint32_t base,
-                          unsigned long long mt, unsigned long long me) {
+                          unsigned long long mt, unsigned long long me, const RunParams *job_params = nullptr,
+                          uint32_t job_stride = 0) {
     const uint32_t nt1 = (uint32_t)(mt & CTR_LOW_MASK);
     const uint32_t nd2 = (uint32_t)(me >> 40), ne2 = (uint32_t)(me & CTR_LOW_MASK);
     const uint32_t nt2 = (ne2 + EXPAND_TILE - 1u) / EXPAND_TILE;
@@ -507,6 +509,12 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
         if (t < nt1) {
             const uint32_t di = c.mt_tiledesc[t];
             const uint32_t kind = c.mt_kind[di], a = c.mt_a[di], b = c.mt_b[di], cc = c.mt_c[di];
+            if (job_params) {  // batched runs: the descriptor names its job
+                const RunParams *jp = reinterpret_cast<const RunParams *>(
+                    reinterpret_cast<const char *>(job_params) + (size_t)c.mt_job[di] * job_stride);
+                keys = jp->keys;
+                scratch = jp->scratch;
+            }
             // a node at depth d writes its sorted run to keys (d even) or scratch (d odd)
             uint32_t *outb = (cc & 1u) ? scratch : keys;
             if (kind == MAP_LEAF_SORT) {
