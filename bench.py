@@ -271,6 +271,95 @@ def vfit(T, torch, stream, sms):
             "points": len(ys), "P": "SMs used (1024-thread blocks, one per SM): 37, 74, 148"}
 
 
+def batch_and_serve(T, torch, np, gen, stream, bs):
+    """The batched configuration: 4096 jobs (seed 42) in one persistent launch
+    against one job per launch, then Poisson arrivals (seed 43) at 0.5x and
+    0.9x of the batched throughput served by continuous batching and by one
+    job per launch."""
+    import oracle
+    kind, param, kseed = gen.jobs(42, 4096)
+    jobs, pristine, work = [], [], []
+    for i in range(4096):
+        if kind[i] == gen.JOB_FIB:
+            jobs.append(T.make_job(T.TREES_PROG_FIB, n=int(param[i])))
+        elif kind[i] == gen.JOB_NQUEENS:
+            jobs.append(T.make_job(T.TREES_PROG_NQUEENS, n=int(param[i])))
+        else:
+            k = torch.from_numpy(gen.keys_u32(int(kseed[i]), int(param[i])).view(np.int32)).cuda()
+            d, sc = torch.empty_like(k), torch.empty_like(k)
+            pristine.append(k)
+            work.append(d)
+            jobs.append(T.make_job(T.TREES_PROG_MERGESORT, n=int(param[i]), keys=d, scratch=sc))
+            jobs[-1]._keep = (d, sc)
+
+    def reset():
+        for k, d in zip(pristine, work):
+            d.copy_(k)
+        torch.cuda.synchronize()
+
+    segs = [T.trees_job_slots(j)[0] for j in jobs]
+    cfg = T.trees_default_config(block_size=bs, map_capacity=1 << 22)
+    ctx = T.trees_create(sum(segs) + 1024, cfg)
+    out = {}
+    times = []
+    for rep in range(3):
+        reset()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        T.trees_batch_run(ctx, jobs, segs, stream)
+        b.record(stream)
+        status, res, steps = T.trees_batch_results(ctx, 4096)
+        assert status == T.TREES_OK and all(r["status"] == T.TREES_OK for r in res)
+        times.append(a.elapsed_time(b))
+    T.trees_destroy(ctx)
+    # spot checks against closed forms / oracle
+    nq = {}
+    for i, r in enumerate(res):
+        if kind[i] == gen.JOB_NQUEENS:
+            n = int(param[i])
+            assert r["result"] == nq.setdefault(n, oracle.nqueens(n))[0]
+        elif kind[i] == gen.JOB_FIB:
+            assert r["epochs"] == 2 * int(param[i]) - 1
+    tasks = sum(r["tasks"] for r in res)
+    bms = min(times)
+    out["batched"] = {"jobs": 4096, "ms": bms, "jobs_per_s": 4096 / (bms / 1000), "steps": steps,
+                      "tasks": tasks, "tasks_per_s": tasks / (bms / 1000)}
+    # one job per launch, back to back
+    reset()
+    solo = T.trees_create(max(segs) + 1024, T.trees_default_config(block_size=bs))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in jobs:
+        T.trees_run(solo, j, stream)
+        assert T.trees_sync(solo) == T.TREES_OK
+    pms = 1000 * (time.perf_counter() - t0)
+    T.trees_destroy(solo)
+    out["one_job_per_launch"] = {"jobs": 4096, "ms": pms, "jobs_per_s": 4096 / (pms / 1000)}
+    # served: continuous batching vs one job per launch, same arrivals
+    batched_rate = 4096 / (bms / 1000)
+    serve = {}
+    for frac in (0.5, 0.9):
+        rate = frac * batched_rate
+        arr = gen.poisson_arrivals(43, 4096, rate)
+        row = {"rate_jobs_per_s": rate}
+        for mode, plain in (("continuous", False), ("one_job_per_launch", True)):
+            reset()
+            srv = T.trees_server_create(sum(segs) + 1024, 4096, 4, cfg)
+            t0 = time.perf_counter()
+            lat, rr = T.trees_server_replay(srv, jobs, arr, segs, plain=plain, stream=stream)
+            wall = time.perf_counter() - t0
+            _, _, launches = T.trees_server_stats(srv)
+            T.trees_server_destroy(srv)
+            assert all(r["status"] == T.TREES_OK for r in rr)
+            lat_ms = np.array(lat) * 1000
+            row[mode] = {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                         "mean_ms": float(lat_ms.mean()), "jobs_per_s": 4096 / wall,
+                         "launches": int(launches) if not plain else 4096}
+        serve[f"{frac}x_batched"] = row
+    out["served"] = serve
+    return out
+
+
 def cpu_baseline(seconds):
     """The oracle's TVM simulator on fib(34), one host core, repeated for about
     `seconds` seconds."""
@@ -487,6 +576,7 @@ def main():
         sch["persistent"] = {"ms": ms_step, "us_per_epoch": us_epoch, "tasks_per_s": tasks / (ms_step / 1000)}
         line["schedulers"] = sch
         line["vfit"] = vfit(T, torch, stream, sms)
+        line["batch_serve"] = batch_and_serve(T, torch, np, gen, stream, 512)
 
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

@@ -82,6 +82,8 @@ typedef struct {
     int32_t inject_stall_epoch; /* test hook, -1 = off: in that epoch the last block leaves
                                    without arriving at the barrier, so the others time out */
     int32_t grid_blocks;     /* persistent grid size; 0 = SMs * blocks_per_sm (capped at co-residency) */
+    int32_t tasks_per_thread; /* TV slots a thread takes per Phase-2 tile: 1, 2 or 4 (0 = 2) */
+    int32_t reserved;
 } trees_config_t;
 
 /* Fills *cfg with the defaults above. */
@@ -159,6 +161,8 @@ typedef struct {
     uint64_t ns;            /* device time of the epoch loop (globaltimer) */
     int32_t status;         /* TREES_OK or the device-side error */
     int32_t error_epoch;    /* epoch in which the error was raised */
+    int32_t grid_blocks;    /* blocks of the run's grid */
+    int32_t block_size;     /* threads per block */
 } trees_stats_t;
 
 /* Statistics of the last run (call after trees_sync). */
@@ -188,9 +192,10 @@ int trees_bfs(trees_ctx *ctx, const int32_t *dev_row_ptr, const int32_t *dev_col
 
 /* ------------------------------------------------------------ measurement */
 
-/* The critical-path floor: a persistent kernel with the context's grid that
- * does nothing but `iters` of the scheduler's grid barrier.  Writes the
- * device time per barrier in microseconds. */
+/* The critical-path floor: a persistent kernel that does nothing but `iters`
+ * of the scheduler's grid barrier, on the grid of the context's last
+ * persistent run (else the context's default grid).  Writes the device time
+ * per barrier in microseconds. */
 int trees_barrier_floor(trees_ctx *ctx, uint32_t iters, void *stream, double *us_per_barrier);
 
 /* ------------------------------------------------------------ batches and serving

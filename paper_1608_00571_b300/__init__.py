@@ -52,7 +52,8 @@ class trees_config_t(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("scheduler", ctypes.c_int32),
                 ("trace", ctypes.c_int32), ("max_epochs", ctypes.c_uint32), ("trace_cap", ctypes.c_uint32),
                 ("timeout_ns", ctypes.c_uint64), ("map_capacity", ctypes.c_uint64),
-                ("inject_stall_epoch", ctypes.c_int32), ("grid_blocks", ctypes.c_int32)]
+                ("inject_stall_epoch", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
+                ("tasks_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class trees_job_t(ctypes.Structure):
@@ -67,7 +68,7 @@ class trees_stats_t(ctypes.Structure):
     _fields_ = [("epochs", ctypes.c_uint64), ("tasks", ctypes.c_uint64), ("forks", ctypes.c_uint64),
                 ("joins", ctypes.c_uint64), ("maps", ctypes.c_uint64), ("peak_slots", ctypes.c_uint64),
                 ("final_slots", ctypes.c_uint64), ("ns", ctypes.c_uint64), ("status", ctypes.c_int32),
-                ("error_epoch", ctypes.c_int32)]
+                ("error_epoch", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("block_size", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

@@ -3,6 +3,7 @@ nvcc for sm_103a.  Used by ``__graft_entry__.build()`` and by the binding when
 the library is missing or older than its sources."""
 from __future__ import annotations
 
+import concurrent.futures
 import fcntl
 import glob
 import os
@@ -43,11 +44,26 @@ def build(force: bool = False, verbose: bool = False) -> str:
         fcntl.flock(lf, fcntl.LOCK_EX)
         if not force and not stale():
             return LIB
+        objdir = os.path.join(HERE, "_build")
+        os.makedirs(objdir, exist_ok=True)
+        flags = [f for f in NVCC_FLAGS if f != "-shared"]
+
+        def compile_one(src):
+            obj = os.path.join(objdir, os.path.basename(src) + ".o")
+            cmd = ["nvcc", *flags, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
+            if verbose:
+                print(" ".join(cmd))
+            subprocess.check_call(cmd)
+            return obj
+
+        srcs = sources()
+        with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
+            objs = list(ex.map(compile_one, srcs))
         tmp = LIB + ".tmp"
-        cmd = ["nvcc", *NVCC_FLAGS, "-I", INCLUDE, "-I", CSRC, "-o", tmp, *sources(), "-lcuda"]
+        link = ["nvcc", "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp, *objs, "-lcuda"]
         if verbose:
-            print(" ".join(cmd))
-        subprocess.check_call(cmd)
+            print(" ".join(link))
+        subprocess.check_call(link)
         os.replace(tmp, LIB)
     return LIB
 

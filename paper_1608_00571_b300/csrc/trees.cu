@@ -25,6 +25,7 @@
 #include "trees_dev.cuh"
 #include "trees_programs.cuh"
 #include "trees_batch.cuh"
+#include "trees_kernels.cuh"
 
 #include <chrono>
 #include <deque>
@@ -35,43 +36,8 @@ using namespace trees;
 
 namespace {
 
-constexpr int NBLK_STATS = 8192;  // per-block statistics slots (blk_stats)
 
 // ------------------------------------------------------------------ kernels
-
-template <int BS>
-__device__ __forceinline__ void block_add_stats(unsigned long long *blk, const Acc &acc, Smem<BS> &sm) {
-    // block-reduce the per-thread counters, then one add per counter per block
-    const uint32_t v = __reduce_add_sync(0xffffffffu, acc.valid);
-    const uint32_t j = __reduce_add_sync(0xffffffffu, acc.joins);
-    const uint32_t m = __reduce_add_sync(0xffffffffu, acc.maps);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        sm.bc64[0] = 0;
-        sm.bc64[1] = 0;
-        sm.bc64[2] = 0;
-    }
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&sm.bc64[0], (unsigned long long)v);
-        atomicAdd(&sm.bc64[1], (unsigned long long)j);
-        atomicAdd(&sm.bc64[2], (unsigned long long)m);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long *b = blk + 4ull * (blockIdx.x % NBLK_STATS);
-        atomicAdd(b + 0, sm.bc64[0]);
-        atomicAdd(b + 1, sm.bc64[1]);
-        atomicAdd(b + 2, sm.bc64[2]);
-    }
-}
-
-template <int BS>
-__device__ __forceinline__ void trace_valid_add(const Conf &c, uint32_t e, uint32_t v, Smem<BS> &sm) {
-    if (!c.trace_on || e >= c.trace_cap) return;
-    const uint32_t w = __reduce_add_sync(0xffffffffu, v);
-    if ((threadIdx.x & 31) == 0 && w) atomicAdd(&c.trace_valid[e], w);
-}
 
 // Zeroes the control block and writes the root task into TV entry 0 for
 // epoch 0 (Sec. 5.2.1).
@@ -103,115 +69,10 @@ __global__ void k_bfs_init(int32_t *level, int32_t nv, int32_t src) {
         level[v] = (v == src) ? 0 : -1;
 }
 
-// The persistent scheduler: the whole epoch loop in one cooperative launch.
-template <int BS>
-__global__ void __launch_bounds__(BS) k_persistent(Ctl *ctl, Conf c, unsigned long long *blk) {
-    __shared__ Smem<BS> sm;
-    uint32_t bar = 0;
-    Acc acc = {0u, 0u, 0u};
-    if (threadIdx.x == 0) {
-        sm.sp = 1;
-        sm.stk[0] = Range{0u, 0u, 1u};
-        sm.next = 1u;
-    }
-    unsigned long long forks_total = 0;
-    uint32_t peak = 1u;
-    uint32_t e = 0;
-    for (;; ++e) {
-        // Phase 1: pop (CEN, NDRange); oldNextFreeCore = nextFreeCore
-        if (threadIdx.x == 0) {
-            int stop = 0;
-            if (sm.sp == 0) {
-                stop = 1;
-            } else if (e >= c.max_epochs) {
-                stop = 2;
-                set_err(ctl, TREES_ERR_EPOCH_LIMIT, e);
-            } else {
-                const Range r = sm.stk[--sm.sp];
-                sm.cen = r.cen;
-                sm.lo = r.lo;
-                sm.hi = r.hi;
-                sm.base = sm.next;
-            }
-            sm.stop = stop;
-            if (!stop && blockIdx.x == 0) {  // clear the counters epoch e+1 will use
-                const uint32_t q = (e + 1u) % 3u;
-                ctl->cnt[q] = 0u;
-                ctl->join[q] = 0u;
-                ctl->mt_ctr[q] = 0ull;
-                ctl->me_ctr[q] = 0ull;
-            }
-        }
-        __syncthreads();
-        if (sm.stop) break;
-        const uint32_t cen = sm.cen, lo = sm.lo, hi = sm.hi, base = sm.base, ep = e % 3u;
-        // Phase 2: every entry of [lo, hi)
-        const uint32_t v0 = acc.valid;
-        for (unsigned long long t0 = (unsigned long long)lo + (unsigned long long)blockIdx.x * BS; t0 < hi;
-             t0 += (unsigned long long)gridDim.x * BS) {
-            const unsigned long long s = t0 + threadIdx.x;
-            epoch_tile<BS>(c, ctl, sm, (uint32_t)s, s < hi, cen, base, ep, e, acc);
-        }
-        trace_valid_add<BS>(c, e, acc.valid - v0, sm);
-        if ((int32_t)e == c.stall_epoch && blockIdx.x == gridDim.x - 1) return;  // test hook: never arrives
-        if (!grid_sync<BS>(ctl, &bar, c.timeout_ns, sm)) break;
-        const unsigned long long mt = vload(&ctl->mt_ctr[ep]), me = vload(&ctl->me_ctr[ep]);
-        if (mt | me) {  // the map operations of this epoch run before the next one (Sec. 5.2.4)
-            map_phase<BS>(c, ctl, sm, ep, e, cen, base, mt, me);
-            if (!grid_sync<BS>(ctl, &bar, c.timeout_ns, sm)) break;
-        }
-        // Phase 3: push the join range, then the fork range; or give the range back
-        if (threadIdx.x == 0) {
-            const uint32_t f = vload(&ctl->cnt[ep]), jf = vload(&ctl->join[ep]);
-            int ok = 1;
-            if (jf) {
-                if (sm.sp < STK_CAP) sm.stk[sm.sp++] = Range{cen, lo, hi};
-                else ok = 0;
-            }
-            if (f) {
-                if (sm.sp < STK_CAP) sm.stk[sm.sp++] = Range{cen + 1u, base, base + f};
-                else ok = 0;
-                sm.next = base + f;
-            } else if (!jf) {
-                sm.next = lo;  // neither forks nor joins: nextFreeCore decreases (Sec. 5.3)
-            }
-            if (!ok) {
-                if (blockIdx.x == 0) set_err(ctl, TREES_ERR_STACK, e);
-                sm.sp = 0;
-            }
-            if (blockIdx.x == 0) {
-                forks_total += f;
-                peak = max(peak, base + f);
-                if (c.trace_on && e < c.trace_cap) {
-                    trees_epoch_t r;
-                    r.cen = cen;
-                    r.lo = lo;
-                    r.hi = hi;
-                    r.valid = 0u;
-                    r.forks = f;
-                    r.joined = jf;
-                    r.maps = (uint32_t)(mt >> 40) + (uint32_t)(me >> 40);
-                    r.pad = 0u;
-                    r.t_ns = globaltimer();
-                    c.trace[e] = r;
-                }
-            }
-        }
-    }
-    block_add_stats<BS>(blk, acc, sm);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctl->epochs = e;
-        ctl->peak = peak;
-        ctl->final_next = sm.next;
-        ctl->forks = forks_total;
-        ctl->t_end = globaltimer();
-    }
-}
-
 // Phase 2 of one epoch as its own kernel (graph and host-loop schedulers).
 // from_ctl = 1: the epoch comes from the control block (graph); 0: from the
 // arguments (host loop, grid sized to the NDRange as in Sec. 5.1.1).
-template <int BS>
+template <int BS, int TPT>
 __global__ void __launch_bounds__(BS) k_epoch(Ctl *ctl, Conf c, unsigned long long *blk, int from_ctl, uint32_t a_cen,
                                               uint32_t a_lo, uint32_t a_hi, uint32_t a_base, uint32_t a_e) {
     __shared__ Smem<BS> sm;
@@ -242,10 +103,11 @@ __global__ void __launch_bounds__(BS) k_epoch(Ctl *ctl, Conf c, unsigned long lo
         ctl->me_ctr[q] = 0ull;
     }
     Acc acc = {0u, 0u, 0u};
-    for (unsigned long long t0 = (unsigned long long)lo + (unsigned long long)blockIdx.x * BS; t0 < hi;
-         t0 += (unsigned long long)gridDim.x * BS) {
-        const unsigned long long s = t0 + threadIdx.x;
-        epoch_tile<BS>(c, ctl, sm, (uint32_t)s, s < hi, cen, base, ep, e, acc);
+    int par = 0;
+    for (unsigned long long t0 = (unsigned long long)lo + (unsigned long long)blockIdx.x * (BS * TPT); t0 < hi;
+         t0 += (unsigned long long)gridDim.x * (BS * TPT)) {
+        epoch_tile<BS, TPT, PM_ALL>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par);
+        par ^= 1;
     }
     trace_valid_add<BS>(c, e, acc.valid, sm);
     block_add_stats<BS>(blk, acc, sm);
@@ -267,7 +129,17 @@ __global__ void __launch_bounds__(BS) k_map(Ctl *ctl, Conf c, int from_ctl, uint
     const uint32_t cen = sm.cen, base = sm.base, e = sm.next, ep = e % 3u;
     const unsigned long long mt = vload(&ctl->mt_ctr[ep]), me = vload(&ctl->me_ctr[ep]);
     if (!(mt | me)) return;
-    map_phase<BS>(c, ctl, sm, ep, e, cen, base, mt, me);
+    map_phase<BS, PM_ALL>(c, ctl, sm, ep, e, cen, base, mt, me);
+}
+
+// The partition sub-phase of one epoch's merges, as its own kernel.
+template <int BS>
+__global__ void __launch_bounds__(BS) k_partition(Ctl *ctl, Conf c, int from_ctl, uint32_t a_e) {
+    if (vload(&ctl->err) != 0 || (from_ctl && vload(&ctl->g_stop) != 0u)) return;
+    const uint32_t e = from_ctl ? vload(&ctl->g_e) : a_e, ep = e % 3u;
+    const unsigned long long mt = vload(&ctl->mt_ctr[ep]);
+    if (!needs_partition(mt)) return;
+    partition_phase<BS>(c, mt, nullptr, 0u);
 }
 
 // Phase 3 + Phase 1 of the graph scheduler (one thread): updates the
@@ -357,20 +229,37 @@ __global__ void __launch_bounds__(BS) k_floor(Ctl *ctl, uint32_t iters, unsigned
 // ------------------------------------------------------------------ host side
 
 struct Kern {
-    const void *persistent, *epoch, *map, *floor;
+    const void *persistent, *epoch, *map, *floor, *partition;
 };
 
-template <int BS>
+template <int BS, int TPT>
 Kern kern_for() {
-    return Kern{(const void *)k_persistent<BS>, (const void *)k_epoch<BS>, (const void *)k_map<BS>,
-                (const void *)k_floor<BS>};
+    return Kern{nullptr, (const void *)k_epoch<BS, TPT>, (const void *)k_map<BS>, (const void *)k_floor<BS>,
+                (const void *)k_partition<BS>};
 }
 
-bool kern_by_bs(int bs, Kern *k) {
-    switch (bs) {
-    case 256: *k = kern_for<256>(); return true;
-    case 512: *k = kern_for<512>(); return true;
-    case 1024: *k = kern_for<1024>(); return true;
+// The persistent kernel compiled for a program.
+const void *persistent_kernel(int program, int bs, int tpt) {
+    switch (program) {
+    case TREES_PROG_FIB: return persistent_kernel_fib(bs, tpt);
+    case TREES_PROG_MERGESORT: return persistent_kernel_ms(bs, tpt);
+    case TREES_PROG_NQUEENS: return persistent_kernel_nq(bs, tpt);
+    case TREES_PROG_BFS: return persistent_kernel_bfs(bs, tpt);
+    default: return persistent_kernel_trav(bs, tpt);
+    }
+}
+
+bool kern_by(int bs, int tpt, Kern *k) {
+    switch (bs * 10 + tpt) {
+    case 2561: *k = kern_for<256, 1>(); return true;
+    case 2562: *k = kern_for<256, 2>(); return true;
+    case 2564: *k = kern_for<256, 4>(); return true;
+    case 5121: *k = kern_for<512, 1>(); return true;
+    case 5122: *k = kern_for<512, 2>(); return true;
+    case 5124: *k = kern_for<512, 4>(); return true;
+    case 10241: *k = kern_for<1024, 1>(); return true;
+    case 10242: *k = kern_for<1024, 2>(); return true;
+    case 10244: *k = kern_for<1024, 4>(); return true;
     default: return false;
     }
 }
@@ -379,7 +268,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
     size_t off_dev, off_code, off_a0, off_a1, off_link, off_result;
-    size_t off_mt[7], off_me[4], off_trace, off_tvalid, off_gstack, off_blk, total;
+    size_t off_mt[8], off_me[4], off_trace, off_tvalid, off_gstack, off_blk, total;
 };
 
 Layout make_layout(size_t cap, size_t mcap, size_t trace_cap, size_t gstack_cap) {
@@ -396,7 +285,7 @@ Layout make_layout(size_t cap, size_t mcap, size_t trace_cap, size_t gstack_cap)
     L.off_a1 = take(cap * 4);
     L.off_link = take(cap * 4);
     L.off_result = take(cap * 8);
-    for (int i = 0; i < 7; ++i) L.off_mt[i] = take(mcap * 4);
+    for (int i = 0; i < 8; ++i) L.off_mt[i] = take(mcap * 4);
     for (int i = 0; i < 4; ++i) L.off_me[i] = take(mcap * 4);
     L.off_trace = take(trace_cap * sizeof(trees_epoch_t));
     L.off_tvalid = take(trace_cap * 4);
@@ -411,6 +300,7 @@ void normalize(trees_config_t *c) {
     if (c->max_epochs == 0) c->max_epochs = 1u << 20;
     if (c->trace_cap == 0) c->trace_cap = 65536;
     if (c->timeout_ns == 0) c->timeout_ns = 2000000000ull;
+    if (c->tasks_per_thread == 0) c->tasks_per_thread = 2;
 }
 
 }  // namespace
@@ -429,12 +319,14 @@ struct trees_ctx {
     int grid = 0, bs = 0;
     Kern kern{};
     cudaStream_t last_stream = nullptr;
+    int last_grid = 0;               // grid of the last persistent run
+    std::map<const void *, int> grid_cache;
     uint32_t *own_scratch = nullptr;
     size_t own_scratch_n = 0;
     // graph scheduler
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    cudaGraphNode_t gnode_epoch = nullptr, gnode_map = nullptr, gnode_p3 = nullptr;
+    cudaGraphNode_t gnode_epoch = nullptr, gnode_map = nullptr, gnode_p3 = nullptr, gnode_part = nullptr;
     cudaGraphConditionalHandle gh = 0;
     // host-loop scheduler
     std::vector<trees_epoch_t> host_trace;
@@ -464,6 +356,8 @@ void trees_default_config(trees_config_t *cfg) {
     cfg->timeout_ns = 2000000000ull;
     cfg->map_capacity = 0;
     cfg->inject_stall_epoch = -1;
+    cfg->grid_blocks = 0;
+    cfg->tasks_per_thread = 2;
 }
 
 static size_t bytes_for_cfg(size_t cap, const trees_config_t &c) {
@@ -484,10 +378,10 @@ static int finish_create(trees_ctx *x) {
     if (cudaGetDevice(&x->device) != cudaSuccess) return TREES_ERR_CUDA;
     if (cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, x->device) != cudaSuccess)
         return TREES_ERR_CUDA;
-    if (!kern_by_bs(x->cfg.block_size, &x->kern)) return TREES_ERR_INVALID_ARG;
+    if (!kern_by(x->cfg.block_size, x->cfg.tasks_per_thread, &x->kern)) return TREES_ERR_INVALID_ARG;
     x->bs = x->cfg.block_size;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, x->kern.persistent, x->bs, 0) != cudaSuccess || occ < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, x->kern.epoch, x->bs, 0) != cudaSuccess || occ < 1)
         return TREES_ERR_CUDA;
     int per_sm = x->cfg.blocks_per_sm > 0 ? std::min(x->cfg.blocks_per_sm, occ) : occ;
     x->grid = x->sms * per_sm;
@@ -503,8 +397,9 @@ static int finish_create(trees_ctx *x) {
     c.link = reinterpret_cast<uint32_t *>(m + L.off_link);
     c.result = reinterpret_cast<unsigned long long *>(m + L.off_result);
     c.cap = x->cap;
-    uint32_t **mt[7] = {&c.mt_kind, &c.mt_a, &c.mt_b, &c.mt_c, &c.mt_job, &c.mt_tilebase, &c.mt_tiledesc};
-    for (int i = 0; i < 7; ++i) *mt[i] = reinterpret_cast<uint32_t *>(m + L.off_mt[i]);
+    uint32_t **mt[8] = {&c.mt_kind, &c.mt_a,        &c.mt_b,        &c.mt_c,
+                         &c.mt_job,  &c.mt_tilebase, &c.mt_tiledesc, &c.mt_split};
+    for (int i = 0; i < 8; ++i) *mt[i] = reinterpret_cast<uint32_t *>(m + L.off_mt[i]);
     uint32_t **me[4] = {&c.me_v, &c.me_base, &c.me_job, &c.me_tfd};
     for (int i = 0; i < 4; ++i) *me[i] = reinterpret_cast<uint32_t *>(m + L.off_me[i]);
     c.mcap = x->mcap;
@@ -523,6 +418,20 @@ static int finish_create(trees_ctx *x) {
     return TREES_OK;
 }
 
+// Co-resident grid for a kernel under the context's limits (cached).
+static int kernel_grid(trees_ctx *x, const void *kern) {
+    if (!kern) return 0;
+    auto it = x->grid_cache.find(kern);
+    if (it != x->grid_cache.end()) return it->second;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, x->bs, 0) != cudaSuccess || occ < 1) return 0;
+    const int per_sm = x->cfg.blocks_per_sm > 0 ? std::min(x->cfg.blocks_per_sm, occ) : occ;
+    int g = x->sms * per_sm;
+    if (x->cfg.grid_blocks > 0) g = std::min(x->cfg.grid_blocks, x->sms * occ);
+    x->grid_cache[kern] = g;
+    return g;
+}
+
 static int validate_cfg(const trees_config_t *cfg, trees_config_t *out) {
     if (cfg) *out = *cfg;
     else trees_default_config(out);
@@ -530,6 +439,8 @@ static int validate_cfg(const trees_config_t *cfg, trees_config_t *out) {
     if (out->block_size != 256 && out->block_size != 512 && out->block_size != 1024) return TREES_ERR_INVALID_ARG;
     if (out->scheduler < TREES_SCHED_PERSISTENT || out->scheduler > TREES_SCHED_HOSTLOOP) return TREES_ERR_INVALID_ARG;
     if (out->blocks_per_sm < 0 || out->grid_blocks < 0) return TREES_ERR_INVALID_ARG;
+    if (out->tasks_per_thread != 1 && out->tasks_per_thread != 2 && out->tasks_per_thread != 4)
+        return TREES_ERR_INVALID_ARG;
     return TREES_OK;
 }
 
@@ -654,10 +565,14 @@ static int build_graph(trees_ctx *x) {
     kp.blockDim = dim3(x->bs);
     kp.kernelParams = ep_args;
     if (cudaGraphAddKernelNode(&x->gnode_epoch, body, nullptr, 0, &kp) != cudaSuccess) return TREES_ERR_CUDA;
+    void *part_args[] = {&x->ctl, &x->conf, &from_ctl, &zero};
+    kp.func = const_cast<void *>(x->kern.partition);
+    kp.kernelParams = part_args;
+    if (cudaGraphAddKernelNode(&x->gnode_part, body, &x->gnode_epoch, 1, &kp) != cudaSuccess) return TREES_ERR_CUDA;
     void *map_args[] = {&x->ctl, &x->conf, &from_ctl, &zero, &zero, &zero};
     kp.func = const_cast<void *>(x->kern.map);
     kp.kernelParams = map_args;
-    if (cudaGraphAddKernelNode(&x->gnode_map, body, &x->gnode_epoch, 1, &kp) != cudaSuccess) return TREES_ERR_CUDA;
+    if (cudaGraphAddKernelNode(&x->gnode_map, body, &x->gnode_part, 1, &kp) != cudaSuccess) return TREES_ERR_CUDA;
     void *p3_args[] = {&x->ctl, &x->conf, &x->gh};
     kp.func = (void *)k_phase3;
     kp.gridDim = dim3(1);
@@ -680,6 +595,10 @@ static int update_graph_args(trees_ctx *x) {
     kp.blockDim = dim3(x->bs);
     kp.kernelParams = ep_args;
     if (cudaGraphExecKernelNodeSetParams(x->gexec, x->gnode_epoch, &kp) != cudaSuccess) return TREES_ERR_CUDA;
+    void *part_args[] = {&x->ctl, &x->conf, &from_ctl, &zero};
+    kp.func = const_cast<void *>(x->kern.partition);
+    kp.kernelParams = part_args;
+    if (cudaGraphExecKernelNodeSetParams(x->gexec, x->gnode_part, &kp) != cudaSuccess) return TREES_ERR_CUDA;
     void *map_args[] = {&x->ctl, &x->conf, &from_ctl, &zero, &zero, &zero};
     kp.func = const_cast<void *>(x->kern.map);
     kp.kernelParams = map_args;
@@ -706,7 +625,8 @@ static int run_hostloop(trees_ctx *x, cudaStream_t st) {
     Ctl *h = x->pinned_ctl;
     for (;;) {
         const uint32_t ep = e % 3u;
-        const uint32_t nb = (hi - lo + x->bs - 1) / x->bs;
+        const uint32_t per = (uint32_t)x->bs * (uint32_t)x->cfg.tasks_per_thread;
+        const uint32_t nb = (hi - lo + per - 1) / per;
         void *args[] = {&x->ctl, &x->conf, &x->blk, nullptr, &cen, &lo, &hi, &base, &e};
         int from_ctl = 0;
         args[3] = &from_ctl;
@@ -719,6 +639,11 @@ static int run_hostloop(trees_ctx *x, cudaStream_t st) {
         }
         const unsigned long long mt = h->mt_ctr[ep], me = h->me_ctr[ep];
         if (mt | me) {  // mapScheduled: run the map kernel before the next epoch
+            if ((uint32_t)(mt & CTR_LOW_MASK) > (uint32_t)(mt >> 40)) {
+                void *pargs[] = {&x->ctl, &x->conf, &from_ctl, &e};
+                if (cudaLaunchKernel(x->kern.partition, dim3(x->grid), dim3(x->bs), pargs, 0, st) != cudaSuccess)
+                    return TREES_ERR_CUDA;
+            }
             void *margs[] = {&x->ctl, &x->conf, &from_ctl, &cen, &base, &e};
             if (cudaLaunchKernel(x->kern.map, dim3(x->grid), dim3(x->bs), margs, 0, st) != cudaSuccess)
                 return TREES_ERR_CUDA;
@@ -859,7 +784,11 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
     switch (x->cfg.scheduler) {
     case TREES_SCHED_PERSISTENT: {
         void *args[] = {&x->ctl, &x->conf, &x->blk};
-        if (cudaLaunchCooperativeKernel(x->kern.persistent, dim3(x->grid), dim3(x->bs), args, 0, st) != cudaSuccess) {
+        const void *kern = persistent_kernel(job->program, x->bs, x->cfg.tasks_per_thread);
+        const int grid = kernel_grid(x, kern);
+        if (!kern || grid < 1) return TREES_ERR_CUDA;
+        x->last_grid = grid;
+        if (cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(x->bs), args, 0, st) != cudaSuccess) {
             cudaGetLastError();
             return TREES_ERR_CUDA;
         }
@@ -920,6 +849,8 @@ int trees_stats(trees_ctx *x, trees_stats_t *out) {
     out->ns = h.t_end > h.t_start ? h.t_end - h.t_start : 0;
     out->status = h.err;
     out->error_epoch = (int32_t)h.err_epoch;
+    out->grid_blocks = x->last_sched == TREES_SCHED_PERSISTENT && x->last_grid ? x->last_grid : x->grid;
+    out->block_size = x->bs;
     return TREES_OK;
 }
 
@@ -999,7 +930,8 @@ int trees_barrier_floor(trees_ctx *x, uint32_t iters, void *stream, double *us) 
     void *args[] = {&x->ctl, &iters, &to};
     if (cudaMemsetAsync(x->ctl, 0, sizeof(Ctl), st) != cudaSuccess ||
         cudaEventRecord(a, st) != cudaSuccess ||
-        cudaLaunchCooperativeKernel(x->kern.floor, dim3(x->grid), dim3(x->bs), args, 0, st) != cudaSuccess ||
+        cudaLaunchCooperativeKernel(x->kern.floor, dim3(x->last_grid ? x->last_grid : x->grid), dim3(x->bs), args, 0,
+                                    st) != cudaSuccess ||
         cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
         cudaGetLastError();
         rc = TREES_ERR_CUDA;
@@ -1060,7 +992,7 @@ int noalloc_setup(int dev, NoallocDevice *d) {
     }
     int sms = 0, occ = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TREES_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k_persistent<1024>, 1024, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel_fib(1024, 2), 1024, 0) !=
             cudaSuccess || occ < 1)
         return TREES_ERR_CUDA;
     if (make_layout(NOALLOC_CAP, 1, 1, STK_CAP).total > NOALLOC_BYTES) return TREES_ERR_CUDA;
@@ -1102,8 +1034,9 @@ extern "C" int trees_fib_noalloc(uint32_t n, uint32_t cutoff, uint64_t *dev_resu
     c.link = reinterpret_cast<uint32_t *>(m0 + L.off_link);
     c.result = reinterpret_cast<unsigned long long *>(m0 + L.off_result);
     c.cap = (uint32_t)NOALLOC_CAP;
-    uint32_t **mt[7] = {&c.mt_kind, &c.mt_a, &c.mt_b, &c.mt_c, &c.mt_job, &c.mt_tilebase, &c.mt_tiledesc};
-    for (int i = 0; i < 7; ++i) *mt[i] = reinterpret_cast<uint32_t *>(m0 + L.off_mt[i]);
+    uint32_t **mt[8] = {&c.mt_kind, &c.mt_a,        &c.mt_b,        &c.mt_c,
+                         &c.mt_job,  &c.mt_tilebase, &c.mt_tiledesc, &c.mt_split};
+    for (int i = 0; i < 8; ++i) *mt[i] = reinterpret_cast<uint32_t *>(m0 + L.off_mt[i]);
     uint32_t **me[4] = {&c.me_v, &c.me_base, &c.me_job, &c.me_tfd};
     for (int i = 0; i < 4; ++i) *me[i] = reinterpret_cast<uint32_t *>(m0 + L.off_me[i]);
     c.mcap = 1;
@@ -1125,7 +1058,7 @@ extern "C" int trees_fib_noalloc(uint32_t n, uint32_t cutoff, uint64_t *dev_resu
     k_setup<<<1, 256, 0, st>>>(ctl, c, TREES_TASK_FIB, n, 0u);
     if (cudaGetLastError() != cudaSuccess) return TREES_ERR_CUDA;
     void *args[] = {&ctl, &c, &blk};
-    if (cudaLaunchCooperativeKernel((const void *)k_persistent<1024>, dim3(d->grid), dim3(1024), args, 0, st) !=
+    if (cudaLaunchCooperativeKernel(persistent_kernel_fib(1024, 2), dim3(d->grid), dim3(1024), args, 0, st) !=
         cudaSuccess) {
         cudaGetLastError();
         return TREES_ERR_CUDA;

@@ -17,6 +17,7 @@
 namespace trees {
 
 constexpr int BSTK = 64;  // range-stack entries per batched job
+constexpr uint32_t PM_BATCH = PM_FIB | PM_MS | PM_NQ | PM_TRAV;  // programs a batch may mix
 
 enum JobState : int32_t { JOB_FREE = 0, JOB_NEW = 1, JOB_ACTIVE = 2, JOB_DONE = 3 };
 
@@ -194,30 +195,34 @@ template <int BS>
 __device__ void batch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, Job *jobs, const uint32_t *joff, uint32_t nj,
                            uint32_t w, bool inr, Acc &acc) {
     const uint32_t NONE = 0xffffffffu;
-    Plan p;
-    p.type = 0u;
-    p.s = 0u;
-    p.a0 = p.a1 = 0u;
-    p.nfork = 0u;
-    p.mkind = p.ma = p.mb = p.mc = p.mtiles = 0u;
-    p.xv = p.xn = 0u;
+    Plan p[1];
+    p[0].s = 0u;
+    p[0].t = 0u;
+    p[0].n = 0u;
+    p[0].m = 0u;
+    p[0].a0 = p[0].a1 = 0u;
     uint32_t j = NONE, cen = 0u;
     Job *J = nullptr;
     if (inr) {
         j = find_job(joff, nj, w);
         J = &jobs[j];
         cen = J->cen;
-        p.s = J->lo + (w - joff[j]);
-        p.type = task_type(c.code[p.s], cen);
-        if (p.type) {
+        const uint32_t s = J->lo + (w - joff[j]);
+        p[0].s = s;
+        const uint32_t t = task_type(c.code[s], cen);
+        p[0].t = t;
+        if (t) {
             acc.valid++;
-            plan_task(c, J->rp, p, cen, J->epochs);
+            const uint32_t a0 = needs_a0(t) ? c.a0[s] : 0u, a1 = needs_a1(t) ? c.a1[s] : 0u;
+            const uint32_t lk = needs_link(t) ? c.link[s] : 0u;
+            plan_task<PM_BATCH>(c, J->rp, p[0], cen, J->epochs, a0, a1, lk);
         }
     }
+    const uint32_t nfork = forks_of(p[0]);
     // per-job fork allocation: one atomic per job per warp
     int end;
     uint32_t ftot;
-    const uint32_t excl = warp_seg_scan(j, p.nfork, &end, &ftot);
+    const uint32_t excl = warp_seg_scan(j, nfork, &end, &ftot);
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t b = 0u, over = 0u;
     if ((int)lane == end && j != NONE && ftot) {
@@ -230,12 +235,11 @@ __device__ void batch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, Job *jobs, con
     b = __shfl_sync(0xffffffffu, b, end);
     over = __shfl_sync(0xffffffffu, over, end);
     uint32_t joined = 0u;
-    if (p.nfork && !over) joined = commit_task(c, J->rp, p, cen, J->base + b + excl);
+    if (nfork && !over) joined = commit_task<PM_BATCH>(c, J->rp, p[0], cen, J->base + b + excl);
     acc.joins += joined;
     // per-job task and join counts
     uint32_t vt, jt;
-    const uint32_t v = p.type != 0u;
-    warp_seg_scan(j, v, &end, &vt);
+    warp_seg_scan(j, p[0].t != 0u, &end, &vt);
     warp_seg_scan(j, joined, &end, &jt);
     if ((int)lane == end && j != NONE) {
         if (vt) atomicAdd(&J->tasks, (unsigned long long)vt);
@@ -244,8 +248,8 @@ __device__ void batch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, Job *jobs, con
             J->join = 1u;
         }
     }
-    if (p.mtiles) atomicAdd(&J->maps, 1ull);
-    if (__syncthreads_or((p.mtiles | p.xn) != 0u)) map_alloc<BS>(c, ctl, sm, p, 0u, 0u, j, acc);
+    if (p[0].m) atomicAdd(&J->maps, 1ull);
+    if (__syncthreads_or(p[0].m != 0u)) map_alloc<BS, 1>(c, ctl, sm, p, cen, 0u, 0u, j, acc);
     __syncthreads();
 }
 
@@ -271,7 +275,11 @@ __global__ void __launch_bounds__(BS) k_batch(Ctl *ctl, Conf c, BatchCtl *bc, Jo
         if (!grid_sync<BS>(ctl, &bar, c.timeout_ns, sm)) break;
         const unsigned long long mt = vload(&ctl->mt_ctr[0]);
         if (mt) {
-            map_phase<BS>(c, ctl, sm, 0u, step, 0u, 0u, mt, 0ull, &jobs[0].rp, (uint32_t)sizeof(Job));
+            if (needs_partition(mt)) {
+                partition_phase<BS>(c, mt, &jobs[0].rp, (uint32_t)sizeof(Job));
+                if (!grid_sync<BS>(ctl, &bar, c.timeout_ns, sm)) break;
+            }
+            map_phase<BS, PM_BATCH>(c, ctl, sm, 0u, step, 0u, 0u, mt, 0ull, &jobs[0].rp, (uint32_t)sizeof(Job));
             if (!grid_sync<BS>(ctl, &bar, c.timeout_ns, sm)) break;
         }
     }

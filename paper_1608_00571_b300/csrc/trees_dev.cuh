@@ -24,7 +24,9 @@ constexpr uint32_t MERGE_TILE = 4096;           // outputs of one merge-path til
 constexpr uint32_t EXPAND_TILE = 4096;          // adjacency entries of one BFS expansion tile
 constexpr unsigned long long CTR_LOW_MASK = (1ull << 40) - 1;  // map counters: (descs << 40) | units
 
-enum MapKind : uint32_t { MAP_LEAF_SORT = 1, MAP_MERGE = 2 };
+enum MapKind : uint32_t { MAP_LEAF_SORT = 1, MAP_MERGE = 2, MAP_EXPAND = 3 };
+constexpr int TPT_MAX = 4;
+constexpr int NBLK_STATS = 8192;                // per-block statistics slots                      // largest number of slots a thread takes per tile
 
 struct Range {
     uint32_t cen, lo, hi;  // epoch number and NDRange [lo, hi) (Sec. 5.1.2)
@@ -48,7 +50,7 @@ struct Conf {
     unsigned long long *result;
     uint32_t cap;
     // tiled map list: one descriptor per map operation, `units` tiles each
-    uint32_t *mt_kind, *mt_a, *mt_b, *mt_c, *mt_job, *mt_tilebase, *mt_tiledesc;
+    uint32_t *mt_kind, *mt_a, *mt_b, *mt_c, *mt_job, *mt_tilebase, *mt_tiledesc, *mt_split;
     // element map list (BFS expansion): one descriptor per vertex, one unit per edge
     uint32_t *me_v, *me_base, *me_job, *me_tfd;
     uint32_t mcap;
@@ -133,12 +135,17 @@ struct Smem {
     static constexpr int NW = BS / 32;
     unsigned int w32[NW];
     unsigned int wflag[NW];
+    unsigned int wv[2][TPT_MAX][NW];  // vector scan words, double-buffered by tile parity
+    unsigned int wvf[2][NW];
+    unsigned int vflags[2];
     unsigned long long w64a[NW];
     unsigned long long w64b[NW];
     unsigned int flags;
     unsigned int bc32[4];
     unsigned long long bc64[4];
     int bar_ok;
+    unsigned int ep_cnt, ep_join;         // the epoch's counters, read right after its barrier
+    unsigned long long ep_mt, ep_me;
     // replicated epoch-range stack and scheduler state (persistent scheduler)
     Range stk[STK_CAP];
     int sp;
@@ -156,8 +163,8 @@ struct Smem {
             uint32_t v[EXPAND_TILE + 2];
         } ex;
         struct {
-            uint32_t toff[BS];   // tile offset of each tiled map request, by request rank
-            uint32_t di[BS];     // its descriptor index
+            uint32_t toff[BS * TPT_MAX];  // tile offset of each tiled map request, by request rank
+            uint32_t di[BS * TPT_MAX];    // its descriptor index
         } rq;
     } u;
 };
@@ -207,6 +214,43 @@ __device__ __forceinline__ uint32_t block_scan_u32(uint32_t v, int pred, uint32_
     *total = sm.w32[NW - 1];
     *any = (int)sm.flags;
     return (wid ? sm.w32[wid - 1] : 0u) + inc - v;
+}
+
+// Exclusive block scan of K values per thread at once (one scan per k), with
+// the block-wide OR of pred.  The shared words are double-buffered by `par`,
+// so consecutive tiles need no barrier between them.
+template <int BS, int K>
+__device__ __forceinline__ void block_scan_vec(const uint32_t (&v)[K], uint32_t (&ex)[K], uint32_t (&tot)[K], int pred,
+                                               int *any, Smem<BS> &sm, int par) {
+    constexpr int NW = BS / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) inc[k] = warp_incl_u32(v[k]);
+    const unsigned int bal = __ballot_sync(0xffffffffu, pred);
+    if (lane == 31) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) sm.wv[par][k][wid] = inc[k];
+    }
+    if (lane == 0) sm.wvf[par][wid] = bal != 0u;
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            uint32_t w = lane < NW ? sm.wv[par][k][lane] : 0u;
+            w = warp_incl_u32(w);
+            if (lane < NW) sm.wv[par][k][lane] = w;
+        }
+        const unsigned int f = __ballot_sync(0xffffffffu, lane < NW ? sm.wvf[par][lane] : 0u);
+        if (lane == 0) sm.vflags[par] = f != 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        tot[k] = sm.wv[par][k][NW - 1];
+        ex[k] = (wid ? sm.wv[par][k][wid - 1] : 0u) + inc[k] - v[k];
+    }
+    *any = (int)sm.vflags[par];
 }
 
 // Exclusive block scan of two u64 values at once.
@@ -272,6 +316,44 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, uint32_t *bar_idx, unsigned 
         fence_acq_rel();
         // one block-uniform decision: stop on a timeout or on any error raised before the barrier
         sm.bar_ok = ok && vload(&ctl->err) == 0;
+    }
+    __syncthreads();
+    return sm.bar_ok != 0;
+}
+
+// grid_sync, then (thread 0, same round trip) the counters of epoch slot ep
+// into shared memory: forks, joinScheduled and both map counters.
+template <int BS>
+__device__ __forceinline__ bool grid_sync_ep(Ctl *ctl, uint32_t *bar_idx, unsigned long long timeout_ns, Smem<BS> &sm,
+                                             uint32_t ep) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t idx = ++(*bar_idx);
+        const unsigned int target = idx * gridDim.x;
+        fence_acq_rel();
+        red_release_add(&ctl->bar_count, 1u);
+        int ok = 1;
+        uint32_t spins = 0;
+        uint64_t t0 = 0;
+        while ((int)(ld_acquire(&ctl->bar_count) - target) < 0) {
+            if ((++spins & 63u) == 0u) {
+                const uint64_t now = globaltimer();
+                if (t0 == 0) {
+                    t0 = now;
+                } else if (now - t0 > timeout_ns) {
+                    set_err(ctl, TREES_ERR_TIMEOUT, idx);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        fence_acq_rel();
+        const int err = vload(&ctl->err);
+        sm.ep_cnt = vload(&ctl->cnt[ep]);
+        sm.ep_join = vload(&ctl->join[ep]);
+        sm.ep_mt = vload(&ctl->mt_ctr[ep]);
+        sm.ep_me = vload(&ctl->me_ctr[ep]);
+        sm.bar_ok = ok && err == 0;
     }
     __syncthreads();
     return sm.bar_ok != 0;

@@ -1,0 +1,9 @@
+// Persistent epoch-loop kernels for one program (PM_TRAV), every block size and
+// slots-per-thread setting.
+#include "trees_kernels.cuh"
+
+namespace trees {
+
+const void *persistent_kernel_trav(int bs, int tpt) { return persistent_kernel_for<PM_TRAV>(bs, tpt); }
+
+}  // namespace trees

@@ -1,0 +1,181 @@
+// The persistent epoch-loop kernel, compiled once per program (see the
+// trees_k_*.cu translation units) so each kernel carries only its program's
+// task types and maps.
+#pragma once
+
+#include "trees_dev.cuh"
+#include "trees_programs.cuh"
+
+namespace trees {
+
+template <int BS>
+__device__ __forceinline__ void block_add_stats(unsigned long long *blk, const Acc &acc, Smem<BS> &sm) {
+    // block-reduce the per-thread counters, then one add per counter per block
+    const uint32_t v = __reduce_add_sync(0xffffffffu, acc.valid);
+    const uint32_t j = __reduce_add_sync(0xffffffffu, acc.joins);
+    const uint32_t m = __reduce_add_sync(0xffffffffu, acc.maps);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sm.bc64[0] = 0;
+        sm.bc64[1] = 0;
+        sm.bc64[2] = 0;
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sm.bc64[0], (unsigned long long)v);
+        atomicAdd(&sm.bc64[1], (unsigned long long)j);
+        atomicAdd(&sm.bc64[2], (unsigned long long)m);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long *b = blk + 4ull * (blockIdx.x % NBLK_STATS);
+        atomicAdd(b + 0, sm.bc64[0]);
+        atomicAdd(b + 1, sm.bc64[1]);
+        atomicAdd(b + 2, sm.bc64[2]);
+    }
+}
+
+template <int BS>
+__device__ __forceinline__ void trace_valid_add(const Conf &c, uint32_t e, uint32_t v, Smem<BS> &sm) {
+    if (!c.trace_on || e >= c.trace_cap) return;
+    const uint32_t w = __reduce_add_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(&c.trace_valid[e], w);
+}
+
+// The persistent scheduler: the whole epoch loop in one cooperative launch.
+template <int BS, int TPT, uint32_t PM>
+__global__ void __launch_bounds__(BS) k_persistent(Ctl *ctl, Conf c, unsigned long long *blk) {
+    __shared__ Smem<BS> sm;
+    uint32_t bar = 0;
+    Acc acc = {0u, 0u, 0u};
+    if (threadIdx.x == 0) {
+        sm.sp = 1;
+        sm.stk[0] = Range{0u, 0u, 1u};
+        sm.next = 1u;
+    }
+    unsigned long long forks_total = 0;
+    uint32_t peak = 1u;
+    uint32_t e = 0;
+    for (;; ++e) {
+        // Phase 1: pop (CEN, NDRange); oldNextFreeCore = nextFreeCore
+        if (threadIdx.x == 0) {
+            int stop = 0;
+            if (sm.sp == 0) {
+                stop = 1;
+            } else if (e >= c.max_epochs) {
+                stop = 2;
+                set_err(ctl, TREES_ERR_EPOCH_LIMIT, e);
+            } else {
+                const Range r = sm.stk[--sm.sp];
+                sm.cen = r.cen;
+                sm.lo = r.lo;
+                sm.hi = r.hi;
+                sm.base = sm.next;
+            }
+            sm.stop = stop;
+            if (!stop && blockIdx.x == 0) {  // clear the counters epoch e+1 will use
+                const uint32_t q = (e + 1u) % 3u;
+                ctl->cnt[q] = 0u;
+                ctl->join[q] = 0u;
+                ctl->mt_ctr[q] = 0ull;
+                ctl->me_ctr[q] = 0ull;
+            }
+        }
+        __syncthreads();
+        if (sm.stop) break;
+        const uint32_t cen = sm.cen, lo = sm.lo, hi = sm.hi, base = sm.base, ep = e % 3u;
+        // Phase 2: every entry of [lo, hi)
+        const uint32_t v0 = acc.valid;
+        int par = 0;
+        for (unsigned long long t0 = (unsigned long long)lo + (unsigned long long)blockIdx.x * (BS * TPT); t0 < hi;
+             t0 += (unsigned long long)gridDim.x * (BS * TPT)) {
+            epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par);
+            par ^= 1;
+        }
+        trace_valid_add<BS>(c, e, acc.valid - v0, sm);
+        if ((int32_t)e == c.stall_epoch && blockIdx.x == gridDim.x - 1) return;  // test hook: never arrives
+        if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, ep)) break;
+        const unsigned long long mt = sm.ep_mt, me = sm.ep_me;
+        if (mt | me) {  // the map operations of this epoch run before the next one (Sec. 5.2.4)
+            if constexpr ((PM & PM_MS) != 0u) {
+                if (needs_partition(mt)) {
+                    partition_phase<BS>(c, mt, nullptr, 0u);
+                    if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, ep)) break;
+                }
+            }
+            map_phase<BS, PM>(c, ctl, sm, ep, e, cen, base, mt, me);
+            if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, ep)) break;
+        }
+        // Phase 3: push the join range, then the fork range; or give the range back
+        if (threadIdx.x == 0) {
+            const uint32_t f = sm.ep_cnt, jf = sm.ep_join;
+            int ok = 1;
+            if (jf) {
+                if (sm.sp < STK_CAP) sm.stk[sm.sp++] = Range{cen, lo, hi};
+                else ok = 0;
+            }
+            if (f) {
+                if (sm.sp < STK_CAP) sm.stk[sm.sp++] = Range{cen + 1u, base, base + f};
+                else ok = 0;
+                sm.next = base + f;
+            } else if (!jf) {
+                sm.next = lo;  // neither forks nor joins: nextFreeCore decreases (Sec. 5.3)
+            }
+            if (!ok) {
+                if (blockIdx.x == 0) set_err(ctl, TREES_ERR_STACK, e);
+                sm.sp = 0;
+            }
+            if (blockIdx.x == 0) {
+                forks_total += f;
+                peak = max(peak, base + f);
+                if (c.trace_on && e < c.trace_cap) {
+                    trees_epoch_t r;
+                    r.cen = cen;
+                    r.lo = lo;
+                    r.hi = hi;
+                    r.valid = 0u;
+                    r.forks = f;
+                    r.joined = jf;
+                    r.maps = (uint32_t)(mt >> 40) + (uint32_t)(me >> 40);
+                    r.pad = 0u;
+                    r.t_ns = globaltimer();
+                    c.trace[e] = r;
+                }
+            }
+        }
+    }
+    block_add_stats<BS>(blk, acc, sm);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->epochs = e;
+        ctl->peak = peak;
+        ctl->final_next = sm.next;
+        ctl->forks = forks_total;
+        ctl->t_end = globaltimer();
+    }
+}
+
+// Returns k_persistent<BS, TPT, PM> for a runtime (bs, tpt), or nullptr.
+template <uint32_t PM>
+const void *persistent_kernel_for(int bs, int tpt) {
+    switch (bs * 10 + tpt) {
+    case 2561: return (const void *)k_persistent<256, 1, PM>;
+    case 2562: return (const void *)k_persistent<256, 2, PM>;
+    case 2564: return (const void *)k_persistent<256, 4, PM>;
+    case 5121: return (const void *)k_persistent<512, 1, PM>;
+    case 5122: return (const void *)k_persistent<512, 2, PM>;
+    case 5124: return (const void *)k_persistent<512, 4, PM>;
+    case 10241: return (const void *)k_persistent<1024, 1, PM>;
+    case 10242: return (const void *)k_persistent<1024, 2, PM>;
+    case 10244: return (const void *)k_persistent<1024, 4, PM>;
+    default: return nullptr;
+    }
+}
+
+// One definition per program, each in its own translation unit.
+const void *persistent_kernel_fib(int bs, int tpt);
+const void *persistent_kernel_ms(int bs, int tpt);
+const void *persistent_kernel_nq(int bs, int tpt);
+const void *persistent_kernel_bfs(int bs, int tpt);
+const void *persistent_kernel_trav(int bs, int tpt);
+
+}  // namespace trees

@@ -22,11 +22,25 @@ struct Acc {
     uint32_t valid, joins, maps;
 };
 
+// Program masks: which task types (and maps) a kernel is compiled for.  A
+// kernel built for one program carries only that program's dispatch cases,
+// as the paper's compiler emits one kernel per program (Sec. 5).
+constexpr uint32_t PM_FIB = 1u, PM_MS = 2u, PM_NQ = 4u, PM_BFS = 8u, PM_TRAV = 16u;
+constexpr uint32_t PM_ALL = PM_FIB | PM_MS | PM_NQ | PM_BFS | PM_TRAV;
+
+__host__ __device__ constexpr uint32_t program_mask(int program) {
+    return program == TREES_PROG_FIB         ? PM_FIB
+           : program == TREES_PROG_MERGESORT ? PM_MS
+           : program == TREES_PROG_NQUEENS   ? PM_NQ
+           : program == TREES_PROG_BFS       ? PM_BFS
+                                             : PM_TRAV;
+}
+
+// What one task decided in step 1: its slot, its type, how many children it
+// forks (or how many map units it schedules when m != 0) and the arguments
+// step 2 needs.
 struct Plan {
-    uint32_t type, s, a0, a1;
-    uint32_t nfork;
-    uint32_t mkind, ma, mb, mc, mtiles;  // tiled map request (leaf sort, merge)
-    uint32_t xv, xn;                     // element map request (BFS expansion)
+    uint32_t s, t, n, m, a0, a1;
 };
 
 // Leaf of the fib cutoff variant: the naive recursion run inside the task
@@ -54,194 +68,200 @@ __device__ __forceinline__ uint32_t nq_free(uint32_t a0, uint32_t a1, uint32_t n
     return ~((a0 & 0xFFFFu) | (a1 & 0xFFFFu) | (a1 >> 16)) & ((1u << n) - 1u);
 }
 
-// Step 1 of a task: read it, emit if it is a leaf, count forks, request maps.
-__device__ __forceinline__ void plan_task(const Conf &c, const RunParams &rp, Plan &p, uint32_t cen, uint32_t e) {
+// Which TV columns a task type reads besides its code.
+__device__ __forceinline__ bool needs_a0(uint32_t t) { return t != 0u && t != TREES_TASK_FIB_SUM; }
+__device__ __forceinline__ bool needs_a1(uint32_t t) {
+    return t == TREES_TASK_MS_SPLIT || t == TREES_TASK_MS_MERGE || t == TREES_TASK_NQ_ROW || t == TREES_TASK_NQ_SUM;
+}
+__device__ __forceinline__ bool needs_link(uint32_t t) { return t == TREES_TASK_FIB_SUM || t == TREES_TASK_NQ_SUM; }
+
+// Step 1 of a task: given its arguments, emit if it is a leaf (own-slot
+// writes, Sec. 4.3.2), count its forks, or request a map.  Only the task
+// types of the programs in PM are compiled in.
+template <uint32_t PM>
+__device__ __forceinline__ void plan_task(const Conf &c, const RunParams &rp, Plan &p, uint32_t cen, uint32_t e,
+                                          uint32_t a0, uint32_t a1, uint32_t lk) {
     const uint32_t s = p.s;
-    switch (p.type) {
-    case TREES_TASK_FIB: {
-        const uint32_t n = c.a0[s];
-        p.a0 = n;
-        if (n < 2u || n <= rp.cutoff) {
-            c.result[s] = n < 2u ? (unsigned long long)n : fib_leaf(n);
-            c.code[s] = 0u;  // emit: the entry is dead (Sec. 4.3.2)
-        } else {
-            p.nfork = 2u;
+    p.a0 = a0;
+    p.a1 = a1;
+    if constexpr ((PM & PM_FIB) != 0u) {
+        if (p.t == TREES_TASK_FIB) {
+            if (a0 < 2u || a0 <= rp.cutoff) {
+                c.result[s] = a0 < 2u ? (unsigned long long)a0 : fib_leaf(a0);
+                c.code[s] = 0u;  // emit: the entry is dead
+            } else {
+                p.n = 2u;
+            }
+            return;
         }
-        break;
+        if (p.t == TREES_TASK_FIB_SUM) {
+            c.result[s] = c.result[lk] + c.result[lk + 1];
+            c.code[s] = 0u;
+            return;
+        }
     }
-    case TREES_TASK_FIB_SUM: {
-        const uint32_t l = c.link[s];
-        c.result[s] = c.result[l] + c.result[l + 1];
-        c.code[s] = 0u;
-        break;
+    if constexpr ((PM & PM_MS) != 0u) {
+        if (p.t == TREES_TASK_MS_SPLIT) {
+            if (a1 - a0 <= rp.leaf) {
+                if (a1 > a0) {
+                    p.m = MAP_LEAF_SORT;
+                    p.n = 1u;
+                }
+                c.code[s] = 0u;
+            } else {
+                p.n = 2u;
+            }
+            return;
+        }
+        if (p.t == TREES_TASK_MS_MERGE) {
+            p.m = MAP_MERGE;
+            p.n = (a1 - a0 + MERGE_TILE - 1u) / MERGE_TILE;
+            c.code[s] = 0u;
+            return;
+        }
     }
-    case TREES_TASK_MS_SPLIT: {
-        const uint32_t lo = c.a0[s], hi = c.a1[s];
-        p.a0 = lo;
-        p.a1 = hi;
-        if (hi - lo <= rp.leaf) {
-            if (hi > lo) {
-                p.mkind = MAP_LEAF_SORT;
-                p.ma = lo;
-                p.mb = hi;
-                p.mc = cen;
-                p.mtiles = 1u;
+    if constexpr ((PM & PM_NQ) != 0u) {
+        if (p.t == TREES_TASK_NQ_ROW) {
+            if ((a0 >> 16) == rp.n) {
+                c.result[s] = 1ull;
+                c.code[s] = 0u;
+                return;
+            }
+            const uint32_t fr = nq_free(a0, a1, rp.n);
+            if (fr == 0u) {
+                c.result[s] = 0ull;
+                c.code[s] = 0u;
+            } else {
+                p.n = (uint32_t)__popc(fr);
+            }
+            return;
+        }
+        if (p.t == TREES_TASK_NQ_SUM) {
+            const uint32_t k = (uint32_t)__popc(nq_free(a0, a1, rp.n));
+            unsigned long long sum = 0;
+            for (uint32_t i = 0; i < k; ++i) sum += c.result[lk + i];
+            c.result[s] = sum;
+            c.code[s] = 0u;
+            return;
+        }
+    }
+    if constexpr ((PM & PM_BFS) != 0u) {
+        if (p.t == TREES_TASK_BFS_VISIT) {
+            const int32_t rb = __ldg(rp.row_ptr + a0), re = __ldg(rp.row_ptr + a0 + 1);
+            if (re > rb) {
+                p.m = MAP_EXPAND;
+                p.a0 = (uint32_t)rb;
+                p.n = (uint32_t)(re - rb);
             }
             c.code[s] = 0u;
-        } else {
-            p.nfork = 2u;
+            return;
         }
-        break;
     }
-    case TREES_TASK_MS_MERGE: {
-        const uint32_t lo = c.a0[s], hi = c.a1[s];
-        p.mkind = MAP_MERGE;
-        p.ma = lo;
-        p.mb = hi;
-        p.mc = cen;
-        p.mtiles = (hi - lo + MERGE_TILE - 1u) / MERGE_TILE;
-        c.code[s] = 0u;
-        break;
-    }
-    case TREES_TASK_NQ_ROW: {
-        const uint32_t a0 = c.a0[s], a1 = c.a1[s], n = rp.n;
-        p.a0 = a0;
-        p.a1 = a1;
-        if ((a0 >> 16) == n) {
-            c.result[s] = 1ull;
+    if constexpr ((PM & PM_TRAV) != 0u) {
+        if (p.t == TREES_TASK_PO) {
+            if ((int32_t)a0 < 0) c.code[s] = 0u;
+            else p.n = 2u;
+            return;
+        }
+        if (p.t == TREES_TASK_PO_AFTER) {
+            rp.visit_epoch[a0] = (int32_t)e;
             c.code[s] = 0u;
-            break;
+            return;
         }
-        const uint32_t fr = nq_free(a0, a1, n);
-        if (fr == 0u) {
-            c.result[s] = 0ull;
+        if (p.t == TREES_TASK_PRE) {
             c.code[s] = 0u;
-        } else {
-            p.nfork = (uint32_t)__popc(fr);
+            if ((int32_t)a0 >= 0) {
+                rp.visit_epoch[a0] = (int32_t)e;
+                p.n = 2u;
+            }
+            return;
         }
-        break;
-    }
-    case TREES_TASK_NQ_SUM: {
-        const uint32_t k = (uint32_t)__popc(nq_free(c.a0[s], c.a1[s], rp.n));
-        const uint32_t l = c.link[s];
-        unsigned long long sum = 0;
-        for (uint32_t i = 0; i < k; ++i) sum += c.result[l + i];
-        c.result[s] = sum;
-        c.code[s] = 0u;
-        break;
-    }
-    case TREES_TASK_BFS_VISIT: {
-        const uint32_t v = c.a0[s];
-        const int32_t rb = __ldg(rp.row_ptr + v), re = __ldg(rp.row_ptr + v + 1);
-        if (re > rb) {
-            p.xv = (uint32_t)rb;
-            p.xn = (uint32_t)(re - rb);
-        }
-        c.code[s] = 0u;
-        break;
-    }
-    case TREES_TASK_PO: {
-        const uint32_t node = c.a0[s];
-        p.a0 = node;
-        if ((int32_t)node < 0) c.code[s] = 0u;
-        else p.nfork = 2u;
-        break;
-    }
-    case TREES_TASK_PO_AFTER: {
-        rp.visit_epoch[c.a0[s]] = (int32_t)e;
-        c.code[s] = 0u;
-        break;
-    }
-    case TREES_TASK_PRE: {
-        const uint32_t node = c.a0[s];
-        p.a0 = node;
-        c.code[s] = 0u;
-        if ((int32_t)node >= 0) {
-            rp.visit_epoch[node] = (int32_t)e;
-            p.nfork = 2u;
-        }
-        break;
-    }
-    default:
-        break;
     }
 }
 
-// Step 2: write the children into [child, child + nfork) for epoch CEN+1 and
-// turn the task into its join continuation.  Returns 1 if it joined.
+__device__ __forceinline__ uint32_t forks_of(const Plan &p) { return p.m ? 0u : p.n; }
+
+// Step 2: write the children into [child, child + n) for epoch CEN+1 and turn
+// the task into its join continuation.  Returns 1 if it joined.
+template <uint32_t PM>
 __device__ __forceinline__ uint32_t commit_task(const Conf &c, const RunParams &rp, const Plan &p, uint32_t cen,
                                                  uint32_t child) {
     const uint32_t s = p.s;
     const uint32_t fe = enc(cen + 1u, 0u);
-    switch (p.type) {
-    case TREES_TASK_FIB:
-        c.code[child] = fe + TREES_TASK_FIB;
-        c.a0[child] = p.a0 - 1u;
-        c.code[child + 1] = fe + TREES_TASK_FIB;
-        c.a0[child + 1] = p.a0 - 2u;
-        c.link[s] = child;
-        c.code[s] = enc(cen, TREES_TASK_FIB_SUM);
-        return 1u;
-    case TREES_TASK_MS_SPLIT: {
-        const uint32_t lo = p.a0, hi = p.a1, mid = lo + (hi - lo) / 2u;
-        c.code[child] = fe + TREES_TASK_MS_SPLIT;
-        c.a0[child] = lo;
-        c.a1[child] = mid;
-        c.code[child + 1] = fe + TREES_TASK_MS_SPLIT;
-        c.a0[child + 1] = mid;
-        c.a1[child + 1] = hi;
-        c.link[s] = child;
-        c.code[s] = enc(cen, TREES_TASK_MS_MERGE);
-        return 1u;
-    }
-    case TREES_TASK_NQ_ROW: {
-        const uint32_t n = rp.n, mask = (1u << n) - 1u;
-        const uint32_t r = p.a0 >> 16, cols = p.a0 & 0xFFFFu, d1 = p.a1 & 0xFFFFu, d2 = p.a1 >> 16;
-        uint32_t fr = nq_free(p.a0, p.a1, n);
-        uint32_t slot = child;
-        while (fr) {
-            const uint32_t b = fr & (0u - fr);  // lowest safe column first
-            fr ^= b;
-            c.code[slot] = fe + TREES_TASK_NQ_ROW;
-            c.a0[slot] = (cols | b) | ((r + 1u) << 16);
-            c.a1[slot] = (((d1 | b) << 1) & mask) | (((d2 | b) >> 1) << 16);
-            ++slot;
+    if constexpr ((PM & PM_FIB) != 0u) {
+        if (p.t == TREES_TASK_FIB) {
+            c.code[child] = fe + TREES_TASK_FIB;
+            c.a0[child] = p.a0 - 1u;
+            c.code[child + 1] = fe + TREES_TASK_FIB;
+            c.a0[child + 1] = p.a0 - 2u;
+            c.link[s] = child;
+            c.code[s] = enc(cen, TREES_TASK_FIB_SUM);
+            return 1u;
         }
-        c.link[s] = child;
-        c.code[s] = enc(cen, TREES_TASK_NQ_SUM);
-        return 1u;
     }
-    case TREES_TASK_PO: {
-        const int32_t node = (int32_t)p.a0;
-        c.code[child] = fe + TREES_TASK_PO;
-        c.a0[child] = (uint32_t)__ldg(rp.right + node);
-        c.code[child + 1] = fe + TREES_TASK_PO;
-        c.a0[child + 1] = (uint32_t)__ldg(rp.left + node);
-        c.link[s] = child;
-        c.code[s] = enc(cen, TREES_TASK_PO_AFTER);
-        return 1u;
+    if constexpr ((PM & PM_MS) != 0u) {
+        if (p.t == TREES_TASK_MS_SPLIT) {
+            const uint32_t lo = p.a0, hi = p.a1, mid = lo + (hi - lo) / 2u;
+            c.code[child] = fe + TREES_TASK_MS_SPLIT;
+            c.a0[child] = lo;
+            c.a1[child] = mid;
+            c.code[child + 1] = fe + TREES_TASK_MS_SPLIT;
+            c.a0[child + 1] = mid;
+            c.a1[child + 1] = hi;
+            c.link[s] = child;
+            c.code[s] = enc(cen, TREES_TASK_MS_MERGE);
+            return 1u;
+        }
     }
-    case TREES_TASK_PRE: {
-        const int32_t node = (int32_t)p.a0;
-        c.code[child] = fe + TREES_TASK_PRE;
-        c.a0[child] = (uint32_t)__ldg(rp.right + node);
-        c.code[child + 1] = fe + TREES_TASK_PRE;
-        c.a0[child + 1] = (uint32_t)__ldg(rp.left + node);
-        return 0u;
+    if constexpr ((PM & PM_NQ) != 0u) {
+        if (p.t == TREES_TASK_NQ_ROW) {
+            const uint32_t n = rp.n, mask = (1u << n) - 1u;
+            const uint32_t r = p.a0 >> 16, cols = p.a0 & 0xFFFFu, d1 = p.a1 & 0xFFFFu, d2 = p.a1 >> 16;
+            uint32_t fr = nq_free(p.a0, p.a1, n);
+            uint32_t slot = child;
+            while (fr) {
+                const uint32_t b = fr & (0u - fr);  // lowest safe column first
+                fr ^= b;
+                c.code[slot] = fe + TREES_TASK_NQ_ROW;
+                c.a0[slot] = (cols | b) | ((r + 1u) << 16);
+                c.a1[slot] = (((d1 | b) << 1) & mask) | (((d2 | b) >> 1) << 16);
+                ++slot;
+            }
+            c.link[s] = child;
+            c.code[s] = enc(cen, TREES_TASK_NQ_SUM);
+            return 1u;
+        }
     }
-    default:
-        return 0u;
+    if constexpr ((PM & PM_TRAV) != 0u) {
+        if (p.t == TREES_TASK_PO || p.t == TREES_TASK_PRE) {
+            const int32_t node = (int32_t)p.a0;
+            c.code[child] = fe + p.t;
+            c.a0[child] = (uint32_t)__ldg(rp.right + node);
+            c.code[child + 1] = fe + p.t;
+            c.a0[child + 1] = (uint32_t)__ldg(rp.left + node);
+            if (p.t == TREES_TASK_PRE) return 0u;
+            c.link[s] = child;
+            c.code[s] = enc(cen, TREES_TASK_PO_AFTER);
+            return 1u;
+        }
     }
+    return 0u;
 }
 
 // Map allocation for one tile: one packed block scan per map list and one
-// atomic per list per block, then coalesced descriptor writes.  Tiled maps
-// also get a tile -> descriptor table, written cooperatively by the block.
-template <int BS>
-__device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan &p, uint32_t ep, uint32_t e,
-                          uint32_t job, Acc &acc) {
-    const unsigned long long qa = p.mtiles ? ((1ull << 40) | p.mtiles) : 0ull;
-    const unsigned long long qb = p.xn ? ((1ull << 40) | p.xn) : 0ull;
+// atomic per list per block, then the descriptor writes.  Tiled maps (leaf
+// sort, merge) also get a tile -> descriptor table, written cooperatively;
+// element maps (BFS expansion) record, for every expansion tile that starts
+// inside them, that they are the tile's first descriptor.
+template <int BS, int TPT>
+__device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan (&p)[TPT], uint32_t cen, uint32_t ep,
+                          uint32_t e, uint32_t job, Acc &acc) {
+    unsigned long long qa = 0ull, qb = 0ull;
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+        if (p[k].m == MAP_LEAF_SORT || p[k].m == MAP_MERGE) qa += (1ull << 40) | p[k].n;
+        else if (p[k].m == MAP_EXPAND) qb += (1ull << 40) | p[k].n;
+    }
     unsigned long long ea, eb, ta, tb;
     block_scan_u64x2<BS>(qa, qb, &ea, &eb, &ta, &tb, sm);
     if (threadIdx.x == 0) {
@@ -258,28 +278,32 @@ __device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan &p, 
         if (!fits) {
             if (threadIdx.x == 0) set_err(ctl, TREES_ERR_CAPACITY, e);
         } else {
-            if (p.mtiles) {
-                const uint32_t rank = (uint32_t)(ea >> 40), toff = (uint32_t)(ea & CTR_LOW_MASK);
+            uint32_t rank = (uint32_t)(ea >> 40), toff = (uint32_t)(ea & CTR_LOW_MASK);
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                if (p[k].m != MAP_LEAF_SORT && p[k].m != MAP_MERGE) continue;
                 const uint32_t di = dbase + rank;
-                c.mt_kind[di] = p.mkind;
-                c.mt_a[di] = p.ma;
-                c.mt_b[di] = p.mb;
-                c.mt_c[di] = p.mc;
+                c.mt_kind[di] = p[k].m;
+                c.mt_a[di] = p[k].a0;
+                c.mt_b[di] = p[k].a1;
+                c.mt_c[di] = cen;
                 c.mt_job[di] = job;
                 c.mt_tilebase[di] = tbase + toff;
                 sm.u.rq.toff[rank] = toff;
                 sm.u.rq.di[rank] = di;
                 acc.maps++;
+                ++rank;
+                toff += p[k].n;
             }
             __syncthreads();
-            for (uint32_t k = threadIdx.x; k < ntile; k += BS) {
-                uint32_t lo = 0, hi = ndesc;  // last request whose first tile is <= k
+            for (uint32_t t = threadIdx.x; t < ntile; t += BS) {
+                uint32_t lo = 0, hi = ndesc;  // last request whose first tile is <= t
                 while (hi - lo > 1u) {
                     const uint32_t mid = (lo + hi) >> 1;
-                    if (sm.u.rq.toff[mid] <= k) lo = mid;
+                    if (sm.u.rq.toff[mid] <= t) lo = mid;
                     else hi = mid;
                 }
-                c.mt_tiledesc[tbase + k] = sm.u.rq.di[lo];
+                c.mt_tiledesc[tbase + t] = sm.u.rq.di[lo];
             }
         }
     }
@@ -294,98 +318,194 @@ __device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan &p, 
                           tiles_end <= c.mcap;
         if (!fits) {
             if (threadIdx.x == 0) set_err(ctl, TREES_ERR_CAPACITY, e);
-        } else if (p.xn) {
-            const uint32_t di = dbase + (uint32_t)(eb >> 40);
-            const uint32_t b = (uint32_t)(ebase + (eb & CTR_LOW_MASK));
-            c.me_v[di] = p.xv;
-            c.me_base[di] = b;
-            c.me_job[di] = job;
-            // every expansion tile whose first element falls in [b, b + xn) starts at this descriptor
-            for (uint32_t t = (b + EXPAND_TILE - 1u) / EXPAND_TILE; t * EXPAND_TILE < b + p.xn; ++t) c.me_tfd[t] = di;
-            acc.maps++;
+        } else {
+            uint32_t di = dbase + (uint32_t)(eb >> 40);
+            uint32_t b = (uint32_t)(ebase + (eb & CTR_LOW_MASK));
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                if (p[k].m != MAP_EXPAND) continue;
+                c.me_v[di] = p[k].a0;
+                c.me_base[di] = b;
+                c.me_job[di] = job;
+                for (uint32_t t = (b + EXPAND_TILE - 1u) / EXPAND_TILE; t * EXPAND_TILE < b + p[k].n; ++t)
+                    c.me_tfd[t] = di;
+                acc.maps++;
+                ++di;
+                b += p[k].n;
+            }
         }
     }
+    __syncthreads();
 }
 
-// One Phase-2 tile: the slots [t0, t0 + BS) of the current range.
-template <int BS>
-__device__ __forceinline__ void epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t s, bool inr, uint32_t cen,
-                                           uint32_t base, uint32_t ep, uint32_t e, Acc &acc) {
-    Plan p;
-    p.type = 0u;
-    p.s = s;
-    p.a0 = p.a1 = 0u;
-    p.nfork = 0u;
-    p.mkind = p.ma = p.mb = p.mc = p.mtiles = 0u;
-    p.xv = p.xn = 0u;
-    if (inr) p.type = task_type(c.code[s], cen);  // invalid or stale entries exit at once (Sec. 5.3)
-    if (p.type) {
-        acc.valid++;
-        plan_task(c, c.rp, p, cen, e);
+// One Phase-2 tile: TPT * BS consecutive slots of the current range starting
+// at t0; slot t0 + k*BS + tid belongs to this thread.  All TV loads of the
+// tile are issued before any task runs, one vector scan hands every (k,
+// thread) its children's offset in k-major order (so the children of a warp
+// are written contiguously), and one atomic per block reserves them.
+template <int BS, int TPT, uint32_t PM>
+__device__ __forceinline__ void epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, unsigned long long t0, uint32_t hi,
+                                           uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, Acc &acc, int par) {
+    Plan p[TPT];
+    uint32_t a0v[TPT], a1v[TPT], lkv[TPT];
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+        const unsigned long long s = t0 + (unsigned long long)k * BS + threadIdx.x;
+        p[k].s = (uint32_t)s;
+        p[k].n = 0u;
+        p[k].m = 0u;
+        // invalid or stale entries exit at once (Sec. 5.3)
+        p[k].t = s < hi ? task_type(c.code[s], cen) : 0u;
     }
-    uint32_t ftot;
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+        const uint32_t s = p[k].s, t = p[k].t;
+        a0v[k] = needs_a0(t) ? c.a0[s] : 0u;
+        a1v[k] = needs_a1(t) ? c.a1[s] : 0u;
+        lkv[k] = needs_link(t) ? c.link[s] : 0u;
+    }
+    uint32_t nf[TPT];
+    int hasmap = 0;
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+        if (p[k].t) {
+            acc.valid++;
+            plan_task<PM>(c, c.rp, p[k], cen, e, a0v[k], a1v[k], lkv[k]);
+        }
+        nf[k] = forks_of(p[k]);
+        hasmap |= p[k].m != 0u;
+    }
+    uint32_t ex[TPT], tot[TPT];
     int anymap;
-    const uint32_t foff = block_scan_u32<BS>(p.nfork, (p.mtiles | p.xn) != 0u, &ftot, &anymap, sm);
-    if (ftot) {
+    block_scan_vec<BS, TPT>(nf, ex, tot, hasmap, &anymap, sm, par);
+    uint32_t all = 0;
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) all += tot[k];
+    if (all) {
         if (threadIdx.x == 0) {
-            const uint32_t b = atomicAdd(&ctl->cnt[ep], ftot);  // one atomic per block (Sec. 5.2.3)
-            const bool over = (unsigned long long)base + b + ftot > c.cap;
+            const uint32_t b = atomicAdd(&ctl->cnt[ep], all);  // one atomic per block (Sec. 5.2.3)
+            const bool over = (unsigned long long)base + b + all > c.cap;
             if (over) set_err(ctl, TREES_ERR_CAPACITY, e);
-            sm.bc32[0] = b;
-            sm.bc32[1] = over;
+            sm.bc32[par] = b;
+            sm.bc32[2 + par] = over;
         }
         __syncthreads();
         uint32_t joined = 0u;
-        if (!sm.bc32[1] && p.nfork) joined = commit_task(c, c.rp, p, cen, base + sm.bc32[0] + foff);
+        if (!sm.bc32[2 + par]) {
+            uint32_t kbase = base + sm.bc32[par];
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                if (nf[k]) joined += commit_task<PM>(c, c.rp, p[k], cen, kbase + ex[k]);
+                kbase += tot[k];
+            }
+        }
         acc.joins += joined;
-        if (__any_sync(0xffffffffu, joined) && (threadIdx.x & 31) == 0) ctl->join[ep] = 1u;  // joinScheduled
+        if (__any_sync(0xffffffffu, joined != 0u) && (threadIdx.x & 31) == 0) ctl->join[ep] = 1u;  // joinScheduled
     }
-    if (anymap) map_alloc<BS>(c, ctl, sm, p, ep, e, 0u, acc);
-    __syncthreads();
+    if constexpr ((PM & (PM_MS | PM_BFS)) != 0u) {
+        if (anymap) map_alloc<BS, TPT>(c, ctl, sm, p, cen, ep, e, 0u, acc);
+    }
 }
 
 // ------------------------------------------------------------------ map operations
 
-// Sorts keys in[lo, hi) (at most LEAF_MAX) in shared memory with a bitonic
-// network and writes them to out[lo, hi).
-template <int BS>
-__device__ void leaf_sort(const uint32_t *in, uint32_t *out, uint32_t lo, uint32_t hi, Smem<BS> &sm) {
-    const uint32_t n = hi - lo;
-    uint32_t P = 1u;
-    while (P < n) P <<= 1;
-    for (uint32_t i = threadIdx.x; i < P; i += BS) sm.u.sortk[i] = i < n ? in[lo + i] : 0xFFFFFFFFu;
-    __syncthreads();
-    for (uint32_t k = 2u; k <= P; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0u; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < P / 2u; i += BS) {
-                const uint32_t a = ((i & ~(j - 1u)) << 1) | (i & (j - 1u)), b = a + j;
-                const uint32_t x = sm.u.sortk[a], y = sm.u.sortk[b];
-                const bool up = (a & k) == 0u;
-                if ((x > y) == up) {
-                    sm.u.sortk[a] = y;
-                    sm.u.sortk[b] = x;
+// Sorts keys in[lo, hi) (at most 1024) ascending with one warp and writes them
+// to out[lo, hi); in == out is allowed.  Lane l ends up holding ranks
+// [32 l, 32 l + 32) in registers: each lane first sorts its own 32 keys with a
+// bitonic network in registers, then five bitonic merge levels join runs of
+// 32, 64, ..., 512 keys across lanes (a flip stage pairing rank p with
+// 2R-1-p, then half-cleaners), so no block barrier is needed.
+__device__ __forceinline__ void warp_leaf_sort(const uint32_t *in, uint32_t *out, uint32_t lo, uint32_t hi) {
+    const uint32_t lane = threadIdx.x & 31u, n = hi - lo;
+    uint32_t x[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        const uint32_t i = (uint32_t)r * 32u + lane;  // any input placement will do
+        x[r] = i < n ? in[lo + i] : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const int q = r ^ j;
+                if (q > r) {
+                    const uint32_t a = x[r], b = x[q], mn = min(a, b), mx = max(a, b);
+                    if ((r & k) == 0) {
+                        x[r] = mn;
+                        x[q] = mx;
+                    } else {
+                        x[r] = mx;
+                        x[q] = mn;
+                    }
                 }
             }
-            __syncthreads();
         }
     }
-    for (uint32_t i = threadIdx.x; i < n; i += BS) out[lo + i] = sm.u.sortk[i];
-    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const uint32_t span = 2u << m;  // lanes of a merged run
+        const bool lower = (lane & (span >> 1)) == 0u;
+        // flip: rank p meets rank 2R-1-p (lane ^ (span-1), register 31-r)
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const uint32_t ya = __shfl_xor_sync(0xffffffffu, x[31 - r], span - 1u);
+            const uint32_t yb = __shfl_xor_sync(0xffffffffu, x[r], span - 1u);
+            x[r] = lower ? min(x[r], ya) : max(x[r], ya);
+            x[31 - r] = lower ? min(x[31 - r], yb) : max(x[31 - r], yb);
+        }
+        // half-cleaners across lanes
+#pragma unroll
+        for (uint32_t jl = span >> 2; jl > 0u; jl >>= 1) {
+            const bool lo_lane = (lane & jl) == 0u;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const uint32_t y = __shfl_xor_sync(0xffffffffu, x[r], jl);
+                x[r] = lo_lane ? min(x[r], y) : max(x[r], y);
+            }
+        }
+        // half-cleaners inside the lane
+#pragma unroll
+        for (int j = 16; j > 0; j >>= 1) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const int q = r ^ j;
+                if (q > r) {
+                    const uint32_t a = x[r], b = x[q];
+                    x[r] = min(a, b);
+                    x[q] = max(a, b);
+                }
+            }
+        }
+    }
+    if (n == 1024u && ((lo & 3u) == 0u)) {
+        uint4 *o = reinterpret_cast<uint4 *>(out + lo + 32u * lane);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[q] = make_uint4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            const uint32_t i = 32u * lane + (uint32_t)r;
+            if (i < n) out[lo + i] = x[r];
+        }
+    }
 }
 
 // Merge path (Odeh et al., "Merge Path -- parallel merging made simple",
-// IPDPSW 2012): the number of A elements among the first `diag` outputs of
-// the stable merge of sorted A and B.  One warp probes 32 points per step.
-__device__ __forceinline__ uint32_t warp_merge_path(const uint32_t *A, uint32_t la, const uint32_t *B, uint32_t lb,
-                                                    uint32_t diag) {
+// IPDPSW 2012): the number of A elements among the first `diag` outputs of the
+// stable merge of sorted A and B.  A group of G lanes (gmask) probes G points
+// per step.
+template <int G>
+__device__ __forceinline__ uint32_t group_merge_path(const uint32_t *A, uint32_t la, const uint32_t *B, uint32_t lb,
+                                                     uint32_t diag, uint32_t gmask, uint32_t glane) {
     uint32_t lo = diag > lb ? diag - lb : 0u, hi = diag < la ? diag : la;
-    const uint32_t lane = threadIdx.x & 31u;
     while (hi > lo) {
-        const uint32_t step = (hi - lo + 31u) / 32u;
-        const uint32_t m = lo + lane * step;
+        const uint32_t step = (hi - lo + G - 1u) / G;
+        const uint32_t m = lo + glane * step;
         bool pr = false;
         if (m < hi) pr = A[m] <= B[diag - 1u - m];
-        const uint32_t cnt = (uint32_t)__popc(__ballot_sync(0xffffffffu, pr));
+        const uint32_t cnt = (uint32_t)__popc(__ballot_sync(gmask, pr) & gmask);
         const uint32_t nlo = cnt ? lo + (cnt - 1u) * step + 1u : lo;
         const uint32_t cap = lo + cnt * step;
         hi = cap < hi ? cap : hi;
@@ -394,24 +514,67 @@ __device__ __forceinline__ uint32_t warp_merge_path(const uint32_t *A, uint32_t 
     return lo;
 }
 
-// One merge-path tile of the merge of in[lo, mid) and in[mid, hi) into
-// out[lo, hi), mid = lo + (hi - lo) / 2: outputs [tile*T, tile*T + T).
+// The sorted runs a merge at depth d reads (depth d+1) and writes (depth d):
+// a node at depth d keeps its run in keys (d even) or scratch (d odd).
+struct MergeBufs {
+    const uint32_t *in;
+    uint32_t *out;
+};
+
+__device__ __forceinline__ void job_buffers(const Conf &c, const RunParams *job_params, uint32_t job_stride,
+                                            uint32_t job, uint32_t **keys, uint32_t **scratch) {
+    if (job_params) {
+        const RunParams *jp =
+            reinterpret_cast<const RunParams *>(reinterpret_cast<const char *>(job_params) + (size_t)job * job_stride);
+        *keys = jp->keys;
+        *scratch = jp->scratch;
+    } else {
+        *keys = c.rp.keys;
+        *scratch = c.rp.scratch;
+    }
+}
+
+// Partition sub-phase of a map epoch: the merge-path split at the first
+// output of every merge tile that does not start its merge, computed in
+// parallel by groups of 8 lanes for all tiles at once.
 template <int BS>
-__device__ void merge_tile(const uint32_t *in, uint32_t *out, uint32_t lo, uint32_t hi, uint32_t tile, Smem<BS> &sm) {
+__device__ void partition_phase(const Conf &c, unsigned long long mt, const RunParams *job_params, uint32_t job_stride) {
+    constexpr uint32_t G = 8;
+    const uint32_t nt1 = (uint32_t)(mt & CTR_LOW_MASK);
+    const uint32_t glane = threadIdx.x % G;
+    const uint32_t gmask = 0xFFu << ((threadIdx.x & 31u) & ~(G - 1u));
+    const uint32_t gid = (blockIdx.x * BS + threadIdx.x) / G, ng = gridDim.x * BS / G;
+    for (uint32_t t = gid; t < nt1; t += ng) {
+        const uint32_t di = c.mt_tiledesc[t];
+        if (c.mt_kind[di] != MAP_MERGE) continue;
+        const uint32_t tin = t - c.mt_tilebase[di];
+        if (tin == 0u) {
+            if (glane == 0u) c.mt_split[t] = 0u;
+            continue;
+        }
+        const uint32_t lo = c.mt_a[di], hi = c.mt_b[di], cc = c.mt_c[di], mid = lo + (hi - lo) / 2u;
+        uint32_t *keys, *scratch;
+        job_buffers(c, job_params, job_stride, c.mt_job[di], &keys, &scratch);
+        const uint32_t *in = (cc & 1u) ? keys : scratch;
+        const uint32_t r = group_merge_path<G>(in + lo, mid - lo, in + mid, hi - mid, tin * MERGE_TILE, gmask, glane);
+        if (glane == 0u) c.mt_split[t] = r;
+    }
+}
+
+// One merge-path tile of the merge of in[lo, mid) and in[mid, hi) into
+// out[lo, hi), mid = lo + (hi - lo) / 2: outputs [tile*T, tile*T + T), whose
+// first output takes i0 keys of the left run before it and whose end takes i1.
+template <int BS>
+__device__ void merge_tile(const uint32_t *in, uint32_t *out, uint32_t lo, uint32_t hi, uint32_t tile, uint32_t i0,
+                           uint32_t i1, Smem<BS> &sm) {
     const uint32_t mid = lo + (hi - lo) / 2u;
     const uint32_t *A = in + lo;
     const uint32_t *B = in + mid;
     const uint32_t la = mid - lo, lb = hi - mid, L = la + lb;
     const uint32_t d0 = tile * MERGE_TILE, d1 = min(d0 + MERGE_TILE, L);
-    const uint32_t wid = threadIdx.x >> 5;
-    if (wid < 2u) {
-        const uint32_t r = warp_merge_path(A, la, B, lb, wid == 0u ? d0 : d1);
-        if ((threadIdx.x & 31u) == 0u) sm.u.mg.split[wid] = r;
-    }
-    __syncthreads();
-    const uint32_t i0 = sm.u.mg.split[0], i1 = sm.u.mg.split[1];
     const uint32_t j0 = d0 - i0, j1 = d1 - i1;
     const uint32_t na = i1 - i0, nb = j1 - j0, nt = na + nb;
+    (void)la;
     uint32_t *sin = sm.u.mg.in;
     for (uint32_t k = threadIdx.x; k < na; k += BS) sin[k] = A[i0 + k];
     for (uint32_t k = threadIdx.x; k < nb; k += BS) sin[na + k] = B[j0 + k];
@@ -495,38 +658,51 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
     __syncthreads();
 }
 
-// The map phase of epoch e: every block takes tiles grid-stride over the
-// tiled list (leaf sorts, merge tiles) followed by the expansion tiles.
-template <int BS>
+// The map phase of epoch e, after the partition sub-phase: leaf sorts one
+// warp per leaf, merge tiles one block per tile, then the expansion tiles.
+template <int BS, uint32_t PM>
 __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, uint32_t e, uint32_t cen, uint32_t base,
                           unsigned long long mt, unsigned long long me, const RunParams *job_params = nullptr,
                           uint32_t job_stride = 0) {
     const uint32_t nt1 = (uint32_t)(mt & CTR_LOW_MASK);
     const uint32_t nd2 = (uint32_t)(me >> 40), ne2 = (uint32_t)(me & CTR_LOW_MASK);
     const uint32_t nt2 = (ne2 + EXPAND_TILE - 1u) / EXPAND_TILE;
-    uint32_t *keys = c.rp.keys, *scratch = c.rp.scratch;
-    for (uint32_t t = blockIdx.x; t < nt1 + nt2; t += gridDim.x) {
-        if (t < nt1) {
+    uint32_t *keys, *scratch;
+    if constexpr ((PM & PM_MS) != 0u) {
+      if (nt1) {
+        // leaves: one warp each
+        const uint32_t gw = (blockIdx.x * BS + threadIdx.x) >> 5, nw = gridDim.x * (BS / 32);
+        for (uint32_t t = gw; t < nt1; t += nw) {
             const uint32_t di = c.mt_tiledesc[t];
-            const uint32_t kind = c.mt_kind[di], a = c.mt_a[di], b = c.mt_b[di], cc = c.mt_c[di];
-            if (job_params) {  // batched runs: the descriptor names its job
-                const RunParams *jp = reinterpret_cast<const RunParams *>(
-                    reinterpret_cast<const char *>(job_params) + (size_t)c.mt_job[di] * job_stride);
-                keys = jp->keys;
-                scratch = jp->scratch;
-            }
-            // a node at depth d writes its sorted run to keys (d even) or scratch (d odd)
-            uint32_t *outb = (cc & 1u) ? scratch : keys;
-            if (kind == MAP_LEAF_SORT) {
-                leaf_sort<BS>(keys, outb, a, b, sm);
-            } else {
-                const uint32_t *inb = (cc & 1u) ? keys : scratch;
-                merge_tile<BS>(inb, outb, a, b, t - c.mt_tilebase[di], sm);
-            }
-        } else {
-            expand_tile<BS>(c, ctl, sm, t - nt1, nd2, ne2, nt2, cen, base, ep, e);
+            if (c.mt_kind[di] != MAP_LEAF_SORT) continue;
+            job_buffers(c, job_params, job_stride, c.mt_job[di], &keys, &scratch);
+            const uint32_t cc = c.mt_c[di];
+            warp_leaf_sort(keys, (cc & 1u) ? scratch : keys, c.mt_a[di], c.mt_b[di]);
         }
+        // merge tiles: one block each
+        for (uint32_t t = blockIdx.x; t < nt1; t += gridDim.x) {
+            const uint32_t di = c.mt_tiledesc[t];
+            if (c.mt_kind[di] != MAP_MERGE) continue;
+            job_buffers(c, job_params, job_stride, c.mt_job[di], &keys, &scratch);
+            const uint32_t lo = c.mt_a[di], hi = c.mt_b[di], cc = c.mt_c[di];
+            const uint32_t tin = t - c.mt_tilebase[di];
+            const uint32_t ntiles = (hi - lo + MERGE_TILE - 1u) / MERGE_TILE;
+            const uint32_t i0 = tin ? c.mt_split[t] : 0u;
+            const uint32_t i1 = tin + 1u < ntiles ? c.mt_split[t + 1u] : (hi - lo) / 2u;
+            merge_tile<BS>((cc & 1u) ? keys : scratch, (cc & 1u) ? scratch : keys, lo, hi, tin, i0, i1, sm);
+        }
+      }
     }
+    if constexpr ((PM & PM_BFS) != 0u) {
+        for (uint32_t t = blockIdx.x; t < nt2; t += gridDim.x)
+            expand_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e);
+    }
+}
+
+// True when some merge of the tiled list spans several tiles, so the
+// partition sub-phase has splits to compute.
+__device__ __forceinline__ bool needs_partition(unsigned long long mt) {
+    return (uint32_t)(mt & CTR_LOW_MASK) > (uint32_t)(mt >> 40);
 }
 
 }  // namespace trees

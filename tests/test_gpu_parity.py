@@ -58,9 +58,10 @@ def host_u32(t):
 
 @pytest.mark.parametrize("sched", SCHEDS)
 @pytest.mark.parametrize("bs", [256, 512, 1024])
-def test_fib20(sched, bs):
+@pytest.mark.parametrize("tpt", [1, 2, 4])
+def test_fib20(sched, bs, tpt):
     sim = oracle.tvm_run(oracle.FIB, fib_n=20)
-    with Ctx(1 << 16, scheduler=sched, block_size=bs, trace=1) as ctx:
+    with Ctx(1 << 16, scheduler=sched, block_size=bs, tasks_per_thread=tpt, trace=1) as ctx:
         assert run(ctx, T.make_job(T.TREES_PROG_FIB, n=20)) == T.TREES_OK
         assert T.trees_result(ctx, 0) == 6765
         st = T.trees_stats(ctx)
@@ -183,6 +184,29 @@ def test_bfs_rmat(scale):
         status, level = bfs_gpu(ctx, row_ptr, col, 0)
         assert status == T.TREES_OK
         assert np.array_equal(level, sim["level"])
+        check_trace(ctx, sim)
+
+
+@pytest.mark.parametrize("tpt", [1, 4])
+def test_all_programs_tasks_per_thread(tpt):
+    cfg = dict(tasks_per_thread=tpt, block_size=256, trace=1)
+    sim = oracle.tvm_run(oracle.NQUEENS, nq_n=9)
+    with Ctx(1 << 16, **cfg) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_NQUEENS, n=9)) == T.TREES_OK
+        assert T.trees_result(ctx, 0) == 352
+        check_trace(ctx, sim)
+    keys = gen.keys_u32(9, 300000)
+    sim = oracle.tvm_run(oracle.MERGESORT, keys=keys, leaf=100)
+    d = dev_u32(keys)
+    with Ctx(1 << 16, **cfg) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_MERGESORT, n=keys.size, keys=d, leaf=100)) == T.TREES_OK
+        assert np.array_equal(host_u32(d), sim["keys"])
+        check_trace(ctx, sim, TRACE_FIELDS + ("maps",))
+    row_ptr, col, _ = gen.rmat(14, 16, seed=3)
+    sim = oracle.tvm_run(oracle.BFS, row_ptr=row_ptr, col=col, src=0)
+    with Ctx(1 << 15, **cfg) as ctx:
+        status, level = bfs_gpu(ctx, row_ptr, col, 0)
+        assert status == T.TREES_OK and np.array_equal(level, sim["level"])
         check_trace(ctx, sim)
 
 
