@@ -42,6 +42,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="headline only (no secondary workloads / fit)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file for the autotuner's choices (default: tune afresh every run)")
     ap.add_argument("--profile-case", default=None,
                     help="PROGRAM:SIZE[:BLOCK] -- run one small case twice and exit (for ncu): "
                          "fib:N, sort:LOG2KEYS, bfs:RMAT_SCALE")
@@ -271,7 +273,7 @@ def vfit(T, torch, stream, sms):
             "points": len(ys), "P": "SMs used (1024-thread blocks, one per SM): 37, 74, 148"}
 
 
-def batch_and_serve(T, torch, np, gen, stream, bs):
+def batch_and_serve(T, torch, np, gen, stream):
     """The batched configuration: 4096 jobs (seed 42) in one persistent launch
     against one job per launch, then Poisson arrivals (seed 43) at 0.5x and
     0.9x of the batched throughput served by continuous batching and by one
@@ -298,20 +300,26 @@ def batch_and_serve(T, torch, np, gen, stream, bs):
         torch.cuda.synchronize()
 
     segs = [T.trees_job_slots(j)[0] for j in jobs]
-    cfg = T.trees_default_config(block_size=bs, map_capacity=1 << 22)
-    ctx = T.trees_create(sum(segs) + 1024, cfg)
     out = {}
-    times = []
-    for rep in range(3):
-        reset()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        T.trees_batch_run(ctx, jobs, segs, stream)
-        b.record(stream)
-        status, res, steps = T.trees_batch_results(ctx, 4096)
-        assert status == T.TREES_OK and all(r["status"] == T.TREES_OK for r in res)
-        times.append(a.elapsed_time(b))
-    T.trees_destroy(ctx)
+    best = None
+    for bs in (256, 512, 1024):  # the batch kernel's block size, tuned here
+        cfg_b = T.trees_default_config(block_size=bs, map_capacity=1 << 22)
+        ctx = T.trees_create(sum(segs) + 1024, cfg_b)
+        times = []
+        for rep in range(3):
+            reset()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            T.trees_batch_run(ctx, jobs, segs, stream)
+            b.record(stream)
+            status, res, steps = T.trees_batch_results(ctx, 4096)
+            assert status == T.TREES_OK and all(r["status"] == T.TREES_OK for r in res)
+            times.append(a.elapsed_time(b))
+        T.trees_destroy(ctx)
+        if best is None or min(times) < best[0]:
+            best = (min(times), bs, res, steps)
+    bms, bs, res, steps = best
+    cfg = T.trees_default_config(block_size=bs, map_capacity=1 << 22)
     # spot checks against closed forms / oracle
     nq = {}
     for i, r in enumerate(res):
@@ -323,10 +331,10 @@ def batch_and_serve(T, torch, np, gen, stream, bs):
     tasks = sum(r["tasks"] for r in res)
     bms = min(times)
     out["batched"] = {"jobs": 4096, "ms": bms, "jobs_per_s": 4096 / (bms / 1000), "steps": steps,
-                      "tasks": tasks, "tasks_per_s": tasks / (bms / 1000)}
+                      "tasks": tasks, "tasks_per_s": tasks / (bms / 1000), "block_size": bs}
     # one job per launch, back to back
     reset()
-    solo = T.trees_create(max(segs) + 1024, T.trees_default_config(block_size=bs))
+    solo = T.trees_create(max(segs) + 1024, T.trees_default_config(block_size=bs, map_capacity=1 << 22))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for j in jobs:
@@ -429,11 +437,19 @@ def main():
     hbm_peak, peak_kind = measured_peaks()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-    # ---------------- headline: fib(34), persistent scheduler
-    cfg = T.trees_default_config(block_size=1024)
-    ctx = T.trees_create(20_000_000, cfg)
-    grid, bs, sms = T.trees_geometry(ctx)
+    tuned = {}
+
+    def tune(job, cap, key, base=None):
+        best, ms, cands = T.trees_autotune(job, cap, base, 2, args.tune_cache, key)
+        tuned[key] = {"block_size": best.block_size, "tasks_per_thread": best.tasks_per_thread,
+                      "scheduler": ["persistent", "graph", "hostloop"][best.scheduler], "ms": ms,
+                      "candidates": len(cands)}
+        return best
+
+    # ---------------- headline: fib(34), autotuned configuration
     job = T.make_job(T.TREES_PROG_FIB, n=FIB_N)
+    cfg = tune(job, 20_000_000, f"fib:n={FIB_N}:cutoff=0", T.trees_default_config(map_capacity=1))
+    ctx = T.trees_create(20_000_000, cfg)
     timed_runs(T, torch, ctx, job, 0, args.warmup, stream, flush)
     clocks = ClockSampler(local)
     if dist is not None:
@@ -447,6 +463,8 @@ def main():
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     stats = T.trees_stats(ctx)
+    grid, bs = stats["grid_blocks"], stats["block_size"]
+    sms = T.trees_geometry(ctx)[2]
     result = T.trees_result(ctx, 0)
     assert result == 5702887, result
     total_ms = sum(times)
@@ -462,7 +480,7 @@ def main():
     T.trees_destroy(ctx)
 
     # per-epoch trace (counts are deterministic) for the algorithmic bytes
-    tctx = T.trees_create(20_000_000, T.trees_default_config(block_size=1024, trace=1))
+    tctx = T.trees_create(20_000_000, T.trees_default_config(block_size=1024, trace=1, map_capacity=1))
     T.trees_run(tctx, job, stream)
     assert T.trees_sync(tctx) == T.TREES_OK
     trace = T.trees_trace(tctx)
@@ -493,24 +511,27 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
         "config": {"workload": f"fib({FIB_N}) uint64 task tree, no sequential cutoff", "n": FIB_N, "cutoff": 0,
-                   "scheduler": "persistent", "block_size": bs, "grid_blocks": grid, "sms": sms,
+                   "scheduler": ["persistent", "graph", "hostloop"][cfg.scheduler], "block_size": bs,
+                   "tasks_per_thread": cfg.tasks_per_thread, "grid_blocks": grid, "sms": sms,
                    "l2": "flushed between steps (256 MiB device write)"},
         "us_per_epoch": us_epoch, "epochs": stats["epochs"], "tasks_per_step": tasks,
         "barrier_floor_us": floor_us, "epoch_over_floor": us_epoch / floor_us,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)",
-                     "algorithmic_bytes_per_launch": alg, "kernel": "k_persistent<1024>"},
+                     "algorithmic_bytes_per_launch": alg,
+                     "kernel": f"k_persistent<{bs},{cfg.tasks_per_thread},PM_FIB>"},
         "clocks": clk, "wall_s_timed_region": wall,
         "e2e": {"value": e2e_value, "unit": "tasks/s", "h2d_bytes_per_step": 12, "d2h_bytes_per_step": 8},
-        "gpu_launches": 2 * args.steps,
+        # per step: k_setup + the persistent kernel, or k_setup + 4 kernels per epoch in the graph
+        "gpu_launches": args.steps * (2 if cfg.scheduler == T.TREES_SCHED_PERSISTENT else 1 + 4 * stats["epochs"]),
     }
 
     if not args.quick:
         workloads = {}
         # fib(34) with a leaf cutoff of 12
-        c2 = T.trees_create(20_000_000, cfg)
         j2 = T.make_job(T.TREES_PROG_FIB, n=FIB_N, cutoff=12)
+        c2 = T.trees_create(200_000, tune(j2, 200_000, f"fib:n={FIB_N}:cutoff=12", T.trees_default_config(map_capacity=1)))
         t2 = timed_runs(T, torch, c2, j2, 10, 2, stream, flush)
         s2 = T.trees_stats(c2)
         assert T.trees_result(c2, 0) == 5702887
@@ -525,8 +546,9 @@ def main():
         src = torch.from_numpy(keys.view(np.int32)).cuda()
         kd = torch.empty_like(src)
         sc = torch.empty_like(src)
-        c3 = T.trees_create(1 << 18, cfg)
         j3 = T.make_job(T.TREES_PROG_MERGESORT, n=n, keys=kd, scratch=sc)
+        kd.copy_(src)
+        c3 = T.trees_create(1 << 18, tune(j3, 1 << 18, "mergesort:n=2^26"))
         t3 = timed_runs(T, torch, c3, j3, 5, 1, stream, None, setup=lambda: kd.copy_(src))
         s3 = T.trees_stats(c3)
         T.trees_destroy(c3)
@@ -546,8 +568,8 @@ def main():
         rp = torch.from_numpy(row_ptr).cuda()
         cl = torch.from_numpy(col).cuda()
         lv = torch.empty(row_ptr.size - 1, dtype=torch.int32, device="cuda")
-        c4 = T.trees_create(1 << 23, cfg)
         j4 = T.make_job(T.TREES_PROG_BFS, n=0, row_ptr=rp, col=cl, level=lv, nv=row_ptr.size - 1)
+        c4 = T.trees_create(1 << 23, tune(j4, 1 << 23, "bfs:rmat22"))
         t4 = timed_runs(T, torch, c4, j4, 5, 1, stream, flush)
         s4 = T.trees_stats(c4)
         T.trees_destroy(c4)
@@ -568,7 +590,9 @@ def main():
         # graph-relaunch and host-loop schedulers on the headline workload
         sch = {}
         for name, sid in (("graph", T.TREES_SCHED_GRAPH), ("hostloop", T.TREES_SCHED_HOSTLOOP)):
-            cx = T.trees_create(20_000_000, T.trees_default_config(block_size=1024, scheduler=sid))
+            cx = T.trees_create(20_000_000, T.trees_default_config(block_size=cfg.block_size, scheduler=sid,
+                                                                  tasks_per_thread=cfg.tasks_per_thread,
+                                                                  map_capacity=1))
             tt = timed_runs(T, torch, cx, job, 5, 1, stream, flush)
             T.trees_destroy(cx)
             mm = statistics.mean(tt)
@@ -576,7 +600,8 @@ def main():
         sch["persistent"] = {"ms": ms_step, "us_per_epoch": us_epoch, "tasks_per_s": tasks / (ms_step / 1000)}
         line["schedulers"] = sch
         line["vfit"] = vfit(T, torch, stream, sms)
-        line["batch_serve"] = batch_and_serve(T, torch, np, gen, stream, 512)
+        line["batch_serve"] = batch_and_serve(T, torch, np, gen, stream)
+    line["autotune"] = tuned
 
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

@@ -198,6 +198,29 @@ int trees_bfs(trees_ctx *ctx, const int32_t *dev_row_ptr, const int32_t *dev_col
  * per barrier in microseconds. */
 int trees_barrier_floor(trees_ctx *ctx, uint32_t iters, void *stream, double *us_per_barrier);
 
+/* ------------------------------------------------------------ autotuning */
+typedef struct {
+    trees_config_t cfg;  /* the candidate configuration */
+    double ms;           /* its best time over the timed runs (device, CUDA events) */
+    int32_t status;      /* TREES_OK, or why the candidate could not run */
+    int32_t pad;
+} trees_tune_entry_t;
+
+/* Picks the configuration that runs `job` fastest on the current device:
+ * every block size {256, 512, 1024} x slots per thread {1, 2, 4} x scheduler
+ * {persistent grid barrier, CUDA-graph relaunch}, each on a fresh context of
+ * capacity_slots slots built from `base` (NULL = defaults), one warm-up and
+ * `reps` timed runs.  A mergesort job's keys are restored from a copy before
+ * every run.  With cache_path and key non-NULL the choice is looked up in and
+ * written to a JSON file mapping keys to configurations (a cached key costs
+ * no runs).  *best receives the configuration, *best_ms its time; up to
+ * table_cap candidates are reported in table (may be NULL), *table_n how many.
+ * Errors: INVALID_ARG, CUDA, or the job's own status when every candidate
+ * fails. */
+int trees_autotune(const trees_job_t *job, size_t capacity_slots, const trees_config_t *base, int32_t reps,
+                   const char *cache_path, const char *key, trees_config_t *best, double *best_ms,
+                   trees_tune_entry_t *table, int32_t table_cap, int32_t *table_n);
+
 /* ------------------------------------------------------------ batches and serving
  * Many independent task trees share one persistent launch (work-together
  * Tenet 1, Sec. 3, applied across jobs): each job owns a segment of the task

@@ -90,6 +90,10 @@ class trees_job_result_t(ctypes.Structure):
         return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "pad"}
 
 
+class trees_tune_entry_t(ctypes.Structure):
+    _fields_ = [("cfg", trees_config_t), ("ms", ctypes.c_double), ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _ctxp = ctypes.c_void_p
@@ -117,6 +121,10 @@ _SIGNATURES = [
     ("trees_bfs", ctypes.c_int, [_ctxp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
     ("trees_barrier_floor", ctypes.c_int, [_ctxp, ctypes.c_uint32, _vp, ctypes.POINTER(ctypes.c_double)]),
     ("trees_fib_noalloc", ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, _vp, _vp, _vp]),
+    ("trees_autotune", ctypes.c_int, [ctypes.POINTER(trees_job_t), ctypes.c_size_t, ctypes.POINTER(trees_config_t),
+                                      ctypes.c_int32, ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(trees_config_t),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(trees_tune_entry_t),
+                                      ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     ("trees_job_slots", ctypes.c_uint64, [ctypes.POINTER(trees_job_t), ctypes.POINTER(ctypes.c_int32)]),
     ("trees_batch_run", ctypes.c_int, [_ctxp, ctypes.POINTER(trees_job_t), ctypes.POINTER(ctypes.c_uint64),
                                        ctypes.c_int32, _vp]),
@@ -294,6 +302,24 @@ def trees_fib_noalloc(n: int, cutoff: int, dev_result, dev_status, stream=None) 
     buffers ``dev_result`` (uint64) and ``dev_status`` (int32).  Returns the
     host-side status; raises only through the caller's own checks."""
     return int(lib().trees_fib_noalloc(n, cutoff, _ptr(dev_result), _ptr(dev_status), _stream(stream)))
+
+
+def trees_autotune(job: trees_job_t, capacity_slots: int, base: trees_config_t | None = None, reps: int = 3,
+                   cache_path: str | None = None, key: str | None = None):
+    """``(best config, best ms, [candidate dicts])``."""
+    best = trees_config_t()
+    ms = ctypes.c_double()
+    cap = 32
+    table = (trees_tune_entry_t * cap)()
+    n = ctypes.c_int32()
+    _check("trees_autotune", lib().trees_autotune(
+        ctypes.byref(job), capacity_slots, ctypes.byref(base) if base else None, reps,
+        cache_path.encode() if cache_path else None, key.encode() if key else None, ctypes.byref(best),
+        ctypes.byref(ms), table, cap, ctypes.byref(n)))
+    cands = [{"block_size": table[i].cfg.block_size, "tasks_per_thread": table[i].cfg.tasks_per_thread,
+              "scheduler": table[i].cfg.scheduler, "ms": table[i].ms, "status": table[i].status}
+             for i in range(n.value)]
+    return best, float(ms.value), cands
 
 
 def trees_job_slots(job: trees_job_t):

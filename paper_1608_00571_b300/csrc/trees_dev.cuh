@@ -20,7 +20,8 @@ namespace trees {
 constexpr uint32_t NTT = TREES_NUM_TASK_TYPES;  // NumTaskTypes of footnote 2, Sec. 5.1.2
 constexpr int STK_CAP = 512;                    // epoch-range stack entries per job
 constexpr int LEAF_MAX = 1024;                  // largest leaf a block sorts in shared memory
-constexpr uint32_t MERGE_TILE = 4096;           // outputs of one merge-path tile
+constexpr uint32_t MERGE_TILE = 2048;           // outputs of one merge-path tile
+constexpr uint32_t MERGE_BUF = 2 * MERGE_TILE + 8; // keys of one staged tile: A run, 16-B gap, B run
 constexpr uint32_t EXPAND_TILE = 4096;          // adjacency entries of one BFS expansion tile
 constexpr unsigned long long CTR_LOW_MASK = (1ull << 40) - 1;  // map counters: (descs << 40) | units
 
@@ -144,6 +145,7 @@ struct Smem {
     unsigned int bc32[4];
     unsigned long long bc64[4];
     int bar_ok;
+    unsigned long long mbar[2];           // mbarriers of the two merge buffers
     unsigned int ep_cnt, ep_join;         // the epoch's counters, read right after its barrier
     unsigned long long ep_mt, ep_me;
     // replicated epoch-range stack and scheduler state (persistent scheduler)
@@ -151,13 +153,8 @@ struct Smem {
     int sp;
     uint32_t next, cen, lo, hi, base;
     int stop;
-    union {
-        uint32_t sortk[LEAF_MAX];
-        struct {
-            uint32_t in[MERGE_TILE];
-            uint32_t out[MERGE_TILE];
-            uint32_t split[2];
-        } mg;
+    union alignas(16) {
+        uint32_t mg[2][MERGE_BUF];  // double-buffered merge tile inputs (TMA destinations)
         struct {
             uint32_t base[EXPAND_TILE + 2];
             uint32_t v[EXPAND_TILE + 2];
@@ -319,6 +316,58 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, uint32_t *bar_idx, unsigned 
     }
     __syncthreads();
     return sm.bar_ok != 0;
+}
+
+// ------------------------------------------------------------------ TMA bulk copies
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Arrive once and announce `bytes` of asynchronous copies on this phase.
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false if it timed out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, unsigned long long timeout_ns) {
+    const uint32_t a = smem_addr(bar);
+    uint64_t t0 = 0;
+    for (uint32_t spin = 0;; ++spin) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((spin & 15u) == 15u) {
+            const uint64_t now = globaltimer();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > timeout_ns) return false;
+        }
+    }
+}
+
+// One-dimensional bulk copy global -> shared (16-byte aligned, multiple of
+// 16 bytes), completing on `bar`.
+__device__ __forceinline__ void tma_load_1d(void *dst_smem, const void *src, uint32_t bytes, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // grid_sync, then (thread 0, same round trip) the counters of epoch slot ep

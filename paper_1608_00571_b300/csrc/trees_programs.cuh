@@ -561,41 +561,138 @@ __device__ void partition_phase(const Conf &c, unsigned long long mt, const RunP
     }
 }
 
-// One merge-path tile of the merge of in[lo, mid) and in[mid, hi) into
-// out[lo, hi), mid = lo + (hi - lo) / 2: outputs [tile*T, tile*T + T), whose
-// first output takes i0 keys of the left run before it and whose end takes i1.
+// One merge tile, resolved: the merge of in[lo, mid) (A) and in[mid, hi) (B)
+// into out[lo, hi) has output tile [d0, d0 + T); it reads A[i0, i1) and
+// B[j0, j1) (indices relative to the runs).
+struct MergeTile {
+    const uint32_t *in;
+    uint32_t *out;
+    uint32_t lo, mid, d0, i0, i1, j0, j1;
+};
+
+// The next merge tile at or after t in steps of gridDim.x (false when none).
+__device__ __forceinline__ bool next_merge_tile(const Conf &c, uint32_t &t, uint32_t nt1, const RunParams *jp,
+                                                uint32_t js, MergeTile &m) {
+    for (; t < nt1; t += gridDim.x) {
+        const uint32_t di = c.mt_tiledesc[t];
+        if (c.mt_kind[di] != MAP_MERGE) continue;
+        uint32_t *keys, *scratch;
+        job_buffers(c, jp, js, c.mt_job[di], &keys, &scratch);
+        const uint32_t lo = c.mt_a[di], hi = c.mt_b[di], cc = c.mt_c[di];
+        const uint32_t tin = t - c.mt_tilebase[di];
+        const uint32_t la = (hi - lo) / 2u, L = hi - lo, ntiles = (L + MERGE_TILE - 1u) / MERGE_TILE;
+        m.in = (cc & 1u) ? keys : scratch;   // the children's runs (depth d+1)
+        m.out = (cc & 1u) ? scratch : keys;  // this node's run (depth d)
+        m.lo = lo;
+        m.mid = lo + la;
+        m.d0 = tin * MERGE_TILE;
+        m.i0 = tin ? c.mt_split[t] : 0u;
+        m.i1 = tin + 1u < ntiles ? c.mt_split[t + 1u] : la;
+        m.j0 = m.d0 - m.i0;
+        m.j1 = min(m.d0 + MERGE_TILE, L) - m.i1;
+        return true;
+    }
+    return false;
+}
+
+// Starts staging a tile into buf: thread 0 issues the bulk copies of the
+// 16-byte aligned middle of each run (TMA, completing on bar); every thread
+// loads its share of the unaligned ends.  A lands at buf[0..), B at
+// buf[T + 4 ..), each shifted by its start's offset within 16 bytes.
 template <int BS>
-__device__ void merge_tile(const uint32_t *in, uint32_t *out, uint32_t lo, uint32_t hi, uint32_t tile, uint32_t i0,
-                           uint32_t i1, Smem<BS> &sm) {
-    const uint32_t mid = lo + (hi - lo) / 2u;
-    const uint32_t *A = in + lo;
-    const uint32_t *B = in + mid;
-    const uint32_t la = mid - lo, lb = hi - mid, L = la + lb;
-    const uint32_t d0 = tile * MERGE_TILE, d1 = min(d0 + MERGE_TILE, L);
-    const uint32_t j0 = d0 - i0, j1 = d1 - i1;
-    const uint32_t na = i1 - i0, nb = j1 - j0, nt = na + nb;
-    (void)la;
-    uint32_t *sin = sm.u.mg.in;
-    for (uint32_t k = threadIdx.x; k < na; k += BS) sin[k] = A[i0 + k];
-    for (uint32_t k = threadIdx.x; k < nb; k += BS) sin[na + k] = B[j0 + k];
-    __syncthreads();
+__device__ __forceinline__ void merge_stage(const MergeTile &m, uint32_t *buf, unsigned long long *bar) {
+    const uint32_t as = m.lo + m.i0, ae = m.lo + m.i1, bs = m.mid + m.j0, be = m.mid + m.j1;
+    const uint32_t as4 = as & ~3u, ae4 = ae & ~3u, bs4 = bs & ~3u, be4 = be & ~3u;
+    uint32_t *sb = buf + MERGE_TILE + 4u;
+    const bool aligned = (reinterpret_cast<uintptr_t>(m.in) & 15u) == 0u;  // else plain loads only
+    const uint32_t abytes = aligned && ae4 > as4 ? (ae4 - as4) * 4u : 0u;
+    const uint32_t bbytes = aligned && be4 > bs4 ? (be4 - bs4) * 4u : 0u;
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();  // earlier generic reads of buf come before the async writes
+        mbar_arrive_expect(bar, abytes + bbytes);
+        if (abytes) tma_load_1d(buf, m.in + as4, abytes, bar);
+        if (bbytes) tma_load_1d(sb, m.in + bs4, bbytes, bar);
+    }
+    for (uint32_t x = (abytes ? ae4 : as) + threadIdx.x; x < ae; x += BS) buf[x - as4] = m.in[x];
+    for (uint32_t x = (bbytes ? be4 : bs) + threadIdx.x; x < be; x += BS) sb[x - bs4] = m.in[x];
+}
+
+// Merges a staged tile: each thread finds its first output's merge-path split
+// in shared memory, merges MPT outputs in registers and stores them with one
+// vector store when aligned.
+template <int BS>
+__device__ __forceinline__ void merge_compute(const MergeTile &m, const uint32_t *buf) {
     constexpr uint32_t MPT = MERGE_TILE / BS;
-    const uint32_t dd = min(threadIdx.x * MPT, nt);
+    const uint32_t na = m.i1 - m.i0, nb = m.j1 - m.j0, nt = na + nb;
+    const uint32_t *sa = buf + ((m.lo + m.i0) & 3u);
+    const uint32_t *sb = buf + MERGE_TILE + 4u + ((m.mid + m.j0) & 3u);
+    const uint32_t dd = min((uint32_t)threadIdx.x * MPT, nt);
     uint32_t a = dd > nb ? dd - nb : 0u, b = dd < na ? dd : na;
     while (a < b) {
-        const uint32_t m = (a + b) >> 1;
-        if (sin[m] <= sin[na + dd - 1u - m]) a = m + 1u;
-        else b = m;
+        const uint32_t mid = (a + b) >> 1;
+        if (sa[mid] <= sb[dd - 1u - mid]) a = mid + 1u;
+        else b = mid;
     }
     uint32_t ia = a, ib = dd - a;
-    const uint32_t dend = min(dd + MPT, nt);
-    for (uint32_t o = dd; o < dend; ++o) {
-        const bool takeA = ia < na && (ib >= nb || sin[ia] <= sin[na + ib]);
-        sm.u.mg.out[o] = takeA ? sin[ia++] : sin[na + ib++];
+    uint32_t v[MPT];
+#pragma unroll
+    for (uint32_t k = 0; k < MPT; ++k) {
+        const bool takeA = ia < na && (ib >= nb || sa[ia] <= sb[ib]);
+        v[k] = takeA ? sa[ia] : sb[ib];
+        ia += takeA;
+        ib += !takeA;
+    }
+    uint32_t *o = m.out + m.lo + m.d0 + dd;
+    const uint32_t cnt = min(MPT, nt - dd);
+    if constexpr (MPT % 4u == 0u) {
+        if (cnt == MPT && ((reinterpret_cast<uintptr_t>(o) & 15u) == 0u)) {
+#pragma unroll
+            for (uint32_t q = 0; q < MPT / 4u; ++q)
+                reinterpret_cast<uint4 *>(o)[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            return;
+        }
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < MPT; ++k)
+        if (k < cnt) o[k] = v[k];
+}
+
+// All merge tiles of the epoch handled by this block, two-stage pipelined:
+// while the block merges one tile from shared memory, the next tile's runs
+// stream in by TMA.  Waits are bounded (TREES_ERR_TIMEOUT).
+template <int BS>
+__device__ void merge_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t nt1, const RunParams *jp, uint32_t js) {
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.mbar[0], 1u);
+        mbar_init(&sm.mbar[1], 1u);
     }
     __syncthreads();
-    for (uint32_t k = threadIdx.x; k < nt; k += BS) out[lo + d0 + k] = sm.u.mg.out[k];
+    uint32_t par0 = 0u, par1 = 0u;
+    uint32_t t = blockIdx.x, b = 0u;
+    MergeTile cur, nxt;
+    bool have = next_merge_tile(c, t, nt1, jp, js, cur);
+    if (have) merge_stage<BS>(cur, sm.u.mg[0], &sm.mbar[0]);
     __syncthreads();
+    while (have) {
+        uint32_t tn = t + gridDim.x;
+        const bool hn = next_merge_tile(c, tn, nt1, jp, js, nxt);
+        if (hn) merge_stage<BS>(nxt, sm.u.mg[b ^ 1u], &sm.mbar[b ^ 1u]);
+        const uint32_t par = b ? par1 : par0;
+        if (!mbar_wait(&sm.mbar[b], par, c.timeout_ns)) {
+            set_err(ctl, TREES_ERR_TIMEOUT, 0u);
+            if (hn) mbar_wait(&sm.mbar[b ^ 1u], b ? par0 : par1, c.timeout_ns);  // let the other copy land
+            __syncthreads();
+            return;
+        }
+        if (b) par1 ^= 1u;
+        else par0 ^= 1u;
+        merge_compute<BS>(cur, sm.u.mg[b]);
+        __syncthreads();  // buffer b is free again; the tails staged for b^1 are visible
+        cur = nxt;
+        t = tn;
+        have = hn;
+        b ^= 1u;
+    }
 }
 
 // One BFS expansion tile: EXPAND_TILE consecutive adjacency entries of the
@@ -679,18 +776,8 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
             const uint32_t cc = c.mt_c[di];
             warp_leaf_sort(keys, (cc & 1u) ? scratch : keys, c.mt_a[di], c.mt_b[di]);
         }
-        // merge tiles: one block each
-        for (uint32_t t = blockIdx.x; t < nt1; t += gridDim.x) {
-            const uint32_t di = c.mt_tiledesc[t];
-            if (c.mt_kind[di] != MAP_MERGE) continue;
-            job_buffers(c, job_params, job_stride, c.mt_job[di], &keys, &scratch);
-            const uint32_t lo = c.mt_a[di], hi = c.mt_b[di], cc = c.mt_c[di];
-            const uint32_t tin = t - c.mt_tilebase[di];
-            const uint32_t ntiles = (hi - lo + MERGE_TILE - 1u) / MERGE_TILE;
-            const uint32_t i0 = tin ? c.mt_split[t] : 0u;
-            const uint32_t i1 = tin + 1u < ntiles ? c.mt_split[t + 1u] : (hi - lo) / 2u;
-            merge_tile<BS>((cc & 1u) ? keys : scratch, (cc & 1u) ? scratch : keys, lo, hi, tin, i0, i1, sm);
-        }
+        // merge tiles: one block each, pipelined
+        merge_phase<BS>(c, ctl, sm, nt1, job_params, job_stride);
       }
     }
     if constexpr ((PM & PM_BFS) != 0u) {

@@ -62,3 +62,13 @@ def test_default_config_without_gpu(libpath):
     assert cfg.inject_stall_epoch == -1
     assert trees.trees_bytes_for(1000, cfg) > 1000 * 24
     assert trees.trees_bytes_for(0, cfg) == 0
+
+
+def test_autotune_cache_hit_needs_no_gpu(libpath, tmp_path):
+    # a cached key is answered from the JSON file before any device work
+    cache = tmp_path / "tune.json"
+    cache.write_text('{\n  "fib:n=34": {"block_size": 256, "tasks_per_thread": 4, "scheduler": 1, "ms": 0.5}\n}\n')
+    best, ms, cands = trees.trees_autotune(trees.make_job(trees.TREES_PROG_FIB, n=34), 1 << 20,
+                                           cache_path=str(cache), key="fib:n=34")
+    assert (best.block_size, best.tasks_per_thread, best.scheduler) == (256, 4, 1)
+    assert ms == 0.5 and cands == []
