@@ -157,11 +157,11 @@ __global__ void k_phase3(Ctl *ctl, Conf c, cudaGraphConditionalHandle h) {
         uint32_t sp = ctl->g_sp, next = base;
         int ok = 1;
         if (jf) {
-            if (sp < c.gstack_cap) c.gstack[sp++] = Range{cen, lo, hi};
+            if (sp < c.gstack_cap) c.gstack[sp++] = Range{cen, lo, hi, 1u};
             else ok = 0;
         }
         if (f) {
-            if (sp < c.gstack_cap) c.gstack[sp++] = Range{cen + 1u, base, base + f};
+            if (sp < c.gstack_cap) c.gstack[sp++] = Range{cen + 1u, base, base + f, 0u};
             else ok = 0;
             next = base + f;
         } else if (!jf) {

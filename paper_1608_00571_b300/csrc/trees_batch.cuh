@@ -66,7 +66,7 @@ __device__ __forceinline__ uint32_t job_advance(const Conf &c, Job &J, uint32_t 
         c.link[r] = 0u;
         c.result[r] = 0ull;
         J.sp = 1;
-        J.stk[0] = Range{0u, r, r + 1u};
+        J.stk[0] = Range{0u, r, r + 1u, 0u};
         J.next = r + 1u;
         J.peak = 1u;
         J.pending = 0u;
@@ -78,11 +78,11 @@ __device__ __forceinline__ uint32_t job_advance(const Conf &c, Job &J, uint32_t 
     if (J.pending) {
         const uint32_t f = vload(&J.cnt), jf = vload(&J.join);
         if (jf) {
-            if (J.sp < BSTK) J.stk[J.sp++] = Range{J.cen, J.lo, J.hi};
+            if (J.sp < BSTK) J.stk[J.sp++] = Range{J.cen, J.lo, J.hi, 1u};
             else J.err = TREES_ERR_STACK;
         }
         if (f) {
-            if (J.sp < BSTK) J.stk[J.sp++] = Range{J.cen + 1u, J.base, J.base + f};
+            if (J.sp < BSTK) J.stk[J.sp++] = Range{J.cen + 1u, J.base, J.base + f, 0u};
             else J.err = TREES_ERR_STACK;
             J.next = J.base + f;
             J.peak = max(J.peak, J.next - J.seg_base);
@@ -190,11 +190,37 @@ __device__ __forceinline__ uint32_t warp_seg_scan(uint32_t key, uint32_t x, int 
     return inc - x;
 }
 
-// One Phase-2 tile of a global step: work items [t0, t0 + BS).
+// largest j in [lo, hi) with joff[j] <= w
+__device__ __forceinline__ uint32_t find_job_in(const uint32_t *joff, uint32_t lo, uint32_t hi, uint32_t w) {
+    while (hi - lo > 1u) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (joff[mid] <= w) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One Phase-2 tile of a global step: work items [t0, t0 + BS).  Thread 0
+// finds the jobs of the tile's first and last items; a tile inside one job
+// (the common case) allocates its forks with one block scan and one atomic,
+// a tile that straddles jobs with a warp-segmented scan and one atomic per
+// job per warp.
 template <int BS>
 __device__ void batch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, Job *jobs, const uint32_t *joff, uint32_t nj,
-                           uint32_t w, bool inr, Acc &acc) {
+                           unsigned long long t0, uint32_t W, Acc &acc) {
     const uint32_t NONE = 0xffffffffu;
+    if (threadIdx.x == 0) {
+        const uint32_t last = (uint32_t)min(t0 + (unsigned long long)BS, (unsigned long long)W) - 1u;
+        const uint32_t jf = find_job(joff, nj, (uint32_t)t0);
+        sm.bc32[0] = jf;
+        sm.bc32[1] = find_job_in(joff, jf, nj, last);
+    }
+    __syncthreads();
+    const uint32_t jf = sm.bc32[0], jl = sm.bc32[1];
+    const bool uniform = jf == jl;
+    const unsigned long long wl = t0 + threadIdx.x;
+    const bool inr = wl < W;
+    const uint32_t w = (uint32_t)wl;
     Plan p[1];
     p[0].s = 0u;
     p[0].t = 0u;
@@ -204,7 +230,7 @@ __device__ void batch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, Job *jobs, con
     uint32_t j = NONE, cen = 0u;
     Job *J = nullptr;
     if (inr) {
-        j = find_job(joff, nj, w);
+        j = uniform ? jf : find_job_in(joff, jf, jl + 1u, w);
         J = &jobs[j];
         cen = J->cen;
         const uint32_t s = J->lo + (w - joff[j]);
@@ -219,35 +245,61 @@ __device__ void batch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, Job *jobs, con
         }
     }
     const uint32_t nfork = forks_of(p[0]);
-    // per-job fork allocation: one atomic per job per warp
-    int end;
-    uint32_t ftot;
-    const uint32_t excl = warp_seg_scan(j, nfork, &end, &ftot);
-    const uint32_t lane = threadIdx.x & 31u;
-    uint32_t b = 0u, over = 0u;
-    if ((int)lane == end && j != NONE && ftot) {
-        b = atomicAdd(&J->cnt, ftot);
-        if ((unsigned long long)J->base + b + ftot > (unsigned long long)J->seg_base + J->seg_cap) {
-            over = 1u;
-            atomicCAS(&J->err, 0, TREES_ERR_CAPACITY);
-        }
-    }
-    b = __shfl_sync(0xffffffffu, b, end);
-    over = __shfl_sync(0xffffffffu, over, end);
     uint32_t joined = 0u;
-    if (nfork && !over) joined = commit_task<PM_BATCH>(c, J->rp, p[0], cen, J->base + b + excl);
-    acc.joins += joined;
-    // per-job task and join counts
-    uint32_t vt, jt;
-    warp_seg_scan(j, p[0].t != 0u, &end, &vt);
-    warp_seg_scan(j, joined, &end, &jt);
-    if ((int)lane == end && j != NONE) {
-        if (vt) atomicAdd(&J->tasks, (unsigned long long)vt);
-        if (jt) {
-            atomicAdd(&J->joins, (unsigned long long)jt);
-            J->join = 1u;
+    if (uniform) {
+        Job *JU = &jobs[jf];
+        uint32_t ftot;
+        int any;
+        const uint32_t foff = block_scan_u32<BS>(nfork, 0, &ftot, &any, sm);
+        if (ftot) {
+            if (threadIdx.x == 0) {
+                const uint32_t b = atomicAdd(&JU->cnt, ftot);
+                const bool over =
+                    (unsigned long long)JU->base + b + ftot > (unsigned long long)JU->seg_base + JU->seg_cap;
+                if (over) atomicCAS(&JU->err, 0, TREES_ERR_CAPACITY);
+                sm.bc32[2] = b;
+                sm.bc32[3] = over;
+            }
+            __syncthreads();
+            if (nfork && !sm.bc32[3]) joined = commit_task<PM_BATCH>(c, JU->rp, p[0], cen, JU->base + sm.bc32[2] + foff);
+        }
+        const uint32_t vt = (uint32_t)__syncthreads_count(p[0].t != 0u);
+        const uint32_t jt = (uint32_t)__syncthreads_count(joined != 0u);
+        if (threadIdx.x == 0) {
+            if (vt) atomicAdd(&JU->tasks, (unsigned long long)vt);
+            if (jt) {
+                atomicAdd(&JU->joins, (unsigned long long)jt);
+                JU->join = 1u;
+            }
+        }
+    } else {
+        int end;
+        uint32_t ftot;
+        const uint32_t excl = warp_seg_scan(j, nfork, &end, &ftot);
+        const uint32_t lane = threadIdx.x & 31u;
+        uint32_t b = 0u, over = 0u;
+        if ((int)lane == end && j != NONE && ftot) {
+            b = atomicAdd(&J->cnt, ftot);
+            if ((unsigned long long)J->base + b + ftot > (unsigned long long)J->seg_base + J->seg_cap) {
+                over = 1u;
+                atomicCAS(&J->err, 0, TREES_ERR_CAPACITY);
+            }
+        }
+        b = __shfl_sync(0xffffffffu, b, end);
+        over = __shfl_sync(0xffffffffu, over, end);
+        if (nfork && !over) joined = commit_task<PM_BATCH>(c, J->rp, p[0], cen, J->base + b + excl);
+        uint32_t vt, jt;
+        warp_seg_scan(j, p[0].t != 0u, &end, &vt);
+        warp_seg_scan(j, joined, &end, &jt);
+        if ((int)lane == end && j != NONE) {
+            if (vt) atomicAdd(&J->tasks, (unsigned long long)vt);
+            if (jt) {
+                atomicAdd(&J->joins, (unsigned long long)jt);
+                J->join = 1u;
+            }
         }
     }
+    acc.joins += joined;
     if (p[0].m) atomicAdd(&J->maps, 1ull);
     if (__syncthreads_or(p[0].m != 0u)) map_alloc<BS, 1>(c, ctl, sm, p, cen, 0u, 0u, j, acc);
     __syncthreads();
@@ -268,10 +320,8 @@ __global__ void __launch_bounds__(BS) k_batch(Ctl *ctl, Conf c, BatchCtl *bc, Jo
         __syncthreads();
         const uint32_t W = s_w, nj = bc->njobs;
         if (W == 0u) break;
-        for (unsigned long long t0 = (unsigned long long)blockIdx.x * BS; t0 < W; t0 += (unsigned long long)gridDim.x * BS) {
-            const unsigned long long w = t0 + threadIdx.x;
-            batch_tile<BS>(c, ctl, sm, jobs, joff, nj, (uint32_t)w, w < W, acc);
-        }
+        for (unsigned long long t0 = (unsigned long long)blockIdx.x * BS; t0 < W; t0 += (unsigned long long)gridDim.x * BS)
+            batch_tile<BS>(c, ctl, sm, jobs, joff, nj, t0, W, acc);
         if (!grid_sync<BS>(ctl, &bar, c.timeout_ns, sm)) break;
         const unsigned long long mt = vload(&ctl->mt_ctr[0]);
         if (mt) {

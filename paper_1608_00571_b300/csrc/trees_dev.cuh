@@ -31,6 +31,7 @@ constexpr int NBLK_STATS = 8192;                // per-block statistics slots   
 
 struct Range {
     uint32_t cen, lo, hi;  // epoch number and NDRange [lo, hi) (Sec. 5.1.2)
+    uint32_t join;         // 1: a join range revisited (continuations), 0: freshly forked tasks
 };
 
 // The job a single-job run executes (copied into the control block per run).
@@ -146,12 +147,13 @@ struct Smem {
     unsigned long long bc64[4];
     int bar_ok;
     unsigned long long mbar[2];           // mbarriers of the two merge buffers
+    uint32_t mtile[2][12];                // merge tiles resolved by thread 0 (one per buffer)
     unsigned int ep_cnt, ep_join;         // the epoch's counters, read right after its barrier
     unsigned long long ep_mt, ep_me;
     // replicated epoch-range stack and scheduler state (persistent scheduler)
     Range stk[STK_CAP];
     int sp;
-    uint32_t next, cen, lo, hi, base;
+    uint32_t next, cen, lo, hi, base, rjoin;
     int stop;
     union alignas(16) {
         uint32_t mg[2][MERGE_BUF];  // double-buffered merge tile inputs (TMA destinations)
@@ -293,8 +295,7 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, uint32_t *bar_idx, unsigned 
     if (threadIdx.x == 0) {
         const uint32_t idx = ++(*bar_idx);
         const unsigned int target = idx * gridDim.x;
-        fence_acq_rel();
-        red_release_add(&ctl->bar_count, 1u);
+        red_release_add(&ctl->bar_count, 1u);  // release: covers the block's writes ordered by bar.sync
         int ok = 1;
         uint32_t spins = 0;
         uint64_t t0 = 0;
@@ -310,7 +311,7 @@ __device__ __forceinline__ bool grid_sync(Ctl *ctl, uint32_t *bar_idx, unsigned 
                 }
             }
         }
-        fence_acq_rel();
+        fence_acq_rel();  // acquire for the whole SM: no stale L1 line of data written before the barrier
         // one block-uniform decision: stop on a timeout or on any error raised before the barrier
         sm.bar_ok = ok && vload(&ctl->err) == 0;
     }
@@ -379,8 +380,7 @@ __device__ __forceinline__ bool grid_sync_ep(Ctl *ctl, uint32_t *bar_idx, unsign
     if (threadIdx.x == 0) {
         const uint32_t idx = ++(*bar_idx);
         const unsigned int target = idx * gridDim.x;
-        fence_acq_rel();
-        red_release_add(&ctl->bar_count, 1u);
+        red_release_add(&ctl->bar_count, 1u);  // release: covers the block's writes ordered by bar.sync
         int ok = 1;
         uint32_t spins = 0;
         uint64_t t0 = 0;
@@ -396,7 +396,7 @@ __device__ __forceinline__ bool grid_sync_ep(Ctl *ctl, uint32_t *bar_idx, unsign
                 }
             }
         }
-        fence_acq_rel();
+        fence_acq_rel();  // acquire for the whole SM: no stale L1 line of data written before the barrier
         const int err = vload(&ctl->err);
         sm.ep_cnt = vload(&ctl->cnt[ep]);
         sm.ep_join = vload(&ctl->join[ep]);

@@ -43,14 +43,21 @@ __device__ __forceinline__ void trace_valid_add(const Conf &c, uint32_t e, uint3
 }
 
 // The persistent scheduler: the whole epoch loop in one cooperative launch.
+// Blocks per SM the kernel is compiled to fit: the mergesort kernel keeps
+// 1024 threads per SM resident (the warp leaf sort would otherwise take the
+// registers of a whole SM); the others take what they need.
+__host__ __device__ constexpr int persistent_min_blocks(int bs, uint32_t pm) {
+    return pm == PM_MS ? (1024 / bs > 0 ? 1024 / bs : 1) : 1;
+}
+
 template <int BS, int TPT, uint32_t PM>
-__global__ void __launch_bounds__(BS) k_persistent(Ctl *ctl, Conf c, unsigned long long *blk) {
+__global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM)) k_persistent(Ctl *ctl, Conf c, unsigned long long *blk) {
     __shared__ Smem<BS> sm;
     uint32_t bar = 0;
     Acc acc = {0u, 0u, 0u};
     if (threadIdx.x == 0) {
         sm.sp = 1;
-        sm.stk[0] = Range{0u, 0u, 1u};
+        sm.stk[0] = Range{0u, 0u, 1u, 0u};
         sm.next = 1u;
     }
     unsigned long long forks_total = 0;
@@ -70,6 +77,7 @@ __global__ void __launch_bounds__(BS) k_persistent(Ctl *ctl, Conf c, unsigned lo
                 sm.cen = r.cen;
                 sm.lo = r.lo;
                 sm.hi = r.hi;
+                sm.rjoin = r.join;
                 sm.base = sm.next;
             }
             sm.stop = stop;
@@ -84,12 +92,13 @@ __global__ void __launch_bounds__(BS) k_persistent(Ctl *ctl, Conf c, unsigned lo
         __syncthreads();
         if (sm.stop) break;
         const uint32_t cen = sm.cen, lo = sm.lo, hi = sm.hi, base = sm.base, ep = e % 3u;
+        const int mode = sm.rjoin ? LOAD_JOIN : LOAD_FRESH;
         // Phase 2: every entry of [lo, hi)
         const uint32_t v0 = acc.valid;
         int par = 0;
         for (unsigned long long t0 = (unsigned long long)lo + (unsigned long long)blockIdx.x * (BS * TPT); t0 < hi;
              t0 += (unsigned long long)gridDim.x * (BS * TPT)) {
-            epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par);
+            epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode);
             par ^= 1;
         }
         trace_valid_add<BS>(c, e, acc.valid - v0, sm);
@@ -111,11 +120,11 @@ __global__ void __launch_bounds__(BS) k_persistent(Ctl *ctl, Conf c, unsigned lo
             const uint32_t f = sm.ep_cnt, jf = sm.ep_join;
             int ok = 1;
             if (jf) {
-                if (sm.sp < STK_CAP) sm.stk[sm.sp++] = Range{cen, lo, hi};
+                if (sm.sp < STK_CAP) sm.stk[sm.sp++] = Range{cen, lo, hi, 1u};
                 else ok = 0;
             }
             if (f) {
-                if (sm.sp < STK_CAP) sm.stk[sm.sp++] = Range{cen + 1u, base, base + f};
+                if (sm.sp < STK_CAP) sm.stk[sm.sp++] = Range{cen + 1u, base, base + f, 0u};
                 else ok = 0;
                 sm.next = base + f;
             } else if (!jf) {

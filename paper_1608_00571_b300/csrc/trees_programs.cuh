@@ -343,26 +343,44 @@ __device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan (&p)
 // tile are issued before any task runs, one vector scan hands every (k,
 // thread) its children's offset in k-major order (so the children of a warp
 // are written contiguously), and one atomic per block reserves them.
+// Which columns Phase 2 reads together with `code`: LOAD_ON_DEMAND reads
+// them after decoding the type; LOAD_FRESH (a range of freshly forked tasks)
+// and LOAD_JOIN (a join range revisited) issue the columns such tasks use in
+// the same round trip as the code.
+constexpr int LOAD_ON_DEMAND = 0, LOAD_FRESH = 1, LOAD_JOIN = 2;
+
 template <int BS, int TPT, uint32_t PM>
 __device__ __forceinline__ void epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, unsigned long long t0, uint32_t hi,
-                                           uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, Acc &acc, int par) {
+                                           uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, Acc &acc, int par,
+                                           int mode = LOAD_ON_DEMAND) {
+    constexpr bool fresh_a1 = (PM & (PM_MS | PM_NQ)) != 0u;
+    constexpr bool join_a0 = (PM & (PM_MS | PM_NQ | PM_TRAV)) != 0u;
+    constexpr bool join_link = (PM & (PM_FIB | PM_NQ)) != 0u;
+    const bool sa0 = mode == LOAD_FRESH || (mode == LOAD_JOIN && join_a0);
+    const bool sa1 = (mode == LOAD_FRESH || mode == LOAD_JOIN) && fresh_a1;
+    const bool slk = mode == LOAD_JOIN && join_link;
     Plan p[TPT];
-    uint32_t a0v[TPT], a1v[TPT], lkv[TPT];
+    uint32_t cd[TPT], a0v[TPT], a1v[TPT], lkv[TPT];
 #pragma unroll
     for (int k = 0; k < TPT; ++k) {
         const unsigned long long s = t0 + (unsigned long long)k * BS + threadIdx.x;
+        const bool in = s < hi;
         p[k].s = (uint32_t)s;
         p[k].n = 0u;
         p[k].m = 0u;
-        // invalid or stale entries exit at once (Sec. 5.3)
-        p[k].t = s < hi ? task_type(c.code[s], cen) : 0u;
+        cd[k] = in ? c.code[s] : 0u;
+        a0v[k] = in && sa0 ? c.a0[s] : 0u;
+        a1v[k] = in && sa1 ? c.a1[s] : 0u;
+        lkv[k] = in && slk ? c.link[s] : 0u;
     }
 #pragma unroll
     for (int k = 0; k < TPT; ++k) {
-        const uint32_t s = p[k].s, t = p[k].t;
-        a0v[k] = needs_a0(t) ? c.a0[s] : 0u;
-        a1v[k] = needs_a1(t) ? c.a1[s] : 0u;
-        lkv[k] = needs_link(t) ? c.link[s] : 0u;
+        const uint32_t s = p[k].s;
+        const uint32_t t = task_type(cd[k], cen);  // invalid or stale entries exit at once (Sec. 5.3)
+        p[k].t = t;
+        if (needs_a0(t) && !sa0) a0v[k] = c.a0[s];
+        if (needs_a1(t) && !sa1) a1v[k] = c.a1[s];
+        if (needs_link(t) && !slk) lkv[k] = c.link[s];
     }
     uint32_t nf[TPT];
     int hasmap = 0;
@@ -657,6 +675,48 @@ __device__ __forceinline__ void merge_compute(const MergeTile &m, const uint32_t
         if (k < cnt) o[k] = v[k];
 }
 
+// Thread 0 resolves the next merge tile at or after *t and publishes it in
+// shared slot `slot` (so every thread of the block agrees on the sequence);
+// returns, after a block barrier, whether there was one.
+template <int BS>
+__device__ __forceinline__ bool publish_merge_tile(const Conf &c, Smem<BS> &sm, uint32_t *t, uint32_t nt1,
+                                                   const RunParams *jp, uint32_t js, uint32_t slot, MergeTile &m) {
+    if (threadIdx.x == 0) {
+        uint32_t tt = *t;
+        MergeTile x;
+        const bool ok = next_merge_tile(c, tt, nt1, jp, js, x);
+        uint32_t *w = sm.mtile[slot];
+        w[0] = ok;
+        w[1] = tt;
+        if (ok) {
+            w[2] = (uint32_t)(reinterpret_cast<uintptr_t>(x.in));
+            w[3] = (uint32_t)(reinterpret_cast<uintptr_t>(x.in) >> 32);
+            w[4] = (uint32_t)(reinterpret_cast<uintptr_t>(x.out));
+            w[5] = (uint32_t)(reinterpret_cast<uintptr_t>(x.out) >> 32);
+            w[6] = x.lo;
+            w[7] = x.mid;
+            w[8] = x.d0;
+            w[9] = x.i0;
+            w[10] = x.i1;
+            w[11] = x.j1;
+        }
+    }
+    __syncthreads();
+    const uint32_t *w = sm.mtile[slot];
+    *t = w[1];
+    if (!w[0]) return false;
+    m.in = reinterpret_cast<const uint32_t *>((uintptr_t)w[2] | ((uintptr_t)w[3] << 32));
+    m.out = reinterpret_cast<uint32_t *>((uintptr_t)w[4] | ((uintptr_t)w[5] << 32));
+    m.lo = w[6];
+    m.mid = w[7];
+    m.d0 = w[8];
+    m.i0 = w[9];
+    m.i1 = w[10];
+    m.j0 = m.d0 - m.i0;
+    m.j1 = w[11];
+    return true;
+}
+
 // All merge tiles of the epoch handled by this block, two-stage pipelined:
 // while the block merges one tile from shared memory, the next tile's runs
 // stream in by TMA.  Waits are bounded (TREES_ERR_TIMEOUT).
@@ -666,20 +726,19 @@ __device__ void merge_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t nt1,
         mbar_init(&sm.mbar[0], 1u);
         mbar_init(&sm.mbar[1], 1u);
     }
-    __syncthreads();
     uint32_t par0 = 0u, par1 = 0u;
     uint32_t t = blockIdx.x, b = 0u;
     MergeTile cur, nxt;
-    bool have = next_merge_tile(c, t, nt1, jp, js, cur);
+    bool have = publish_merge_tile<BS>(c, sm, &t, nt1, jp, js, 0u, cur);
     if (have) merge_stage<BS>(cur, sm.u.mg[0], &sm.mbar[0]);
     __syncthreads();
     while (have) {
         uint32_t tn = t + gridDim.x;
-        const bool hn = next_merge_tile(c, tn, nt1, jp, js, nxt);
+        const bool hn = publish_merge_tile<BS>(c, sm, &tn, nt1, jp, js, b ^ 1u, nxt);
         if (hn) merge_stage<BS>(nxt, sm.u.mg[b ^ 1u], &sm.mbar[b ^ 1u]);
         const uint32_t par = b ? par1 : par0;
         if (!mbar_wait(&sm.mbar[b], par, c.timeout_ns)) {
-            set_err(ctl, TREES_ERR_TIMEOUT, 0u);
+            set_err(ctl, TREES_ERR_TIMEOUT, 0x80000000u | t);  // marks a merge-tile wait, with its tile
             if (hn) mbar_wait(&sm.mbar[b ^ 1u], b ? par0 : par1, c.timeout_ns);  // let the other copy land
             __syncthreads();
             return;
@@ -712,12 +771,12 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
         sm.u.ex.v[k] = c.me_v[dfirst + k];
     }
     __syncthreads();
-    uint32_t claimed[EPT];
-    uint32_t nc = 0;
-    const int32_t nlev = (int32_t)(cen + 1u);
+    // stage 1: every element's adjacency index (load-balanced search in shared memory)
+    uint32_t ed[EPT];
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j) {
         const uint32_t g = g0 + j * BS + threadIdx.x;
+        ed[j] = 0xFFFFFFFFu;
         if (g < g1) {
             uint32_t lo = 0, hi = nloc;
             while (hi - lo > 1u) {
@@ -725,12 +784,22 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
                 if (sm.u.ex.base[mid] <= g) lo = mid;
                 else hi = mid;
             }
-            const uint32_t edge = sm.u.ex.v[lo] + (g - sm.u.ex.base[lo]);
-            const int32_t u = __ldg(c.rp.col + edge);
-            int32_t *lv = c.rp.level + u;
-            if (*(volatile int32_t *)lv < 0 && atomicCAS(lv, -1, nlev) == -1) claimed[nc++] = (uint32_t)u;
+            ed[j] = sm.u.ex.v[lo] + (g - sm.u.ex.base[lo]);
         }
     }
+    // stage 2: all neighbour ids, then all their levels, in flight together
+    int32_t uu[EPT], lv[EPT];
+#pragma unroll
+    for (uint32_t j = 0; j < EPT; ++j) uu[j] = ed[j] != 0xFFFFFFFFu ? __ldg(c.rp.col + ed[j]) : -1;
+#pragma unroll
+    for (uint32_t j = 0; j < EPT; ++j) lv[j] = uu[j] >= 0 ? c.rp.level[uu[j]] : 0;
+    // stage 3: claim unvisited neighbours (the CAS decides between competing visits)
+    const int32_t nlev = (int32_t)(cen + 1u);
+    uint32_t cmask = 0u;
+#pragma unroll
+    for (uint32_t j = 0; j < EPT; ++j)
+        if (uu[j] >= 0 && lv[j] < 0 && atomicCAS(c.rp.level + uu[j], -1, nlev) == -1) cmask |= 1u << j;
+    const uint32_t nc = (uint32_t)__popc(cmask);
     uint32_t ftot;
     int any;
     const uint32_t off = block_scan_u32<BS>(nc, 0, &ftot, &any, sm);
@@ -745,10 +814,14 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
         __syncthreads();
         if (!sm.bc32[1]) {
             const uint32_t code = enc(cen + 1u, TREES_TASK_BFS_VISIT);
-            const uint32_t slot0 = base + sm.bc32[0] + off;
-            for (uint32_t i = 0; i < nc; ++i) {
-                c.code[slot0 + i] = code;
-                c.a0[slot0 + i] = claimed[i];
+            uint32_t slot = base + sm.bc32[0] + off;
+#pragma unroll
+            for (uint32_t j = 0; j < EPT; ++j) {
+                if ((cmask >> j) & 1u) {
+                    c.code[slot] = code;
+                    c.a0[slot] = (uint32_t)uu[j];
+                    ++slot;
+                }
             }
         }
     }

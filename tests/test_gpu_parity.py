@@ -128,6 +128,17 @@ def test_mergesort(sched, n):
         check_trace(ctx, sim, TRACE_FIELDS + ("maps",))
 
 
+@pytest.mark.parametrize("sched", [T.TREES_SCHED_PERSISTENT, T.TREES_SCHED_GRAPH])
+@pytest.mark.parametrize("bs", [256, 512, 1024])
+@pytest.mark.parametrize("n", [5000, 100000, (1 << 20) + 3])
+def test_mergesort_block_sizes(sched, bs, n):
+    keys = gen.keys_u32(7 * n + bs, n)
+    d = dev_u32(keys)
+    with Ctx(1 << 16, scheduler=sched, block_size=bs, timeout_ns=200_000_000) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_MERGESORT, n=n, keys=d)) == T.TREES_OK
+        assert np.array_equal(host_u32(d), np.sort(keys))
+
+
 @pytest.mark.parametrize("leaf", [1, 3, 64, 1000])
 def test_mergesort_leaf_sizes_and_duplicates(leaf):
     rng = np.random.default_rng(leaf)

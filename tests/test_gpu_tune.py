@@ -40,4 +40,5 @@ def test_autotune_restores_mergesort_keys():
     job = T.make_job(T.TREES_PROG_MERGESORT, n=keys.size, keys=d, scratch=sc)
     best, ms, cands = T.trees_autotune(job, 1 << 12, reps=1)
     assert ms > 0 and len(cands) == 18
+    assert all(c["status"] == T.TREES_OK for c in cands), [c for c in cands if c["status"]]
     assert np.array_equal(d.cpu().numpy().view(np.uint32), keys)   # the caller's keys are left as they were
