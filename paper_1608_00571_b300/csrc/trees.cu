@@ -106,7 +106,9 @@ __global__ void __launch_bounds__(BS) k_epoch(Ctl *ctl, Conf c, unsigned long lo
     int par = 0;
     for (unsigned long long t0 = (unsigned long long)lo + (unsigned long long)blockIdx.x * (BS * TPT); t0 < hi;
          t0 += (unsigned long long)gridDim.x * (BS * TPT)) {
-        epoch_tile<BS, TPT, PM_ALL>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par);
+        TileLoad<TPT> L;
+        tile_load<BS, TPT, PM_ALL>(c, t0, hi, LOAD_ON_DEMAND, L);
+        epoch_tile<BS, TPT, PM_ALL>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, LOAD_ON_DEMAND, L);
         par ^= 1;
     }
     trace_valid_add<BS>(c, e, acc.valid, sm);

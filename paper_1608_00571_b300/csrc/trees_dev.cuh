@@ -22,7 +22,8 @@ constexpr int STK_CAP = 512;                    // epoch-range stack entries per
 constexpr int LEAF_MAX = 1024;                  // largest leaf a block sorts in shared memory
 constexpr uint32_t MERGE_TILE = 2048;           // outputs of one merge-path tile
 constexpr uint32_t MERGE_BUF = 2 * MERGE_TILE + 8; // keys of one staged tile: A run, 16-B gap, B run
-constexpr uint32_t EXPAND_TILE = 4096;          // adjacency entries of one BFS expansion tile
+constexpr uint32_t EXPAND_TILE = 2048;          // adjacency entries of one BFS expansion tile
+constexpr int MCHUNK = 32;                      // merge tiles a block resolves at once
 constexpr unsigned long long CTR_LOW_MASK = (1ull << 40) - 1;  // map counters: (descs << 40) | units
 
 enum MapKind : uint32_t { MAP_LEAF_SORT = 1, MAP_MERGE = 2, MAP_EXPAND = 3 };
@@ -147,7 +148,7 @@ struct Smem {
     unsigned long long bc64[4];
     int bar_ok;
     unsigned long long mbar[2];           // mbarriers of the two merge buffers
-    uint32_t mtile[2][12];                // merge tiles resolved by thread 0 (one per buffer)
+    uint32_t mtab[MCHUNK][12];            // the block's next merge tiles, resolved in parallel
     unsigned int ep_cnt, ep_join;         // the epoch's counters, read right after its barrier
     unsigned long long ep_mt, ep_me;
     // replicated epoch-range stack and scheduler state (persistent scheduler)

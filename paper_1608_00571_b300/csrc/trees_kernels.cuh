@@ -47,7 +47,7 @@ __device__ __forceinline__ void trace_valid_add(const Conf &c, uint32_t e, uint3
 // 1024 threads per SM resident (the warp leaf sort would otherwise take the
 // registers of a whole SM); the others take what they need.
 __host__ __device__ constexpr int persistent_min_blocks(int bs, uint32_t pm) {
-    return pm == PM_MS ? (1024 / bs > 0 ? 1024 / bs : 1) : 1;
+    return (pm == PM_MS || pm == PM_FIB) ? (1024 / bs > 0 ? 1024 / bs : 1) : 1;
 }
 
 template <int BS, int TPT, uint32_t PM>
@@ -95,10 +95,17 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM)) k_persisten
         const int mode = sm.rjoin ? LOAD_JOIN : LOAD_FRESH;
         // Phase 2: every entry of [lo, hi)
         const uint32_t v0 = acc.valid;
+        // tiles grid-stride over [lo, hi); the next tile's columns load while this one runs
         int par = 0;
-        for (unsigned long long t0 = (unsigned long long)lo + (unsigned long long)blockIdx.x * (BS * TPT); t0 < hi;
-             t0 += (unsigned long long)gridDim.x * (BS * TPT)) {
-            epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode);
+        const unsigned long long step = (unsigned long long)gridDim.x * (BS * TPT);
+        unsigned long long t0 = (unsigned long long)lo + (unsigned long long)blockIdx.x * (BS * TPT);
+        TileLoad<TPT> cur, nxt;
+        if (t0 < hi) tile_load<BS, TPT, PM>(c, t0, hi, mode, cur);
+        for (; t0 < hi; t0 += step) {
+            const bool more = t0 + step < hi;
+            if (more) tile_load<BS, TPT, PM>(c, t0 + step, hi, mode, nxt);
+            epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode, cur);
+            if (more) cur = nxt;
             par ^= 1;
         }
         trace_valid_add<BS>(c, e, acc.valid - v0, sm);

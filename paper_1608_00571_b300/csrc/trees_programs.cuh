@@ -349,10 +349,36 @@ __device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan (&p)
 // the same round trip as the code.
 constexpr int LOAD_ON_DEMAND = 0, LOAD_FRESH = 1, LOAD_JOIN = 2;
 
+// The TV columns of one tile, loaded ahead of running it.
+template <int TPT>
+struct TileLoad {
+    uint32_t cd[TPT], a0[TPT], a1[TPT], lk[TPT];
+};
+
+template <int BS, int TPT, uint32_t PM>
+__device__ __forceinline__ void tile_load(const Conf &c, unsigned long long t0, uint32_t hi, int mode,
+                                          TileLoad<TPT> &L) {
+    constexpr bool fresh_a1 = (PM & (PM_MS | PM_NQ)) != 0u;
+    constexpr bool join_a0 = (PM & (PM_MS | PM_NQ | PM_TRAV)) != 0u;
+    constexpr bool join_link = (PM & (PM_FIB | PM_NQ)) != 0u;
+    const bool sa0 = mode == LOAD_FRESH || (mode == LOAD_JOIN && join_a0);
+    const bool sa1 = (mode == LOAD_FRESH || mode == LOAD_JOIN) && fresh_a1;
+    const bool slk = mode == LOAD_JOIN && join_link;
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+        const unsigned long long s = t0 + (unsigned long long)k * BS + threadIdx.x;
+        const bool in = s < hi;
+        L.cd[k] = in ? c.code[s] : 0u;
+        L.a0[k] = in && sa0 ? c.a0[s] : 0u;
+        L.a1[k] = in && sa1 ? c.a1[s] : 0u;
+        L.lk[k] = in && slk ? c.link[s] : 0u;
+    }
+}
+
 template <int BS, int TPT, uint32_t PM>
 __device__ __forceinline__ void epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, unsigned long long t0, uint32_t hi,
                                            uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, Acc &acc, int par,
-                                           int mode = LOAD_ON_DEMAND) {
+                                           int mode, const TileLoad<TPT> &L) {
     constexpr bool fresh_a1 = (PM & (PM_MS | PM_NQ)) != 0u;
     constexpr bool join_a0 = (PM & (PM_MS | PM_NQ | PM_TRAV)) != 0u;
     constexpr bool join_link = (PM & (PM_FIB | PM_NQ)) != 0u;
@@ -360,27 +386,18 @@ __device__ __forceinline__ void epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm
     const bool sa1 = (mode == LOAD_FRESH || mode == LOAD_JOIN) && fresh_a1;
     const bool slk = mode == LOAD_JOIN && join_link;
     Plan p[TPT];
-    uint32_t cd[TPT], a0v[TPT], a1v[TPT], lkv[TPT];
+    uint32_t a0v[TPT], a1v[TPT], lkv[TPT];
 #pragma unroll
     for (int k = 0; k < TPT; ++k) {
-        const unsigned long long s = t0 + (unsigned long long)k * BS + threadIdx.x;
-        const bool in = s < hi;
-        p[k].s = (uint32_t)s;
+        const uint32_t s = (uint32_t)(t0 + (unsigned long long)k * BS + threadIdx.x);
+        const uint32_t t = task_type(L.cd[k], cen);  // invalid or stale entries exit at once (Sec. 5.3)
+        p[k].s = s;
+        p[k].t = t;
         p[k].n = 0u;
         p[k].m = 0u;
-        cd[k] = in ? c.code[s] : 0u;
-        a0v[k] = in && sa0 ? c.a0[s] : 0u;
-        a1v[k] = in && sa1 ? c.a1[s] : 0u;
-        lkv[k] = in && slk ? c.link[s] : 0u;
-    }
-#pragma unroll
-    for (int k = 0; k < TPT; ++k) {
-        const uint32_t s = p[k].s;
-        const uint32_t t = task_type(cd[k], cen);  // invalid or stale entries exit at once (Sec. 5.3)
-        p[k].t = t;
-        if (needs_a0(t) && !sa0) a0v[k] = c.a0[s];
-        if (needs_a1(t) && !sa1) a1v[k] = c.a1[s];
-        if (needs_link(t) && !slk) lkv[k] = c.link[s];
+        a0v[k] = needs_a0(t) && !sa0 ? c.a0[s] : L.a0[k];
+        a1v[k] = needs_a1(t) && !sa1 ? c.a1[s] : L.a1[k];
+        lkv[k] = needs_link(t) && !slk ? c.link[s] : L.lk[k];
     }
     uint32_t nf[TPT];
     int hasmap = 0;
@@ -588,29 +605,26 @@ struct MergeTile {
     uint32_t lo, mid, d0, i0, i1, j0, j1;
 };
 
-// The next merge tile at or after t in steps of gridDim.x (false when none).
-__device__ __forceinline__ bool next_merge_tile(const Conf &c, uint32_t &t, uint32_t nt1, const RunParams *jp,
-                                                uint32_t js, MergeTile &m) {
-    for (; t < nt1; t += gridDim.x) {
-        const uint32_t di = c.mt_tiledesc[t];
-        if (c.mt_kind[di] != MAP_MERGE) continue;
-        uint32_t *keys, *scratch;
-        job_buffers(c, jp, js, c.mt_job[di], &keys, &scratch);
-        const uint32_t lo = c.mt_a[di], hi = c.mt_b[di], cc = c.mt_c[di];
-        const uint32_t tin = t - c.mt_tilebase[di];
-        const uint32_t la = (hi - lo) / 2u, L = hi - lo, ntiles = (L + MERGE_TILE - 1u) / MERGE_TILE;
-        m.in = (cc & 1u) ? keys : scratch;   // the children's runs (depth d+1)
-        m.out = (cc & 1u) ? scratch : keys;  // this node's run (depth d)
-        m.lo = lo;
-        m.mid = lo + la;
-        m.d0 = tin * MERGE_TILE;
-        m.i0 = tin ? c.mt_split[t] : 0u;
-        m.i1 = tin + 1u < ntiles ? c.mt_split[t + 1u] : la;
-        m.j0 = m.d0 - m.i0;
-        m.j1 = min(m.d0 + MERGE_TILE, L) - m.i1;
-        return true;
-    }
-    return false;
+// Resolves merge tile t of the tiled map list (false when it is not a merge).
+__device__ __forceinline__ bool resolve_merge_tile(const Conf &c, uint32_t t, const RunParams *jp, uint32_t js,
+                                                   MergeTile &m) {
+    const uint32_t di = c.mt_tiledesc[t];
+    if (c.mt_kind[di] != MAP_MERGE) return false;
+    uint32_t *keys, *scratch;
+    job_buffers(c, jp, js, c.mt_job[di], &keys, &scratch);
+    const uint32_t lo = c.mt_a[di], hi = c.mt_b[di], cc = c.mt_c[di];
+    const uint32_t tin = t - c.mt_tilebase[di];
+    const uint32_t la = (hi - lo) / 2u, L = hi - lo, ntiles = (L + MERGE_TILE - 1u) / MERGE_TILE;
+    m.in = (cc & 1u) ? keys : scratch;   // the children's runs (depth d+1)
+    m.out = (cc & 1u) ? scratch : keys;  // this node's run (depth d)
+    m.lo = lo;
+    m.mid = lo + la;
+    m.d0 = tin * MERGE_TILE;
+    m.i0 = tin ? c.mt_split[t] : 0u;
+    m.i1 = tin + 1u < ntiles ? c.mt_split[t + 1u] : la;
+    m.j0 = m.d0 - m.i0;
+    m.j1 = min(m.d0 + MERGE_TILE, L) - m.i1;
+    return true;
 }
 
 // Starts staging a tile into buf: thread 0 issues the bulk copies of the
@@ -675,82 +689,87 @@ __device__ __forceinline__ void merge_compute(const MergeTile &m, const uint32_t
         if (k < cnt) o[k] = v[k];
 }
 
-// Thread 0 resolves the next merge tile at or after *t and publishes it in
-// shared slot `slot` (so every thread of the block agrees on the sequence);
-// returns, after a block barrier, whether there was one.
-template <int BS>
-__device__ __forceinline__ bool publish_merge_tile(const Conf &c, Smem<BS> &sm, uint32_t *t, uint32_t nt1,
-                                                   const RunParams *jp, uint32_t js, uint32_t slot, MergeTile &m) {
-    if (threadIdx.x == 0) {
-        uint32_t tt = *t;
-        MergeTile x;
-        const bool ok = next_merge_tile(c, tt, nt1, jp, js, x);
-        uint32_t *w = sm.mtile[slot];
-        w[0] = ok;
-        w[1] = tt;
-        if (ok) {
-            w[2] = (uint32_t)(reinterpret_cast<uintptr_t>(x.in));
-            w[3] = (uint32_t)(reinterpret_cast<uintptr_t>(x.in) >> 32);
-            w[4] = (uint32_t)(reinterpret_cast<uintptr_t>(x.out));
-            w[5] = (uint32_t)(reinterpret_cast<uintptr_t>(x.out) >> 32);
-            w[6] = x.lo;
-            w[7] = x.mid;
-            w[8] = x.d0;
-            w[9] = x.i0;
-            w[10] = x.i1;
-            w[11] = x.j1;
-        }
-    }
-    __syncthreads();
-    const uint32_t *w = sm.mtile[slot];
-    *t = w[1];
-    if (!w[0]) return false;
-    m.in = reinterpret_cast<const uint32_t *>((uintptr_t)w[2] | ((uintptr_t)w[3] << 32));
-    m.out = reinterpret_cast<uint32_t *>((uintptr_t)w[4] | ((uintptr_t)w[5] << 32));
-    m.lo = w[6];
-    m.mid = w[7];
-    m.d0 = w[8];
-    m.i0 = w[9];
-    m.i1 = w[10];
-    m.j0 = m.d0 - m.i0;
-    m.j1 = w[11];
-    return true;
+__device__ __forceinline__ void put_merge_tile(uint32_t *w, bool ok, const MergeTile &x) {
+    w[0] = ok;
+    if (!ok) return;
+    w[1] = (uint32_t)(reinterpret_cast<uintptr_t>(x.in));
+    w[2] = (uint32_t)(reinterpret_cast<uintptr_t>(x.in) >> 32);
+    w[3] = (uint32_t)(reinterpret_cast<uintptr_t>(x.out));
+    w[4] = (uint32_t)(reinterpret_cast<uintptr_t>(x.out) >> 32);
+    w[5] = x.lo;
+    w[6] = x.mid;
+    w[7] = x.d0;
+    w[8] = x.i0;
+    w[9] = x.i1;
+    w[10] = x.j1;
 }
 
-// All merge tiles of the epoch handled by this block, two-stage pipelined:
-// while the block merges one tile from shared memory, the next tile's runs
-// stream in by TMA.  Waits are bounded (TREES_ERR_TIMEOUT).
+__device__ __forceinline__ void get_merge_tile(const uint32_t *w, MergeTile &m) {
+    m.in = reinterpret_cast<const uint32_t *>((uintptr_t)w[1] | ((uintptr_t)w[2] << 32));
+    m.out = reinterpret_cast<uint32_t *>((uintptr_t)w[3] | ((uintptr_t)w[4] << 32));
+    m.lo = w[5];
+    m.mid = w[6];
+    m.d0 = w[7];
+    m.i0 = w[8];
+    m.i1 = w[9];
+    m.j0 = m.d0 - m.i0;
+    m.j1 = w[10];
+}
+
+// All merge tiles of the epoch handled by this block (tiles blockIdx.x +
+// k*gridDim.x), two-stage pipelined: while the block merges one tile from
+// shared memory, the next tile's runs stream in by TMA.  The block resolves
+// its tiles MCHUNK at a time, one thread per tile, into a shared table that
+// every thread then walks in the same order.  Waits are bounded
+// (TREES_ERR_TIMEOUT).
 template <int BS>
 __device__ void merge_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t nt1, const RunParams *jp, uint32_t js) {
     if (threadIdx.x == 0) {
         mbar_init(&sm.mbar[0], 1u);
         mbar_init(&sm.mbar[1], 1u);
     }
-    uint32_t par0 = 0u, par1 = 0u;
-    uint32_t t = blockIdx.x, b = 0u;
-    MergeTile cur, nxt;
-    bool have = publish_merge_tile<BS>(c, sm, &t, nt1, jp, js, 0u, cur);
-    if (have) merge_stage<BS>(cur, sm.u.mg[0], &sm.mbar[0]);
-    __syncthreads();
-    while (have) {
-        uint32_t tn = t + gridDim.x;
-        const bool hn = publish_merge_tile<BS>(c, sm, &tn, nt1, jp, js, b ^ 1u, nxt);
-        if (hn) merge_stage<BS>(nxt, sm.u.mg[b ^ 1u], &sm.mbar[b ^ 1u]);
-        const uint32_t par = b ? par1 : par0;
-        if (!mbar_wait(&sm.mbar[b], par, c.timeout_ns)) {
-            set_err(ctl, TREES_ERR_TIMEOUT, 0x80000000u | t);  // marks a merge-tile wait, with its tile
-            if (hn) mbar_wait(&sm.mbar[b ^ 1u], b ? par0 : par1, c.timeout_ns);  // let the other copy land
-            __syncthreads();
-            return;
+    uint32_t par0 = 0u, par1 = 0u, b = 0u;
+    const uint32_t stride = gridDim.x * (uint32_t)MCHUNK;
+    for (uint32_t c0 = blockIdx.x; c0 < nt1; c0 += stride) {
+        __syncthreads();  // the previous chunk's table is no longer read
+        if (threadIdx.x < (uint32_t)MCHUNK) {
+            const uint32_t t = c0 + threadIdx.x * gridDim.x;
+            MergeTile x;
+            const bool ok = t < nt1 && resolve_merge_tile(c, t, jp, js, x);
+            put_merge_tile(sm.mtab[threadIdx.x], ok, x);
         }
-        if (b) par1 ^= 1u;
-        else par0 ^= 1u;
-        merge_compute<BS>(cur, sm.u.mg[b]);
-        __syncthreads();  // buffer b is free again; the tails staged for b^1 are visible
-        cur = nxt;
-        t = tn;
-        have = hn;
-        b ^= 1u;
+        __syncthreads();
+        int k = 0;
+        while (k < MCHUNK && !sm.mtab[k][0]) ++k;
+        MergeTile cur, nxt;
+        if (k < MCHUNK) {
+            get_merge_tile(sm.mtab[k], cur);
+            merge_stage<BS>(cur, sm.u.mg[b], &sm.mbar[b]);
+        }
+        __syncthreads();
+        while (k < MCHUNK) {
+            int kn = k + 1;
+            while (kn < MCHUNK && !sm.mtab[kn][0]) ++kn;
+            if (kn < MCHUNK) {
+                get_merge_tile(sm.mtab[kn], nxt);
+                merge_stage<BS>(nxt, sm.u.mg[b ^ 1u], &sm.mbar[b ^ 1u]);
+            }
+            const bool landed = mbar_wait(&sm.mbar[b], b ? par1 : par0, c.timeout_ns);
+            if (b) par1 ^= 1u;
+            else par0 ^= 1u;
+            merge_compute<BS>(cur, sm.u.mg[b]);
+            // buffer b is free again and the tails staged for b^1 are visible; a wait that ran
+            // out anywhere in the block is seen by every thread here, so all leave together
+            if (__syncthreads_or(!landed)) {
+                if (threadIdx.x == 0) set_err(ctl, TREES_ERR_TIMEOUT, 0x80000000u | (c0 + (uint32_t)k * gridDim.x));
+                if (kn < MCHUNK) mbar_wait(&sm.mbar[b ^ 1u], b ? par0 : par1, c.timeout_ns);  // let the copy land
+                __syncthreads();
+                return;
+            }
+            cur = nxt;
+            k = kn;
+            b ^= 1u;
+        }
     }
 }
 
