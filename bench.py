@@ -220,6 +220,23 @@ def bfs_alg_bytes(row_ptr, level):
     return 8 * edges + 48 * nreach, edges
 
 
+# ------------------------------------------------------------ multi-rank
+
+def reduce_max_ms(total_ms, dist, device):
+    """The timed region's length as the slowest rank saw it (max over ranks)."""
+    if dist is None:
+        return total_ms
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, tasks_per_step, total_ms):
+    """Whole-job throughput: every rank runs `steps` replicas of the task tree."""
+    return world * steps * tasks_per_step / (total_ms / 1000.0)
+
+
 # ------------------------------------------------------------ runners
 
 def timed_runs(T, torch, ctx, job, steps, warmup, stream, flush=None, setup=None):
@@ -468,14 +485,10 @@ def main():
     sms = T.trees_geometry(ctx)[2]
     result = T.trees_result(ctx, 0)
     assert result == 5702887, result
-    total_ms = sum(times)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max_ms(sum(times), dist, "cuda")
     tasks = stats["tasks"]
     ms_step = total_ms / args.steps
-    value = world * args.steps * tasks / (total_ms / 1000.0)
+    value = job_value(world, args.steps, tasks, total_ms)
     us_epoch = 1000.0 * ms_step / stats["epochs"]
     floor_us = T.trees_barrier_floor(ctx, 20000, stream)
     T.trees_destroy(ctx)
