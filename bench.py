@@ -45,7 +45,7 @@ def parse_args():
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file for the autotuner's choices (default: tune afresh every run)")
     ap.add_argument("--profile-case", default=None,
-                    help="PROGRAM:SIZE[:BLOCK[:SLOTS_PER_THREAD]] -- run one small case twice and exit "
+                    help="PROGRAM:SIZE[:BLOCK[:SLOTS_PER_THREAD[:SCHEDULER]]] -- run one small case twice and exit "
                          "(for ncu): fib:N, sort:LOG2KEYS, bfs:RMAT_SCALE")
     return ap.parse_args()
 
@@ -60,6 +60,7 @@ def profile_case(spec):
     prog, size = parts[0], int(parts[1])
     bs = int(parts[2]) if len(parts) > 2 else 1024
     tpt = int(parts[3]) if len(parts) > 3 else 2
+    sched = {"persistent": 0, "graph": 1, "hostloop": 2}[parts[4]] if len(parts) > 4 else 0
     torch.cuda.set_device(0)
     s = torch.cuda.current_stream()
     keep = []
@@ -67,21 +68,23 @@ def profile_case(spec):
         a, b = 0, 1
         for _ in range(size + 1):
             a, b = b, a + b
-        ctx = T.trees_create(2 * a + 1024, T.trees_default_config(block_size=bs, tasks_per_thread=tpt, map_capacity=1))
+        ctx = T.trees_create(2 * a + 1024, T.trees_default_config(block_size=bs, tasks_per_thread=tpt, map_capacity=1, scheduler=sched))
         job = T.make_job(T.TREES_PROG_FIB, n=size)
     elif prog == "sort":
         n = 1 << size
         kd = torch.from_numpy(gen.keys_u32(1, n).view(np.int32)).cuda()
         sc = torch.empty_like(kd)
         keep += [kd, sc]
-        ctx = T.trees_create(max(4 * n // 1024, 1024), T.trees_default_config(block_size=bs, tasks_per_thread=tpt))
+        ctx = T.trees_create(max(4 * n // 1024, 1024),
+                             T.trees_default_config(block_size=bs, tasks_per_thread=tpt, scheduler=sched))
         job = T.make_job(T.TREES_PROG_MERGESORT, n=n, keys=kd, scratch=sc)
     elif prog == "bfs":
         row_ptr, col, _ = gen.rmat(size, 16, seed=2)
         rp, cl = torch.from_numpy(row_ptr).cuda(), torch.from_numpy(col).cuda()
         lv = torch.empty(row_ptr.size - 1, dtype=torch.int32, device="cuda")
         keep += [rp, cl, lv]
-        ctx = T.trees_create(row_ptr.size + 1024, T.trees_default_config(block_size=bs, tasks_per_thread=tpt))
+        ctx = T.trees_create(row_ptr.size + 1024,
+                             T.trees_default_config(block_size=bs, tasks_per_thread=tpt, scheduler=sched))
         job = T.make_job(T.TREES_PROG_BFS, n=0, row_ptr=rp, col=cl, level=lv, nv=row_ptr.size - 1)
     else:
         raise SystemExit(f"unknown profile case {spec}")

@@ -175,8 +175,11 @@ typedef struct {
     uint32_t forks;   /* nextFreeCore - oldNextFreeCore */
     uint32_t joined;  /* joinScheduled */
     uint32_t maps;    /* map operations scheduled */
-    uint32_t pad;
-    uint64_t t_ns;    /* globaltimer at the end of the epoch */
+    uint32_t ns_phase2;    /* persistent scheduler: ns from the previous epoch's end to the
+                            * barrier after Phase 2 (0 under the other schedulers) */
+    uint64_t t_ns;         /* globaltimer at the end of the epoch */
+    uint32_t ns_partition; /* persistent scheduler: ns of the merge partition sub-phase */
+    uint32_t ns_map;       /* persistent scheduler: ns of the map operations */
 } trees_epoch_t;
 
 /* Copies up to `cap` per-epoch records of the last run (config.trace = 1)

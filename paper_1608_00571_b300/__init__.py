@@ -77,7 +77,8 @@ class trees_stats_t(ctypes.Structure):
 class trees_epoch_t(ctypes.Structure):
     _fields_ = [("cen", ctypes.c_uint32), ("lo", ctypes.c_uint32), ("hi", ctypes.c_uint32),
                 ("valid", ctypes.c_uint32), ("forks", ctypes.c_uint32), ("joined", ctypes.c_uint32),
-                ("maps", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("t_ns", ctypes.c_uint64)]
+                ("maps", ctypes.c_uint32), ("ns_phase2", ctypes.c_uint32), ("t_ns", ctypes.c_uint64),
+                ("ns_partition", ctypes.c_uint32), ("ns_map", ctypes.c_uint32)]
 
 
 class trees_job_result_t(ctypes.Structure):

@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(BS) k_epoch(Ctl *ctl, Conf c, unsigned long lo
          t0 += (unsigned long long)gridDim.x * (BS * TPT)) {
         TileLoad<TPT> L;
         tile_load<BS, TPT, PM_ALL>(c, t0, hi, LOAD_ON_DEMAND, L);
-        epoch_tile<BS, TPT, PM_ALL>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, LOAD_ON_DEMAND, L);
+        epoch_tile<BS, TPT, PM_ALL>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, LOAD_ON_DEMAND, L,
+                                    hi - lo <= (uint32_t)(BS * TPT));
         par ^= 1;
     }
     trace_valid_add<BS>(c, e, acc.valid, sm);
@@ -180,7 +181,9 @@ __global__ void k_phase3(Ctl *ctl, Conf c, cudaGraphConditionalHandle h) {
             r.forks = f;
             r.joined = jf;
             r.maps = (uint32_t)(mt >> 40) + (uint32_t)(me >> 40);
-            r.pad = 0u;
+            r.ns_phase2 = 0u;
+            r.ns_partition = 0u;
+            r.ns_map = 0u;
             r.t_ns = globaltimer();
             c.trace[e] = r;
         }
@@ -268,9 +271,11 @@ bool kern_by(int bs, int tpt, Kern *k) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+constexpr int NMT = 7;  // tiled-map descriptor columns: kind, a, b, c, job, first tile, split
+
 struct Layout {
     size_t off_dev, off_code, off_a0, off_a1, off_link, off_result;
-    size_t off_mt[8], off_me[4], off_trace, off_tvalid, off_gstack, off_blk, total;
+    size_t off_mt[NMT], off_me[4], off_trace, off_tvalid, off_gstack, off_blk, total;
 };
 
 Layout make_layout(size_t cap, size_t mcap, size_t trace_cap, size_t gstack_cap) {
@@ -287,7 +292,7 @@ Layout make_layout(size_t cap, size_t mcap, size_t trace_cap, size_t gstack_cap)
     L.off_a1 = take(cap * 4);
     L.off_link = take(cap * 4);
     L.off_result = take(cap * 8);
-    for (int i = 0; i < 8; ++i) L.off_mt[i] = take(mcap * 4);
+    for (int i = 0; i < NMT; ++i) L.off_mt[i] = take(mcap * 4);
     for (int i = 0; i < 4; ++i) L.off_me[i] = take(mcap * 4);
     L.off_trace = take(trace_cap * sizeof(trees_epoch_t));
     L.off_tvalid = take(trace_cap * 4);
@@ -399,9 +404,8 @@ static int finish_create(trees_ctx *x) {
     c.link = reinterpret_cast<uint32_t *>(m + L.off_link);
     c.result = reinterpret_cast<unsigned long long *>(m + L.off_result);
     c.cap = x->cap;
-    uint32_t **mt[8] = {&c.mt_kind, &c.mt_a,        &c.mt_b,        &c.mt_c,
-                         &c.mt_job,  &c.mt_tilebase, &c.mt_tiledesc, &c.mt_split};
-    for (int i = 0; i < 8; ++i) *mt[i] = reinterpret_cast<uint32_t *>(m + L.off_mt[i]);
+    uint32_t **mt[NMT] = {&c.mt_kind, &c.mt_a, &c.mt_b, &c.mt_c, &c.mt_job, &c.mt_tilebase, &c.mt_split};
+    for (int i = 0; i < NMT; ++i) *mt[i] = reinterpret_cast<uint32_t *>(m + L.off_mt[i]);
     uint32_t **me[4] = {&c.me_v, &c.me_base, &c.me_job, &c.me_tfd};
     for (int i = 0; i < 4; ++i) *me[i] = reinterpret_cast<uint32_t *>(m + L.off_me[i]);
     c.mcap = x->mcap;
@@ -1036,9 +1040,8 @@ extern "C" int trees_fib_noalloc(uint32_t n, uint32_t cutoff, uint64_t *dev_resu
     c.link = reinterpret_cast<uint32_t *>(m0 + L.off_link);
     c.result = reinterpret_cast<unsigned long long *>(m0 + L.off_result);
     c.cap = (uint32_t)NOALLOC_CAP;
-    uint32_t **mt[8] = {&c.mt_kind, &c.mt_a,        &c.mt_b,        &c.mt_c,
-                         &c.mt_job,  &c.mt_tilebase, &c.mt_tiledesc, &c.mt_split};
-    for (int i = 0; i < 8; ++i) *mt[i] = reinterpret_cast<uint32_t *>(m0 + L.off_mt[i]);
+    uint32_t **mt[NMT] = {&c.mt_kind, &c.mt_a, &c.mt_b, &c.mt_c, &c.mt_job, &c.mt_tilebase, &c.mt_split};
+    for (int i = 0; i < NMT; ++i) *mt[i] = reinterpret_cast<uint32_t *>(m0 + L.off_mt[i]);
     uint32_t **me[4] = {&c.me_v, &c.me_base, &c.me_job, &c.me_tfd};
     for (int i = 0; i < 4; ++i) *me[i] = reinterpret_cast<uint32_t *>(m0 + L.off_me[i]);
     c.mcap = 1;

@@ -21,14 +21,15 @@ constexpr uint32_t NTT = TREES_NUM_TASK_TYPES;  // NumTaskTypes of footnote 2, S
 constexpr int STK_CAP = 512;                    // epoch-range stack entries per job
 constexpr int LEAF_MAX = 1024;                  // largest leaf a block sorts in shared memory
 constexpr uint32_t MERGE_TILE = 2048;           // outputs of one merge-path tile
-constexpr uint32_t MERGE_BUF = 2 * MERGE_TILE + 8; // keys of one staged tile: A run, 16-B gap, B run
+constexpr uint32_t MERGE_STAGE = MERGE_TILE + 16; // words of one staged tile: A's and B's 16-byte chunks, packed
+constexpr int MERGE_NST = 4;                    // merge tiles staged per block (ring of TMA buffers)
 constexpr uint32_t EXPAND_TILE = 2048;          // adjacency entries of one BFS expansion tile
-constexpr int MCHUNK = 32;                      // merge tiles a block resolves at once
+constexpr int MCHUNK = 64;                      // merge tiles a block resolves at once
 constexpr unsigned long long CTR_LOW_MASK = (1ull << 40) - 1;  // map counters: (descs << 40) | units
 
 enum MapKind : uint32_t { MAP_LEAF_SORT = 1, MAP_MERGE = 2, MAP_EXPAND = 3 };
-constexpr int TPT_MAX = 4;
-constexpr int NBLK_STATS = 8192;                // per-block statistics slots                      // largest number of slots a thread takes per tile
+constexpr int TPT_MAX = 4;                      // largest number of slots a thread takes per tile
+constexpr int NBLK_STATS = 8192;                // per-block statistics slots
 
 struct Range {
     uint32_t cen, lo, hi;  // epoch number and NDRange [lo, hi) (Sec. 5.1.2)
@@ -53,7 +54,7 @@ struct Conf {
     unsigned long long *result;
     uint32_t cap;
     // tiled map list: one descriptor per map operation, `units` tiles each
-    uint32_t *mt_kind, *mt_a, *mt_b, *mt_c, *mt_job, *mt_tilebase, *mt_tiledesc, *mt_split;
+    uint32_t *mt_kind, *mt_a, *mt_b, *mt_c, *mt_job, *mt_tilebase, *mt_split;
     // element map list (BFS expansion): one descriptor per vertex, one unit per edge
     uint32_t *me_v, *me_base, *me_job, *me_tfd;
     uint32_t mcap;
@@ -147,7 +148,8 @@ struct Smem {
     unsigned int bc32[4];
     unsigned long long bc64[4];
     int bar_ok;
-    unsigned long long mbar[2];           // mbarriers of the two merge buffers
+    unsigned long long mbar[MERGE_NST];   // mbarriers of the merge stage buffers
+    unsigned long long mvalid;            // which entries of mtab are merge tiles
     uint32_t mtab[MCHUNK][12];            // the block's next merge tiles, resolved in parallel
     unsigned int ep_cnt, ep_join;         // the epoch's counters, read right after its barrier
     unsigned long long ep_mt, ep_me;
@@ -157,15 +159,11 @@ struct Smem {
     uint32_t next, cen, lo, hi, base, rjoin;
     int stop;
     union alignas(16) {
-        uint32_t mg[2][MERGE_BUF];  // double-buffered merge tile inputs (TMA destinations)
+        uint32_t mg[MERGE_NST][MERGE_STAGE];  // staged merge tile inputs (TMA destinations)
         struct {
             uint32_t base[EXPAND_TILE + 2];
             uint32_t v[EXPAND_TILE + 2];
         } ex;
-        struct {
-            uint32_t toff[BS * TPT_MAX];  // tile offset of each tiled map request, by request rank
-            uint32_t di[BS * TPT_MAX];    // its descriptor index
-        } rq;
     } u;
 };
 

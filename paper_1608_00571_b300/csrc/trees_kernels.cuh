@@ -62,6 +62,9 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM)) k_persisten
     }
     unsigned long long forks_total = 0;
     uint32_t peak = 1u;
+    // trace timestamps (block 0, thread 0): previous epoch's end, end of Phase 2, of partition, of maps
+    const bool stamp = c.trace_on && blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long t_prev = stamp ? globaltimer() : 0ull, t_p2 = 0ull, t_pt = 0ull, t_mp = 0ull;
     uint32_t e = 0;
     for (;; ++e) {
         // Phase 1: pop (CEN, NDRange); oldNextFreeCore = nextFreeCore
@@ -97,6 +100,7 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM)) k_persisten
         const uint32_t v0 = acc.valid;
         // tiles grid-stride over [lo, hi); the next tile's columns load while this one runs
         int par = 0;
+        const bool solo = hi - lo <= (uint32_t)(BS * TPT);  // only block 0 has a tile
         const unsigned long long step = (unsigned long long)gridDim.x * (BS * TPT);
         unsigned long long t0 = (unsigned long long)lo + (unsigned long long)blockIdx.x * (BS * TPT);
         TileLoad<TPT> cur, nxt;
@@ -104,23 +108,26 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM)) k_persisten
         for (; t0 < hi; t0 += step) {
             const bool more = t0 + step < hi;
             if (more) tile_load<BS, TPT, PM>(c, t0 + step, hi, mode, nxt);
-            epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode, cur);
+            epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode, cur, solo);
             if (more) cur = nxt;
             par ^= 1;
         }
         trace_valid_add<BS>(c, e, acc.valid - v0, sm);
         if ((int32_t)e == c.stall_epoch && blockIdx.x == gridDim.x - 1) return;  // test hook: never arrives
         if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, ep)) break;
+        if (stamp) t_p2 = t_pt = t_mp = globaltimer();
         const unsigned long long mt = sm.ep_mt, me = sm.ep_me;
         if (mt | me) {  // the map operations of this epoch run before the next one (Sec. 5.2.4)
             if constexpr ((PM & PM_MS) != 0u) {
                 if (needs_partition(mt)) {
                     partition_phase<BS>(c, mt, nullptr, 0u);
                     if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, ep)) break;
+                    if (stamp) t_pt = t_mp = globaltimer();
                 }
             }
             map_phase<BS, PM>(c, ctl, sm, ep, e, cen, base, mt, me);
             if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, ep)) break;
+            if (stamp) t_mp = globaltimer();
         }
         // Phase 3: push the join range, then the fork range; or give the range back
         if (threadIdx.x == 0) {
@@ -153,8 +160,11 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM)) k_persisten
                     r.forks = f;
                     r.joined = jf;
                     r.maps = (uint32_t)(mt >> 40) + (uint32_t)(me >> 40);
-                    r.pad = 0u;
                     r.t_ns = globaltimer();
+                    r.ns_phase2 = (uint32_t)(t_p2 - t_prev);
+                    r.ns_partition = (uint32_t)(t_pt - t_p2);
+                    r.ns_map = (uint32_t)(t_mp - t_pt);
+                    t_prev = r.t_ns;
                     c.trace[e] = r;
                 }
             }

@@ -289,21 +289,9 @@ __device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan (&p)
                 c.mt_c[di] = cen;
                 c.mt_job[di] = job;
                 c.mt_tilebase[di] = tbase + toff;
-                sm.u.rq.toff[rank] = toff;
-                sm.u.rq.di[rank] = di;
                 acc.maps++;
                 ++rank;
                 toff += p[k].n;
-            }
-            __syncthreads();
-            for (uint32_t t = threadIdx.x; t < ntile; t += BS) {
-                uint32_t lo = 0, hi = ndesc;  // last request whose first tile is <= t
-                while (hi - lo > 1u) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (sm.u.rq.toff[mid] <= t) lo = mid;
-                    else hi = mid;
-                }
-                c.mt_tiledesc[tbase + t] = sm.u.rq.di[lo];
             }
         }
     }
@@ -378,7 +366,7 @@ __device__ __forceinline__ void tile_load(const Conf &c, unsigned long long t0, 
 template <int BS, int TPT, uint32_t PM>
 __device__ __forceinline__ void epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, unsigned long long t0, uint32_t hi,
                                            uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, Acc &acc, int par,
-                                           int mode, const TileLoad<TPT> &L) {
+                                           int mode, const TileLoad<TPT> &L, bool solo) {
     constexpr bool fresh_a1 = (PM & (PM_MS | PM_NQ)) != 0u;
     constexpr bool join_a0 = (PM & (PM_MS | PM_NQ | PM_TRAV)) != 0u;
     constexpr bool join_link = (PM & (PM_FIB | PM_NQ)) != 0u;
@@ -417,17 +405,30 @@ __device__ __forceinline__ void epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm
 #pragma unroll
     for (int k = 0; k < TPT; ++k) all += tot[k];
     if (all) {
-        if (threadIdx.x == 0) {
-            const uint32_t b = atomicAdd(&ctl->cnt[ep], all);  // one atomic per block (Sec. 5.2.3)
-            const bool over = (unsigned long long)base + b + all > c.cap;
-            if (over) set_err(ctl, TREES_ERR_CAPACITY, e);
-            sm.bc32[par] = b;
-            sm.bc32[2 + par] = over;
+        // solo: this tile is the whole range, so no other block forks this epoch, its children
+        // start at offset 0 and the count is published without waiting for the atomic's answer
+        uint32_t b0 = 0u, over0 = 0u;
+        if (solo) {
+            over0 = (unsigned long long)base + all > c.cap;
+            if (threadIdx.x == 0) {
+                atomicAdd(&ctl->cnt[ep], all);  // result unused: a fire-and-forget reduction
+                if (over0) set_err(ctl, TREES_ERR_CAPACITY, e);
+            }
+        } else {
+            if (threadIdx.x == 0) {
+                const uint32_t b = atomicAdd(&ctl->cnt[ep], all);  // one atomic per block (Sec. 5.2.3)
+                const bool over = (unsigned long long)base + b + all > c.cap;
+                if (over) set_err(ctl, TREES_ERR_CAPACITY, e);
+                sm.bc32[par] = b;
+                sm.bc32[2 + par] = over;
+            }
+            __syncthreads();
+            b0 = sm.bc32[par];
+            over0 = sm.bc32[2 + par];
         }
-        __syncthreads();
         uint32_t joined = 0u;
-        if (!sm.bc32[2 + par]) {
-            uint32_t kbase = base + sm.bc32[par];
+        if (!over0) {
+            uint32_t kbase = base + b0;
 #pragma unroll
             for (int k = 0; k < TPT; ++k) {
                 if (nf[k]) joined += commit_task<PM>(c, c.rp, p[k], cen, kbase + ex[k]);
@@ -514,7 +515,7 @@ __device__ __forceinline__ void warp_leaf_sort(const uint32_t *in, uint32_t *out
             }
         }
     }
-    if (n == 1024u && ((lo & 3u) == 0u)) {
+    if (n == 1024u && ((reinterpret_cast<uintptr_t>(out + lo) & 15u) == 0u)) {  // the address, not just lo
         uint4 *o = reinterpret_cast<uint4 *>(out + lo + 32u * lane);
 #pragma unroll
         for (int q = 0; q < 8; ++q) o[q] = make_uint4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
@@ -525,28 +526,6 @@ __device__ __forceinline__ void warp_leaf_sort(const uint32_t *in, uint32_t *out
             if (i < n) out[lo + i] = x[r];
         }
     }
-}
-
-// Merge path (Odeh et al., "Merge Path -- parallel merging made simple",
-// IPDPSW 2012): the number of A elements among the first `diag` outputs of the
-// stable merge of sorted A and B.  A group of G lanes (gmask) probes G points
-// per step.
-template <int G>
-__device__ __forceinline__ uint32_t group_merge_path(const uint32_t *A, uint32_t la, const uint32_t *B, uint32_t lb,
-                                                     uint32_t diag, uint32_t gmask, uint32_t glane) {
-    uint32_t lo = diag > lb ? diag - lb : 0u, hi = diag < la ? diag : la;
-    while (hi > lo) {
-        const uint32_t step = (hi - lo + G - 1u) / G;
-        const uint32_t m = lo + glane * step;
-        bool pr = false;
-        if (m < hi) pr = A[m] <= B[diag - 1u - m];
-        const uint32_t cnt = (uint32_t)__popc(__ballot_sync(gmask, pr) & gmask);
-        const uint32_t nlo = cnt ? lo + (cnt - 1u) * step + 1u : lo;
-        const uint32_t cap = lo + cnt * step;
-        hi = cap < hi ? cap : hi;
-        lo = nlo;
-    }
-    return lo;
 }
 
 // The sorted runs a merge at depth d reads (depth d+1) and writes (depth d):
@@ -569,30 +548,101 @@ __device__ __forceinline__ void job_buffers(const Conf &c, const RunParams *job_
     }
 }
 
+// The descriptor that owns tile t of the epoch's tiled map list.  One atomic
+// hands out a request's descriptors and tiles together, so descriptors own
+// consecutive tile ranges in descriptor order and mt_tilebase is
+// non-decreasing: the owner is the last descriptor whose first tile is <= t.
+// The proportional guess t * ndesc / ntile is exact when the descriptors have
+// equal tile counts (every level of a mergesort); else a binary search.
+__device__ __forceinline__ uint32_t tile_owner(const Conf &c, uint32_t t, uint32_t ndesc, uint32_t ntile) {
+    const uint32_t g = (uint32_t)((unsigned long long)t * ndesc / ntile);
+    const uint32_t b0 = c.mt_tilebase[g];
+    const uint32_t b1 = g + 1u < ndesc ? c.mt_tilebase[g + 1u] : ntile;
+    if (b0 <= t && t < b1) return g;
+    uint32_t lo = 0u, hi = ndesc;  // tilebase[lo] <= t < tilebase[hi] (tilebase[ndesc] = ntile)
+    while (hi - lo > 1u) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (c.mt_tilebase[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Partition sub-phase of a map epoch: the merge-path split at the first
 // output of every merge tile that does not start its merge, computed in
-// parallel by groups of 8 lanes for all tiles at once.
+// parallel by groups of 4 lanes for all tiles at once.  A group runs the
+// searches of up to PNS tiles side by side, so their global loads overlap
+// and the phase costs about one search's chain of dependent loads.
 template <int BS>
 __device__ void partition_phase(const Conf &c, unsigned long long mt, const RunParams *job_params, uint32_t job_stride) {
-    constexpr uint32_t G = 8;
-    const uint32_t nt1 = (uint32_t)(mt & CTR_LOW_MASK);
+    constexpr uint32_t G = 4, PNS = 4;  // 4 probes a step: fewer scattered DRAM sectors per step than 8
+    const uint32_t nt1 = (uint32_t)(mt & CTR_LOW_MASK), nd1 = (uint32_t)(mt >> 40);
     const uint32_t glane = threadIdx.x % G;
-    const uint32_t gmask = 0xFFu << ((threadIdx.x & 31u) & ~(G - 1u));
+    static_assert(G >= 1u && G <= 32u && (G & (G - 1u)) == 0u, "groups tile the warp");
+    const uint32_t gmask = (uint32_t)((1ull << G) - 1ull) << ((threadIdx.x & 31u) & ~(G - 1u));  // this group's lanes
     const uint32_t gid = (blockIdx.x * BS + threadIdx.x) / G, ng = gridDim.x * BS / G;
-    for (uint32_t t = gid; t < nt1; t += ng) {
-        const uint32_t di = c.mt_tiledesc[t];
-        if (c.mt_kind[di] != MAP_MERGE) continue;
-        const uint32_t tin = t - c.mt_tilebase[di];
-        if (tin == 0u) {
-            if (glane == 0u) c.mt_split[t] = 0u;
-            continue;
+    for (uint32_t t0 = gid; t0 < nt1; t0 += PNS * ng) {
+        const uint32_t *A[PNS], *B[PNS];
+        uint32_t diag[PNS], lo[PNS], hi[PNS], tt[PNS];
+        bool want[PNS];
+#pragma unroll
+        for (uint32_t q = 0; q < PNS; ++q) {
+            const uint32_t t = t0 + q * ng;
+            tt[q] = t;
+            want[q] = false;
+            lo[q] = hi[q] = diag[q] = 0u;
+            A[q] = B[q] = nullptr;
+            if (t >= nt1) continue;
+            const uint32_t di = tile_owner(c, t, nd1, nt1);
+            if (c.mt_kind[di] != MAP_MERGE) continue;
+            want[q] = true;
+            const uint32_t tin = t - c.mt_tilebase[di];
+            if (tin == 0u) continue;  // split 0, no search
+            const uint32_t a = c.mt_a[di], b = c.mt_b[di], cc = c.mt_c[di], mid = a + (b - a) / 2u;
+            uint32_t *keys, *scratch;
+            job_buffers(c, job_params, job_stride, c.mt_job[di], &keys, &scratch);
+            const uint32_t *in = (cc & 1u) ? keys : scratch;
+            const uint32_t la = mid - a, lb = b - mid, d = tin * MERGE_TILE;
+            A[q] = in + a;
+            B[q] = in + mid;
+            diag[q] = d;
+            lo[q] = d > lb ? d - lb : 0u;
+            hi[q] = d < la ? d : la;
         }
-        const uint32_t lo = c.mt_a[di], hi = c.mt_b[di], cc = c.mt_c[di], mid = lo + (hi - lo) / 2u;
-        uint32_t *keys, *scratch;
-        job_buffers(c, job_params, job_stride, c.mt_job[di], &keys, &scratch);
-        const uint32_t *in = (cc & 1u) ? keys : scratch;
-        const uint32_t r = group_merge_path<G>(in + lo, mid - lo, in + mid, hi - mid, tin * MERGE_TILE, gmask, glane);
-        if (glane == 0u) c.mt_split[t] = r;
+        // merge path (Odeh et al., "Merge Path -- parallel merging made simple", IPDPSW 2012):
+        // the split is the number of A keys among the first diag outputs, A winning ties; G probes
+        // per search and step
+        for (;;) {
+            bool pr[PNS], any = false;
+            uint32_t step[PNS];
+#pragma unroll
+            for (uint32_t q = 0; q < PNS; ++q) {
+                pr[q] = false;
+                step[q] = 0u;
+                if (hi[q] > lo[q]) {
+                    any = true;
+                    step[q] = (hi[q] - lo[q] + G - 1u) / G;
+                    const uint32_t m = lo[q] + glane * step[q];
+                    if (m < hi[q]) pr[q] = A[q][m] <= B[q][diag[q] - 1u - m];
+                }
+            }
+            if (!any) break;  // lo and hi are the same on every lane of the group
+#pragma unroll
+            for (uint32_t q = 0; q < PNS; ++q) {
+                if (hi[q] > lo[q]) {
+                    const uint32_t cnt = (uint32_t)__popc(__ballot_sync(gmask, pr[q]) & gmask);
+                    const uint32_t nlo = cnt ? lo[q] + (cnt - 1u) * step[q] + 1u : lo[q];
+                    const uint32_t cap = lo[q] + cnt * step[q];
+                    hi[q] = cap < hi[q] ? cap : hi[q];
+                    lo[q] = nlo;
+                }
+            }
+        }
+        if (glane == 0u) {
+#pragma unroll
+            for (uint32_t q = 0; q < PNS; ++q)
+                if (want[q]) c.mt_split[tt[q]] = lo[q];
+        }
     }
 }
 
@@ -602,13 +652,13 @@ __device__ void partition_phase(const Conf &c, unsigned long long mt, const RunP
 struct MergeTile {
     const uint32_t *in;
     uint32_t *out;
-    uint32_t lo, mid, d0, i0, i1, j0, j1;
+    uint32_t lo, mid, hi, d0, i0, i1, j0, j1;
 };
 
 // Resolves merge tile t of the tiled map list (false when it is not a merge).
-__device__ __forceinline__ bool resolve_merge_tile(const Conf &c, uint32_t t, const RunParams *jp, uint32_t js,
-                                                   MergeTile &m) {
-    const uint32_t di = c.mt_tiledesc[t];
+__device__ __forceinline__ bool resolve_merge_tile(const Conf &c, uint32_t t, uint32_t nd1, uint32_t nt1,
+                                                   const RunParams *jp, uint32_t js, MergeTile &m) {
+    const uint32_t di = tile_owner(c, t, nd1, nt1);
     if (c.mt_kind[di] != MAP_MERGE) return false;
     uint32_t *keys, *scratch;
     job_buffers(c, jp, js, c.mt_job[di], &keys, &scratch);
@@ -619,6 +669,7 @@ __device__ __forceinline__ bool resolve_merge_tile(const Conf &c, uint32_t t, co
     m.out = (cc & 1u) ? scratch : keys;  // this node's run (depth d)
     m.lo = lo;
     m.mid = lo + la;
+    m.hi = hi;
     m.d0 = tin * MERGE_TILE;
     m.i0 = tin ? c.mt_split[t] : 0u;
     m.i1 = tin + 1u < ntiles ? c.mt_split[t + 1u] : la;
@@ -627,26 +678,65 @@ __device__ __forceinline__ bool resolve_merge_tile(const Conf &c, uint32_t t, co
     return true;
 }
 
-// Starts staging a tile into buf: thread 0 issues the bulk copies of the
-// 16-byte aligned middle of each run (TMA, completing on bar); every thread
-// loads its share of the unaligned ends.  A lands at buf[0..), B at
-// buf[T + 4 ..), each shifted by its start's offset within 16 bytes.
+// Where a staged tile lives in its buffer: A's keys widened to whole 16-byte
+// chunks [as4, ae4u) at word 0, B's chunks [bs4, be4u) right behind them at
+// word sbo (a multiple of 4, so both bulk copies start 16-byte aligned).  The
+// two spans hold at most T + 12 words.
+struct StageLayout {
+    uint32_t as, ae, bs, be, as4, ae4u, bs4, be4u, sbo;
+};
+
+__device__ __forceinline__ StageLayout stage_layout(const MergeTile &m) {
+    StageLayout L;
+    L.as = m.lo + m.i0;
+    L.ae = m.lo + m.i1;
+    L.bs = m.mid + m.j0;
+    L.be = m.mid + m.j1;
+    L.as4 = L.as & ~3u;
+    L.ae4u = (L.ae + 3u) & ~3u;
+    L.bs4 = L.bs & ~3u;
+    L.be4u = (L.be + 3u) & ~3u;
+    L.sbo = L.ae > L.as ? L.ae4u - L.as4 : 0u;
+    return L;
+}
+
+// Starts staging a tile into buf: thread 0 issues one bulk copy (TMA,
+// completing on bar) per run over its whole 16-byte chunks.  A chunk may
+// reach past the run but never past the merge's end hi, which is inside the
+// array; a last partial chunk beyond hi (hi not a multiple of 4) is loaded
+// with plain loads, and so is everything when the array is not 16-byte
+// aligned.
 template <int BS>
 __device__ __forceinline__ void merge_stage(const MergeTile &m, uint32_t *buf, unsigned long long *bar) {
-    const uint32_t as = m.lo + m.i0, ae = m.lo + m.i1, bs = m.mid + m.j0, be = m.mid + m.j1;
-    const uint32_t as4 = as & ~3u, ae4 = ae & ~3u, bs4 = bs & ~3u, be4 = be & ~3u;
-    uint32_t *sb = buf + MERGE_TILE + 4u;
-    const bool aligned = (reinterpret_cast<uintptr_t>(m.in) & 15u) == 0u;  // else plain loads only
-    const uint32_t abytes = aligned && ae4 > as4 ? (ae4 - as4) * 4u : 0u;
-    const uint32_t bbytes = aligned && be4 > bs4 ? (be4 - bs4) * 4u : 0u;
+    const StageLayout L = stage_layout(m);
+    uint32_t *sb = buf + L.sbo;
+    const bool aligned = (reinterpret_cast<uintptr_t>(m.in) & 15u) == 0u;
+    const uint32_t ac = L.ae4u <= m.hi ? L.ae4u : (L.ae & ~3u);  // end of A's bulk-copied chunks
+    const uint32_t bc = L.be4u <= m.hi ? L.be4u : (L.be & ~3u);
+    const uint32_t abytes = aligned && L.ae > L.as && ac > L.as4 ? (ac - L.as4) * 4u : 0u;
+    const uint32_t bbytes = aligned && L.be > L.bs && bc > L.bs4 ? (bc - L.bs4) * 4u : 0u;
     if (threadIdx.x == 0) {
         fence_proxy_async_smem();  // earlier generic reads of buf come before the async writes
         mbar_arrive_expect(bar, abytes + bbytes);
-        if (abytes) tma_load_1d(buf, m.in + as4, abytes, bar);
-        if (bbytes) tma_load_1d(sb, m.in + bs4, bbytes, bar);
+        if (abytes) tma_load_1d(buf, m.in + L.as4, abytes, bar);
+        if (bbytes) tma_load_1d(sb, m.in + L.bs4, bbytes, bar);
     }
-    for (uint32_t x = (abytes ? ae4 : as) + threadIdx.x; x < ae; x += BS) buf[x - as4] = m.in[x];
-    for (uint32_t x = (bbytes ? be4 : bs) + threadIdx.x; x < be; x += BS) sb[x - bs4] = m.in[x];
+    for (uint32_t x = (abytes ? ac : L.as) + threadIdx.x; x < L.ae; x += BS) buf[x - L.as4] = m.in[x];
+    for (uint32_t x = (bbytes ? bc : L.bs) + threadIdx.x; x < L.be; x += BS) sb[x - L.bs4] = m.in[x];
+}
+
+// Merge-path split of diagonal d (Odeh et al.'s merge path, for the tile
+// merges of Sec. 5.2.4): how many of the first d outputs of merging sa[0, na)
+// and sb[0, nb) come from A, A winning ties.
+__device__ __forceinline__ uint32_t smem_merge_path(const uint32_t *sa, uint32_t na, const uint32_t *sb, uint32_t nb,
+                                                    uint32_t d) {
+    uint32_t a = d > nb ? d - nb : 0u, b = d < na ? d : na;
+    while (a < b) {
+        const uint32_t mid = (a + b) >> 1;
+        if (sa[mid] <= sb[d - 1u - mid]) a = mid + 1u;
+        else b = mid;
+    }
+    return a;
 }
 
 // Merges a staged tile: each thread finds its first output's merge-path split
@@ -655,25 +745,38 @@ __device__ __forceinline__ void merge_stage(const MergeTile &m, uint32_t *buf, u
 template <int BS>
 __device__ __forceinline__ void merge_compute(const MergeTile &m, const uint32_t *buf) {
     constexpr uint32_t MPT = MERGE_TILE / BS;
+    const StageLayout L = stage_layout(m);
     const uint32_t na = m.i1 - m.i0, nb = m.j1 - m.j0, nt = na + nb;
-    const uint32_t *sa = buf + ((m.lo + m.i0) & 3u);
-    const uint32_t *sb = buf + MERGE_TILE + 4u + ((m.mid + m.j0) & 3u);
+    const uint32_t *sa = buf + (L.as - L.as4);
+    const uint32_t *sb = buf + L.sbo + (L.bs - L.bs4);
     const uint32_t dd = min((uint32_t)threadIdx.x * MPT, nt);
-    uint32_t a = dd > nb ? dd - nb : 0u, b = dd < na ? dd : na;
-    while (a < b) {
-        const uint32_t mid = (a + b) >> 1;
-        if (sa[mid] <= sb[dd - 1u - mid]) a = mid + 1u;
-        else b = mid;
-    }
+    const uint32_t a = smem_merge_path(sa, na, sb, nb, dd);
     uint32_t ia = a, ib = dd - a;
     uint32_t v[MPT];
+#ifdef TREES_MERGE_2LOAD
 #pragma unroll
     for (uint32_t k = 0; k < MPT; ++k) {
         const bool takeA = ia < na && (ib >= nb || sa[ia] <= sb[ib]);
-        v[k] = takeA ? sa[ia] : sb[ib];
+        v[k] = takeA ? sa[ia] : sb[min(ib, nb)];
         ia += takeA;
         ib += !takeA;
     }
+#else
+    // the two run heads stay in registers: one shared-memory load per output.  Indices stop at
+    // the runs' ends (ia never passes na; ib is clamped for the last thread of a short tile), and
+    // a head read at an end stays inside the staged buffer and is never taken.
+    uint32_t ka = sa[ia], kb = sb[ib];
+#pragma unroll
+    for (uint32_t k = 0; k < MPT; ++k) {
+        const bool takeA = ia < na && (ib >= nb || ka <= kb);
+        v[k] = takeA ? ka : kb;
+        ia += takeA;
+        ib += !takeA;
+        const uint32_t x = takeA ? sa[ia] : sb[min(ib, nb)];
+        ka = takeA ? x : ka;
+        kb = takeA ? kb : x;
+    }
+#endif
     uint32_t *o = m.out + m.lo + m.d0 + dd;
     const uint32_t cnt = min(MPT, nt - dd);
     if constexpr (MPT % 4u == 0u) {
@@ -689,15 +792,14 @@ __device__ __forceinline__ void merge_compute(const MergeTile &m, const uint32_t
         if (k < cnt) o[k] = v[k];
 }
 
-__device__ __forceinline__ void put_merge_tile(uint32_t *w, bool ok, const MergeTile &x) {
-    w[0] = ok;
-    if (!ok) return;
-    w[1] = (uint32_t)(reinterpret_cast<uintptr_t>(x.in));
-    w[2] = (uint32_t)(reinterpret_cast<uintptr_t>(x.in) >> 32);
-    w[3] = (uint32_t)(reinterpret_cast<uintptr_t>(x.out));
-    w[4] = (uint32_t)(reinterpret_cast<uintptr_t>(x.out) >> 32);
-    w[5] = x.lo;
-    w[6] = x.mid;
+__device__ __forceinline__ void put_merge_tile(uint32_t *w, const MergeTile &x) {
+    w[0] = (uint32_t)(reinterpret_cast<uintptr_t>(x.in));
+    w[1] = (uint32_t)(reinterpret_cast<uintptr_t>(x.in) >> 32);
+    w[2] = (uint32_t)(reinterpret_cast<uintptr_t>(x.out));
+    w[3] = (uint32_t)(reinterpret_cast<uintptr_t>(x.out) >> 32);
+    w[4] = x.lo;
+    w[5] = x.mid;
+    w[6] = x.hi;
     w[7] = x.d0;
     w[8] = x.i0;
     w[9] = x.i1;
@@ -705,10 +807,11 @@ __device__ __forceinline__ void put_merge_tile(uint32_t *w, bool ok, const Merge
 }
 
 __device__ __forceinline__ void get_merge_tile(const uint32_t *w, MergeTile &m) {
-    m.in = reinterpret_cast<const uint32_t *>((uintptr_t)w[1] | ((uintptr_t)w[2] << 32));
-    m.out = reinterpret_cast<uint32_t *>((uintptr_t)w[3] | ((uintptr_t)w[4] << 32));
-    m.lo = w[5];
-    m.mid = w[6];
+    m.in = reinterpret_cast<const uint32_t *>((uintptr_t)w[0] | ((uintptr_t)w[1] << 32));
+    m.out = reinterpret_cast<uint32_t *>((uintptr_t)w[2] | ((uintptr_t)w[3] << 32));
+    m.lo = w[4];
+    m.mid = w[5];
+    m.hi = w[6];
     m.d0 = w[7];
     m.i0 = w[8];
     m.i1 = w[9];
@@ -717,58 +820,73 @@ __device__ __forceinline__ void get_merge_tile(const uint32_t *w, MergeTile &m) 
 }
 
 // All merge tiles of the epoch handled by this block (tiles blockIdx.x +
-// k*gridDim.x), two-stage pipelined: while the block merges one tile from
-// shared memory, the next tile's runs stream in by TMA.  The block resolves
-// its tiles MCHUNK at a time, one thread per tile, into a shared table that
-// every thread then walks in the same order.  Waits are bounded
-// (TREES_ERR_TIMEOUT).
+// k*gridDim.x), pipelined MERGE_NST deep: while the block merges one tile
+// from shared memory, the next MERGE_NST - 1 tiles stream in by TMA.  The
+// block resolves its tiles MCHUNK at a time, one thread per tile, into a
+// shared table that every thread then walks in the same order.  Waits are
+// bounded (TREES_ERR_TIMEOUT); on a timeout the block lets its copies in
+// flight land before it leaves.
 template <int BS>
-__device__ void merge_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t nt1, const RunParams *jp, uint32_t js) {
-    if (threadIdx.x == 0) {
-        mbar_init(&sm.mbar[0], 1u);
-        mbar_init(&sm.mbar[1], 1u);
-    }
-    uint32_t par0 = 0u, par1 = 0u, b = 0u;
+__device__ void merge_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t nt1, uint32_t nd1, const RunParams *jp,
+                            uint32_t js) {
+    static_assert(MCHUNK <= 64 && MCHUNK <= BS, "one resolver thread per table entry, one mask bit each");
+    if (threadIdx.x == 0)
+        for (int q = 0; q < MERGE_NST; ++q) mbar_init(&sm.mbar[q], 1u);
+    uint32_t phase = 0u;  // bit q: parity of buffer q's next completion
+    uint32_t gs = 0u;     // tiles staged so far; tile number g uses buffer g % MERGE_NST
     const uint32_t stride = gridDim.x * (uint32_t)MCHUNK;
     for (uint32_t c0 = blockIdx.x; c0 < nt1; c0 += stride) {
         __syncthreads();  // the previous chunk's table is no longer read
-        if (threadIdx.x < (uint32_t)MCHUNK) {
+        if (threadIdx.x < 64u) {
             const uint32_t t = c0 + threadIdx.x * gridDim.x;
             MergeTile x;
-            const bool ok = t < nt1 && resolve_merge_tile(c, t, jp, js, x);
-            put_merge_tile(sm.mtab[threadIdx.x], ok, x);
+            const bool ok = threadIdx.x < (uint32_t)MCHUNK && t < nt1 && resolve_merge_tile(c, t, nd1, nt1, jp, js, x);
+            if (ok) put_merge_tile(sm.mtab[threadIdx.x], x);
+            const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+            if ((threadIdx.x & 31u) == 0u) reinterpret_cast<uint32_t *>(&sm.mvalid)[threadIdx.x >> 5] = bal;
         }
         __syncthreads();
-        int k = 0;
-        while (k < MCHUNK && !sm.mtab[k][0]) ++k;
-        MergeTile cur, nxt;
-        if (k < MCHUNK) {
-            get_merge_tile(sm.mtab[k], cur);
-            merge_stage<BS>(cur, sm.u.mg[b], &sm.mbar[b]);
+        unsigned long long to_stage = sm.mvalid, to_merge = to_stage;
+        uint32_t gc = gs;  // the next tile to merge
+        for (int q = 0; q < MERGE_NST - 1 && to_stage; ++q, ++gs) {
+            const int k = __ffsll((long long)to_stage) - 1;
+            to_stage &= to_stage - 1ull;
+            MergeTile x;
+            get_merge_tile(sm.mtab[k], x);
+            merge_stage<BS>(x, sm.u.mg[gs % MERGE_NST], &sm.mbar[gs % MERGE_NST]);
         }
         __syncthreads();
-        while (k < MCHUNK) {
-            int kn = k + 1;
-            while (kn < MCHUNK && !sm.mtab[kn][0]) ++kn;
-            if (kn < MCHUNK) {
-                get_merge_tile(sm.mtab[kn], nxt);
-                merge_stage<BS>(nxt, sm.u.mg[b ^ 1u], &sm.mbar[b ^ 1u]);
+        while (to_merge) {
+            if (to_stage) {  // buffer gs % MERGE_NST was freed by the barrier that ended the last merge
+                const int k = __ffsll((long long)to_stage) - 1;
+                to_stage &= to_stage - 1ull;
+                MergeTile x;
+                get_merge_tile(sm.mtab[k], x);
+                merge_stage<BS>(x, sm.u.mg[gs % MERGE_NST], &sm.mbar[gs % MERGE_NST]);
+                ++gs;
             }
-            const bool landed = mbar_wait(&sm.mbar[b], b ? par1 : par0, c.timeout_ns);
-            if (b) par1 ^= 1u;
-            else par0 ^= 1u;
+            const uint32_t b = gc % MERGE_NST;
+            const bool landed = mbar_wait(&sm.mbar[b], (phase >> b) & 1u, c.timeout_ns);
+            phase ^= 1u << b;
+            const int k = __ffsll((long long)to_merge) - 1;
+            to_merge &= to_merge - 1ull;
+            MergeTile cur;
+            get_merge_tile(sm.mtab[k], cur);
             merge_compute<BS>(cur, sm.u.mg[b]);
-            // buffer b is free again and the tails staged for b^1 are visible; a wait that ran
-            // out anywhere in the block is seen by every thread here, so all leave together
+            ++gc;
+            // buffer b is free again and the tails staged for later tiles are visible; a wait that
+            // ran out anywhere in the block is seen by every thread here, so all leave together
             if (__syncthreads_or(!landed)) {
                 if (threadIdx.x == 0) set_err(ctl, TREES_ERR_TIMEOUT, 0x80000000u | (c0 + (uint32_t)k * gridDim.x));
-                if (kn < MCHUNK) mbar_wait(&sm.mbar[b ^ 1u], b ? par0 : par1, c.timeout_ns);  // let the copy land
+                phase ^= 1u << b;  // wait again for the tile that ran out, then for every later one
+                for (--gc; gc < gs; ++gc) {  // let the copies in flight land
+                    const uint32_t q = gc % MERGE_NST;
+                    mbar_wait(&sm.mbar[q], (phase >> q) & 1u, c.timeout_ns);
+                    phase ^= 1u << q;
+                }
                 __syncthreads();
                 return;
             }
-            cur = nxt;
-            k = kn;
-            b ^= 1u;
         }
     }
 }
@@ -853,7 +971,7 @@ template <int BS, uint32_t PM>
 __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, uint32_t e, uint32_t cen, uint32_t base,
                           unsigned long long mt, unsigned long long me, const RunParams *job_params = nullptr,
                           uint32_t job_stride = 0) {
-    const uint32_t nt1 = (uint32_t)(mt & CTR_LOW_MASK);
+    const uint32_t nt1 = (uint32_t)(mt & CTR_LOW_MASK), nd1 = (uint32_t)(mt >> 40);
     const uint32_t nd2 = (uint32_t)(me >> 40), ne2 = (uint32_t)(me & CTR_LOW_MASK);
     const uint32_t nt2 = (ne2 + EXPAND_TILE - 1u) / EXPAND_TILE;
     uint32_t *keys, *scratch;
@@ -862,14 +980,14 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
         // leaves: one warp each
         const uint32_t gw = (blockIdx.x * BS + threadIdx.x) >> 5, nw = gridDim.x * (BS / 32);
         for (uint32_t t = gw; t < nt1; t += nw) {
-            const uint32_t di = c.mt_tiledesc[t];
+            const uint32_t di = tile_owner(c, t, nd1, nt1);
             if (c.mt_kind[di] != MAP_LEAF_SORT) continue;
             job_buffers(c, job_params, job_stride, c.mt_job[di], &keys, &scratch);
             const uint32_t cc = c.mt_c[di];
             warp_leaf_sort(keys, (cc & 1u) ? scratch : keys, c.mt_a[di], c.mt_b[di]);
         }
         // merge tiles: one block each, pipelined
-        merge_phase<BS>(c, ctl, sm, nt1, job_params, job_stride);
+        merge_phase<BS>(c, ctl, sm, nt1, nd1, job_params, job_stride);
       }
     }
     if constexpr ((PM & PM_BFS) != 0u) {

@@ -139,6 +139,33 @@ def test_mergesort_block_sizes(sched, bs, n):
         assert np.array_equal(host_u32(d), np.sort(keys))
 
 
+@pytest.mark.parametrize("sched", [T.TREES_SCHED_PERSISTENT, T.TREES_SCHED_GRAPH])
+@pytest.mark.parametrize("layout", ["keys_offset", "both_offset", "sorted", "reversed", "two_values"])
+@pytest.mark.parametrize("n", [300001, (1 << 19) + 2])
+def test_mergesort_alignment_and_order(sched, layout, n):
+    """Arrays that are only 4-byte aligned (the merge stages fall back to plain
+    loads for one or both buffers) and inputs whose merge tiles read all keys
+    from one run (sorted, reversed) or from long runs of equal keys."""
+    keys = gen.keys_u32(31 + n, n)
+    if layout == "sorted":
+        keys = np.sort(keys)
+    elif layout == "reversed":
+        keys = np.sort(keys)[::-1].copy()
+    elif layout == "two_values":
+        keys = (keys & 1) * np.uint32(0xFFFFFFFF)
+    keys = keys.astype(np.uint32)
+    kb = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    sb = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    d = kb[1:] if layout in ("keys_offset", "both_offset") else kb[:n]
+    sc = sb[1:] if layout == "both_offset" else sb[:n]
+    d.copy_(torch.from_numpy(keys.view(np.int32)))
+    with Ctx(1 << 16, scheduler=sched, timeout_ns=500_000_000) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_MERGESORT, n=n, keys=d, scratch=sc)) == T.TREES_OK
+        assert np.array_equal(host_u32(d), np.sort(keys))
+        if layout in ("keys_offset", "both_offset"):
+            assert int(kb[0].item()) == 0  # nothing written in front of the array
+
+
 @pytest.mark.parametrize("leaf", [1, 3, 64, 1000])
 def test_mergesort_leaf_sizes_and_duplicates(leaf):
     rng = np.random.default_rng(leaf)
