@@ -753,15 +753,6 @@ __device__ __forceinline__ void merge_compute(const MergeTile &m, const uint32_t
     const uint32_t a = smem_merge_path(sa, na, sb, nb, dd);
     uint32_t ia = a, ib = dd - a;
     uint32_t v[MPT];
-#ifdef TREES_MERGE_2LOAD
-#pragma unroll
-    for (uint32_t k = 0; k < MPT; ++k) {
-        const bool takeA = ia < na && (ib >= nb || sa[ia] <= sb[ib]);
-        v[k] = takeA ? sa[ia] : sb[min(ib, nb)];
-        ia += takeA;
-        ib += !takeA;
-    }
-#else
     // the two run heads stay in registers: one shared-memory load per output.  Indices stop at
     // the runs' ends (ia never passes na; ib is clamped for the last thread of a short tile), and
     // a head read at an end stays inside the staged buffer and is never taken.
@@ -776,7 +767,6 @@ __device__ __forceinline__ void merge_compute(const MergeTile &m, const uint32_t
         ka = takeA ? x : ka;
         kb = takeA ? kb : x;
     }
-#endif
     uint32_t *o = m.out + m.lo + m.d0 + dd;
     const uint32_t cnt = min(MPT, nt - dd);
     if constexpr (MPT % 4u == 0u) {
