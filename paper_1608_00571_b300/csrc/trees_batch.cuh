@@ -241,7 +241,7 @@ __device__ void batch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, Job *jobs, con
             acc.valid++;
             const uint32_t a0 = needs_a0(t) ? c.a0[s] : 0u, a1 = needs_a1(t) ? c.a1[s] : 0u;
             const uint32_t lk = needs_link(t) ? c.link[s] : 0u;
-            plan_task<PM_BATCH>(c, J->rp, p[0], cen, J->epochs, a0, a1, lk);
+            plan_task<PM_BATCH, merge_tile(BS)>(c, J->rp, p[0], cen, J->epochs, a0, a1, lk);
         }
     }
     const uint32_t nfork = forks_of(p[0]);

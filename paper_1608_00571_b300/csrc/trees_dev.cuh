@@ -20,9 +20,21 @@ namespace trees {
 constexpr uint32_t NTT = TREES_NUM_TASK_TYPES;  // NumTaskTypes of footnote 2, Sec. 5.1.2
 constexpr int STK_CAP = 512;                    // epoch-range stack entries per job
 constexpr int LEAF_MAX = 1024;                  // largest leaf a block sorts in shared memory
-constexpr uint32_t MERGE_TILE = 2048;           // outputs of one merge-path tile
-constexpr uint32_t MERGE_STAGE = MERGE_TILE + 16; // words of one staged tile: A's and B's 16-byte chunks, packed
-constexpr int MERGE_NST = 4;                    // merge tiles staged per block (ring of TMA buffers)
+// Outputs per thread of a merge tile (Sec. 5.2.4's map operations, tiled by
+// merge path) for a block of bs threads: odd counts keep the threads' probes
+// and run heads on distinct shared-memory banks.  A full tile is bs *
+// merge_mpt(bs) outputs, as many as two staged tiles fit in the 48 KB of
+// static shared memory a block may hold; a tile of at most bs *
+// merge_mpt_small(bs) outputs (the whole merge of two short runs) is merged
+// with the smaller count so that fewer threads idle.
+__host__ __device__ constexpr uint32_t merge_mpt(int bs) { return bs <= 256 ? 17u : bs <= 512 ? 7u : 3u; }
+__host__ __device__ constexpr uint32_t merge_mpt_small(int bs) { return bs <= 256 ? 9u : bs <= 512 ? 5u : 3u; }
+__host__ __device__ constexpr uint32_t merge_tile(int bs) { return (uint32_t)bs * merge_mpt(bs); }
+// Words of one staged tile: A's and B's 16-byte chunks, packed.
+__host__ __device__ constexpr uint32_t merge_stage(int bs) { return merge_tile(bs) + 16u; }
+// Merge tiles staged per block (a ring of TMA buffers): one merging while the
+// next streams in.
+__host__ __device__ constexpr int merge_nst(int) { return 2; }
 constexpr uint32_t EXPAND_TILE = 2048;          // adjacency entries of one BFS expansion tile
 constexpr int MCHUNK = 64;                      // merge tiles a block resolves at once
 constexpr unsigned long long CTR_LOW_MASK = (1ull << 40) - 1;  // map counters: (descs << 40) | units
@@ -148,7 +160,7 @@ struct Smem {
     unsigned int bc32[4];
     unsigned long long bc64[4];
     int bar_ok;
-    unsigned long long mbar[MERGE_NST];   // mbarriers of the merge stage buffers
+    unsigned long long mbar[merge_nst(BS)];  // mbarriers of the merge stage buffers
     unsigned long long mvalid;            // which entries of mtab are merge tiles
     uint32_t mtab[MCHUNK][12];            // the block's next merge tiles, resolved in parallel
     unsigned int ep_cnt, ep_join;         // the epoch's counters, read right after its barrier
@@ -159,13 +171,16 @@ struct Smem {
     uint32_t next, cen, lo, hi, base, rjoin;
     int stop;
     union alignas(16) {
-        uint32_t mg[MERGE_NST][MERGE_STAGE];  // staged merge tile inputs (TMA destinations)
+        uint32_t mg[merge_nst(BS)][merge_stage(BS)];  // staged merge tile inputs (TMA destinations)
         struct {
             uint32_t base[EXPAND_TILE + 2];
             uint32_t v[EXPAND_TILE + 2];
         } ex;
     } u;
 };
+
+static_assert(sizeof(Smem<256>) <= 48 * 1024 && sizeof(Smem<512>) <= 48 * 1024 && sizeof(Smem<1024>) <= 48 * 1024,
+              "a block's static shared memory is limited to 48 KB");
 
 // ------------------------------------------------------------------ scans
 
@@ -368,6 +383,25 @@ __device__ __forceinline__ void tma_load_1d(void *dst_smem, const void *src, uin
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One-dimensional bulk copy shared -> global (both 16-byte aligned, a
+// multiple of 16 bytes), tracked by this thread's bulk async-groups.
+__device__ __forceinline__ void tma_store_1d(void *dst, const void *src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src_smem)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// This thread's bulk stores have finished reading their shared-memory sources.
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// This thread's bulk stores are complete, their global writes ordered before
+// its later generic memory operations.
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 // grid_sync, then (thread 0, same round trip) the counters of epoch slot ep

@@ -78,7 +78,7 @@ __device__ __forceinline__ bool needs_link(uint32_t t) { return t == TREES_TASK_
 // Step 1 of a task: given its arguments, emit if it is a leaf (own-slot
 // writes, Sec. 4.3.2), count its forks, or request a map.  Only the task
 // types of the programs in PM are compiled in.
-template <uint32_t PM>
+template <uint32_t PM, uint32_t MT>
 __device__ __forceinline__ void plan_task(const Conf &c, const RunParams &rp, Plan &p, uint32_t cen, uint32_t e,
                                           uint32_t a0, uint32_t a1, uint32_t lk) {
     const uint32_t s = p.s;
@@ -115,7 +115,7 @@ __device__ __forceinline__ void plan_task(const Conf &c, const RunParams &rp, Pl
         }
         if (p.t == TREES_TASK_MS_MERGE) {
             p.m = MAP_MERGE;
-            p.n = (a1 - a0 + MERGE_TILE - 1u) / MERGE_TILE;
+            p.n = (a1 - a0 + MT - 1u) / MT;  // merge tiles of MT outputs
             c.code[s] = 0u;
             return;
         }
@@ -393,7 +393,7 @@ __device__ __forceinline__ void epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm
     for (int k = 0; k < TPT; ++k) {
         if (p[k].t) {
             acc.valid++;
-            plan_task<PM>(c, c.rp, p[k], cen, e, a0v[k], a1v[k], lkv[k]);
+            plan_task<PM, merge_tile(BS)>(c, c.rp, p[k], cen, e, a0v[k], a1v[k], lkv[k]);
         }
         nf[k] = forks_of(p[k]);
         hasmap |= p[k].m != 0u;
@@ -602,7 +602,7 @@ __device__ void partition_phase(const Conf &c, unsigned long long mt, const RunP
             uint32_t *keys, *scratch;
             job_buffers(c, job_params, job_stride, c.mt_job[di], &keys, &scratch);
             const uint32_t *in = (cc & 1u) ? keys : scratch;
-            const uint32_t la = mid - a, lb = b - mid, d = tin * MERGE_TILE;
+            const uint32_t la = mid - a, lb = b - mid, d = tin * merge_tile(BS);
             A[q] = in + a;
             B[q] = in + mid;
             diag[q] = d;
@@ -656,6 +656,7 @@ struct MergeTile {
 };
 
 // Resolves merge tile t of the tiled map list (false when it is not a merge).
+template <int BS>
 __device__ __forceinline__ bool resolve_merge_tile(const Conf &c, uint32_t t, uint32_t nd1, uint32_t nt1,
                                                    const RunParams *jp, uint32_t js, MergeTile &m) {
     const uint32_t di = tile_owner(c, t, nd1, nt1);
@@ -664,17 +665,22 @@ __device__ __forceinline__ bool resolve_merge_tile(const Conf &c, uint32_t t, ui
     job_buffers(c, jp, js, c.mt_job[di], &keys, &scratch);
     const uint32_t lo = c.mt_a[di], hi = c.mt_b[di], cc = c.mt_c[di];
     const uint32_t tin = t - c.mt_tilebase[di];
-    const uint32_t la = (hi - lo) / 2u, L = hi - lo, ntiles = (L + MERGE_TILE - 1u) / MERGE_TILE;
+    constexpr uint32_t T = merge_tile(BS);
+    const uint32_t la = (hi - lo) / 2u, L = hi - lo, ntiles = (L + T - 1u) / T;
     m.in = (cc & 1u) ? keys : scratch;   // the children's runs (depth d+1)
     m.out = (cc & 1u) ? scratch : keys;  // this node's run (depth d)
     m.lo = lo;
     m.mid = lo + la;
     m.hi = hi;
-    m.d0 = tin * MERGE_TILE;
-    m.i0 = tin ? c.mt_split[t] : 0u;
-    m.i1 = tin + 1u < ntiles ? c.mt_split[t + 1u] : la;
+    m.d0 = tin * T;
+    const uint32_t lb = L - la, dend = min(m.d0 + T, L);
+    const uint32_t s0 = tin ? c.mt_split[t] : 0u, s1 = tin + 1u < ntiles ? c.mt_split[t + 1u] : la;
+    // merge-path splits of sorted runs already satisfy these bounds; the clamps keep every copy
+    // and index of the tile inside its runs, its output and its stage buffer whatever the splits
+    m.i0 = min(max(s0, m.d0 > lb ? m.d0 - lb : 0u), min(m.d0, la));
+    m.i1 = min(max(s1, max(m.i0, dend > lb ? dend - lb : 0u)), min(la, m.i0 + (dend - m.d0)));
     m.j0 = m.d0 - m.i0;
-    m.j1 = min(m.d0 + MERGE_TILE, L) - m.i1;
+    m.j1 = dend - m.i1;
     return true;
 }
 
@@ -705,7 +711,9 @@ __device__ __forceinline__ StageLayout stage_layout(const MergeTile &m) {
 // reach past the run but never past the merge's end hi, which is inside the
 // array; a last partial chunk beyond hi (hi not a multiple of 4) is loaded
 // with plain loads, and so is everything when the array is not 16-byte
-// aligned.
+// aligned.  buf may still be the source of an earlier tile's bulk store:
+// thread 0 waits for those reads before its copies, and the block waits with
+// it before plain loads write buf.
 template <int BS>
 __device__ __forceinline__ void merge_stage(const MergeTile &m, uint32_t *buf, unsigned long long *bar) {
     const StageLayout L = stage_layout(m);
@@ -715,12 +723,15 @@ __device__ __forceinline__ void merge_stage(const MergeTile &m, uint32_t *buf, u
     const uint32_t bc = L.be4u <= m.hi ? L.be4u : (L.be & ~3u);
     const uint32_t abytes = aligned && L.ae > L.as && ac > L.as4 ? (ac - L.as4) * 4u : 0u;
     const uint32_t bbytes = aligned && L.be > L.bs && bc > L.bs4 ? (bc - L.bs4) * 4u : 0u;
+    const bool plain = (abytes ? ac : L.as) < L.ae || (bbytes ? bc : L.bs) < L.be;  // the same on every thread
     if (threadIdx.x == 0) {
+        bulk_wait_read_all();      // earlier bulk stores no longer read buf
         fence_proxy_async_smem();  // earlier generic reads of buf come before the async writes
         mbar_arrive_expect(bar, abytes + bbytes);
         if (abytes) tma_load_1d(buf, m.in + L.as4, abytes, bar);
         if (bbytes) tma_load_1d(sb, m.in + L.bs4, bbytes, bar);
     }
+    if (plain) __syncthreads();
     for (uint32_t x = (abytes ? ac : L.as) + threadIdx.x; x < L.ae; x += BS) buf[x - L.as4] = m.in[x];
     for (uint32_t x = (bbytes ? bc : L.bs) + threadIdx.x; x < L.be; x += BS) sb[x - L.bs4] = m.in[x];
 }
@@ -739,20 +750,19 @@ __device__ __forceinline__ uint32_t smem_merge_path(const uint32_t *sa, uint32_t
     return a;
 }
 
-// Merges a staged tile: each thread finds its first output's merge-path split
-// in shared memory, merges MPT outputs in registers and stores them with one
-// vector store when aligned.
-template <int BS>
-__device__ __forceinline__ void merge_compute(const MergeTile &m, const uint32_t *buf) {
-    constexpr uint32_t MPT = MERGE_TILE / BS;
+// Merges a staged tile into registers: each thread finds the merge-path split
+// of its first output dd in shared memory and merges the next MPT outputs
+// (an odd count, see merge_mpt) into v.
+template <int BS, uint32_t MPT>
+__device__ __forceinline__ void merge_compute(const MergeTile &m, const uint32_t *buf, uint32_t (&v)[MPT],
+                                              uint32_t &dd) {
     const StageLayout L = stage_layout(m);
     const uint32_t na = m.i1 - m.i0, nb = m.j1 - m.j0, nt = na + nb;
     const uint32_t *sa = buf + (L.as - L.as4);
     const uint32_t *sb = buf + L.sbo + (L.bs - L.bs4);
-    const uint32_t dd = min((uint32_t)threadIdx.x * MPT, nt);
+    dd = min((uint32_t)threadIdx.x * MPT, nt);
     const uint32_t a = smem_merge_path(sa, na, sb, nb, dd);
     uint32_t ia = a, ib = dd - a;
-    uint32_t v[MPT];
     // the two run heads stay in registers: one shared-memory load per output.  Indices stop at
     // the runs' ends (ia never passes na; ib is clamped for the last thread of a short tile), and
     // a head read at an end stays inside the staged buffer and is never taken.
@@ -767,19 +777,42 @@ __device__ __forceinline__ void merge_compute(const MergeTile &m, const uint32_t
         ka = takeA ? x : ka;
         kb = takeA ? kb : x;
     }
-    uint32_t *o = m.out + m.lo + m.d0 + dd;
-    const uint32_t cnt = min(MPT, nt - dd);
-    if constexpr (MPT % 4u == 0u) {
-        if (cnt == MPT && ((reinterpret_cast<uintptr_t>(o) & 15u) == 0u)) {
-#pragma unroll
-            for (uint32_t q = 0; q < MPT / 4u; ++q)
-                reinterpret_cast<uint4 *>(o)[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-            return;
-        }
-    }
+}
+
+// Writes a merged tile: after the block has finished reading buf, each thread
+// puts its outputs back into buf (consecutive threads MPT words apart, an odd
+// stride: no bank conflicts), and thread 0 stores the tile's contiguous
+// output with one bulk copy; without 16-byte alignment the block copies it
+// out with coalesced stores instead.
+template <int BS, uint32_t MPT>
+__device__ __forceinline__ void merge_write(const MergeTile &m, uint32_t *buf, const uint32_t (&v)[MPT], uint32_t dd) {
+    const uint32_t nt = (m.i1 - m.i0) + (m.j1 - m.j0);
 #pragma unroll
     for (uint32_t k = 0; k < MPT; ++k)
-        if (k < cnt) o[k] = v[k];
+        if (dd + k < nt) buf[dd + k] = v[k];
+    uint32_t *o = m.out + m.lo + m.d0;
+    const bool bulk = ((reinterpret_cast<uintptr_t>(o) & 15u) == 0u) && (nt & 3u) == 0u;
+    if (bulk) fence_proxy_async_smem();  // these generic writes come before the bulk copy's reads
+    __syncthreads();
+    if (bulk) {
+        if (threadIdx.x == 0 && nt) tma_store_1d(o, buf, nt * 4u);
+    } else {
+        for (uint32_t i = threadIdx.x; i < nt; i += BS) o[i] = buf[i];
+        __syncthreads();  // buf is read before the next tile is staged into it
+    }
+}
+
+// One staged tile, start to end, with MPT outputs per thread; false (and
+// nothing written) when the tile's copy did not land on some thread.
+template <int BS, uint32_t MPT>
+__device__ __forceinline__ bool merge_run(const MergeTile &m, uint32_t *buf, bool landed) {
+    uint32_t v[MPT], dd;
+    merge_compute<BS, MPT>(m, buf, v, dd);
+    // every thread has read buf and the tails staged for later tiles are visible; a wait that ran
+    // out anywhere in the block is seen by every thread here, so all leave together
+    if (__syncthreads_or(!landed)) return false;
+    merge_write<BS, MPT>(m, buf, v, dd);
+    return true;
 }
 
 __device__ __forceinline__ void put_merge_tile(uint32_t *w, const MergeTile &x) {
@@ -810,8 +843,8 @@ __device__ __forceinline__ void get_merge_tile(const uint32_t *w, MergeTile &m) 
 }
 
 // All merge tiles of the epoch handled by this block (tiles blockIdx.x +
-// k*gridDim.x), pipelined MERGE_NST deep: while the block merges one tile
-// from shared memory, the next MERGE_NST - 1 tiles stream in by TMA.  The
+// k*gridDim.x), pipelined merge_nst(BS) deep: while the block merges one
+// tile from shared memory, the next ones stream in by TMA.  The
 // block resolves its tiles MCHUNK at a time, one thread per tile, into a
 // shared table that every thread then walks in the same order.  Waits are
 // bounded (TREES_ERR_TIMEOUT); on a timeout the block lets its copies in
@@ -820,17 +853,18 @@ template <int BS>
 __device__ void merge_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t nt1, uint32_t nd1, const RunParams *jp,
                             uint32_t js) {
     static_assert(MCHUNK <= 64 && MCHUNK <= BS, "one resolver thread per table entry, one mask bit each");
+    constexpr int NST = merge_nst(BS);
     if (threadIdx.x == 0)
-        for (int q = 0; q < MERGE_NST; ++q) mbar_init(&sm.mbar[q], 1u);
+        for (int q = 0; q < NST; ++q) mbar_init(&sm.mbar[q], 1u);
     uint32_t phase = 0u;  // bit q: parity of buffer q's next completion
-    uint32_t gs = 0u;     // tiles staged so far; tile number g uses buffer g % MERGE_NST
+    uint32_t gs = 0u;     // tiles staged so far; tile number g uses buffer g % NST
     const uint32_t stride = gridDim.x * (uint32_t)MCHUNK;
     for (uint32_t c0 = blockIdx.x; c0 < nt1; c0 += stride) {
         __syncthreads();  // the previous chunk's table is no longer read
         if (threadIdx.x < 64u) {
             const uint32_t t = c0 + threadIdx.x * gridDim.x;
             MergeTile x;
-            const bool ok = threadIdx.x < (uint32_t)MCHUNK && t < nt1 && resolve_merge_tile(c, t, nd1, nt1, jp, js, x);
+            const bool ok = threadIdx.x < (uint32_t)MCHUNK && t < nt1 && resolve_merge_tile<BS>(c, t, nd1, nt1, jp, js, x);
             if (ok) put_merge_tile(sm.mtab[threadIdx.x], x);
             const uint32_t bal = __ballot_sync(0xffffffffu, ok);
             if ((threadIdx.x & 31u) == 0u) reinterpret_cast<uint32_t *>(&sm.mvalid)[threadIdx.x >> 5] = bal;
@@ -838,47 +872,50 @@ __device__ void merge_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t nt1,
         __syncthreads();
         unsigned long long to_stage = sm.mvalid, to_merge = to_stage;
         uint32_t gc = gs;  // the next tile to merge
-        for (int q = 0; q < MERGE_NST - 1 && to_stage; ++q, ++gs) {
+        for (int q = 0; q < NST - 1 && to_stage; ++q, ++gs) {
             const int k = __ffsll((long long)to_stage) - 1;
             to_stage &= to_stage - 1ull;
             MergeTile x;
             get_merge_tile(sm.mtab[k], x);
-            merge_stage<BS>(x, sm.u.mg[gs % MERGE_NST], &sm.mbar[gs % MERGE_NST]);
+            merge_stage<BS>(x, sm.u.mg[gs % NST], &sm.mbar[gs % NST]);
         }
         __syncthreads();
         while (to_merge) {
-            if (to_stage) {  // buffer gs % MERGE_NST was freed by the barrier that ended the last merge
+            if (to_stage) {  // buffer gs % NST was freed by the barrier that ended the last merge
                 const int k = __ffsll((long long)to_stage) - 1;
                 to_stage &= to_stage - 1ull;
                 MergeTile x;
                 get_merge_tile(sm.mtab[k], x);
-                merge_stage<BS>(x, sm.u.mg[gs % MERGE_NST], &sm.mbar[gs % MERGE_NST]);
+                merge_stage<BS>(x, sm.u.mg[gs % NST], &sm.mbar[gs % NST]);
                 ++gs;
             }
-            const uint32_t b = gc % MERGE_NST;
+            const uint32_t b = gc % NST;
             const bool landed = mbar_wait(&sm.mbar[b], (phase >> b) & 1u, c.timeout_ns);
             phase ^= 1u << b;
             const int k = __ffsll((long long)to_merge) - 1;
             to_merge &= to_merge - 1ull;
             MergeTile cur;
             get_merge_tile(sm.mtab[k], cur);
-            merge_compute<BS>(cur, sm.u.mg[b]);
+            const uint32_t nt = (cur.i1 - cur.i0) + (cur.j1 - cur.j0);
+            const bool ok = nt <= (uint32_t)BS * merge_mpt_small(BS)
+                                ? merge_run<BS, merge_mpt_small(BS)>(cur, sm.u.mg[b], landed)
+                                : merge_run<BS, merge_mpt(BS)>(cur, sm.u.mg[b], landed);
             ++gc;
-            // buffer b is free again and the tails staged for later tiles are visible; a wait that
-            // ran out anywhere in the block is seen by every thread here, so all leave together
-            if (__syncthreads_or(!landed)) {
+            if (!ok) {
                 if (threadIdx.x == 0) set_err(ctl, TREES_ERR_TIMEOUT, 0x80000000u | (c0 + (uint32_t)k * gridDim.x));
                 phase ^= 1u << b;  // wait again for the tile that ran out, then for every later one
                 for (--gc; gc < gs; ++gc) {  // let the copies in flight land
-                    const uint32_t q = gc % MERGE_NST;
+                    const uint32_t q = gc % NST;
                     mbar_wait(&sm.mbar[q], (phase >> q) & 1u, c.timeout_ns);
                     phase ^= 1u << q;
                 }
+                if (threadIdx.x == 0) bulk_wait_all();
                 __syncthreads();
                 return;
             }
         }
     }
+    if (threadIdx.x == 0) bulk_wait_all();  // the outputs are in memory before the block's next barrier
 }
 
 // One BFS expansion tile: EXPAND_TILE consecutive adjacency entries of the
