@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(BS) k_epoch(Ctl *ctl, Conf c, unsigned long lo
         TileLoad<TPT> L;
         tile_load<BS, TPT, PM_ALL>(c, t0, hi, LOAD_ON_DEMAND, L);
         epoch_tile<BS, TPT, PM_ALL>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, LOAD_ON_DEMAND, L,
-                                    hi - lo <= (uint32_t)(BS * TPT));
+                                    hi - lo <= (uint32_t)(BS * TPT), 0u);
         par ^= 1;
     }
     trace_valid_add<BS>(c, e, acc.valid, sm);

@@ -47,6 +47,7 @@ struct Range {
     uint32_t cen, lo, hi;  // epoch number and NDRange [lo, hi) (Sec. 5.1.2)
     uint32_t join;         // 1: a join range revisited (continuations), 0: freshly forked tasks
 };
+static_assert(sizeof(Range) == 16, "ranges move as 16-byte vectors");
 
 // The job a single-job run executes (copied into the control block per run).
 struct RunParams {
@@ -100,6 +101,7 @@ struct Ctl {
     unsigned int epochs, peak, final_next, pad1;
     // scheduler state for the graph and host-loop schedulers
     unsigned int g_cen, g_lo, g_hi, g_base, g_e, g_next, g_sp, g_stop;
+    unsigned int g_rjoin, pad2;      // the persistent scheduler's solo runs publish the same state
 };
 
 struct Dev {
@@ -170,6 +172,7 @@ struct Smem {
     int sp;
     uint32_t next, cen, lo, hi, base, rjoin;
     int stop;
+    unsigned int solo_late;  // a solo run has used its share of the barrier timeout
     union alignas(16) {
         uint32_t mg[merge_nst(BS)][merge_stage(BS)];  // staged merge tile inputs (TMA destinations)
         struct {

@@ -50,50 +50,217 @@ __host__ __device__ constexpr int persistent_min_blocks(int bs, uint32_t pm) {
     return (pm == PM_MS || pm == PM_FIB) ? (1024 / bs > 0 ? 1024 / bs : 1) : 1;
 }
 
+// Scheduler state a persistent block carries between epochs (thread 0's).
+struct SchedState {
+    unsigned long long forks_total;
+    uint32_t peak;
+    // trace timestamps (block 0): previous epoch's end, end of Phase 2, of partition, of maps
+    unsigned long long t_prev, t_p2, t_pt, t_mp;
+};
+
+// Phase 1 (thread 0): pop (CEN, NDRange) for epoch e and set
+// oldNextFreeCore = nextFreeCore, or stop; block 0 clears the counters epoch
+// e+1 will use.
+template <int BS>
+__device__ __forceinline__ void phase1(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t e) {
+    int stop = 0;
+    if (sm.sp == 0) {
+        stop = 1;
+    } else if (e >= c.max_epochs) {
+        stop = 2;
+        set_err(ctl, TREES_ERR_EPOCH_LIMIT, e);
+    } else {
+        const Range r = sm.stk[--sm.sp];
+        sm.cen = r.cen;
+        sm.lo = r.lo;
+        sm.hi = r.hi;
+        sm.rjoin = r.join;
+        sm.base = sm.next;
+    }
+    sm.stop = stop;
+    if (!stop && blockIdx.x == 0) {
+        const uint32_t q = (e + 1u) % 3u;
+        ctl->cnt[q] = 0u;
+        ctl->join[q] = 0u;
+        ctl->mt_ctr[q] = 0ull;
+        ctl->me_ctr[q] = 0ull;
+    }
+}
+
+// Phase 3 (thread 0): push the join range, then the fork range; or give the
+// range back.  Block 0 also keeps the run's statistics and writes the trace.
+template <int BS>
+__device__ __forceinline__ void phase3(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t e, uint32_t f, uint32_t jf,
+                                       unsigned long long mt, unsigned long long me, SchedState &st) {
+    const uint32_t cen = sm.cen, lo = sm.lo, hi = sm.hi, base = sm.base;
+    int ok = 1;
+    if (jf) {
+        if (sm.sp < STK_CAP) sm.stk[sm.sp++] = Range{cen, lo, hi, 1u};
+        else ok = 0;
+    }
+    if (f) {
+        if (sm.sp < STK_CAP) sm.stk[sm.sp++] = Range{cen + 1u, base, base + f, 0u};
+        else ok = 0;
+        sm.next = base + f;
+    } else if (!jf) {
+        sm.next = lo;  // neither forks nor joins: nextFreeCore decreases (Sec. 5.3)
+    }
+    if (!ok) {
+        if (blockIdx.x == 0) set_err(ctl, TREES_ERR_STACK, e);
+        sm.sp = 0;
+    }
+    if (blockIdx.x == 0) {
+        st.forks_total += f;
+        st.peak = max(st.peak, base + f);
+        if (c.trace_on && e < c.trace_cap) {
+            trees_epoch_t r;
+            r.cen = cen;
+            r.lo = lo;
+            r.hi = hi;
+            r.valid = 0u;
+            r.forks = f;
+            r.joined = jf;
+            r.maps = (uint32_t)(mt >> 40) + (uint32_t)(me >> 40);
+            r.t_ns = globaltimer();
+            r.ns_phase2 = (uint32_t)(st.t_p2 - st.t_prev);
+            r.ns_partition = (uint32_t)(st.t_pt - st.t_p2);
+            r.ns_map = (uint32_t)(st.t_mp - st.t_pt);
+            st.t_prev = r.t_ns;
+            c.trace[e] = r;
+        }
+    }
+}
+
+// Ranges of at most SOLO_TILES tiles, for programs without map operations,
+// are worked by block 0 alone, epoch after epoch, each closed by a block
+// barrier instead of a grid barrier: the same epochs, ranges and fork counts
+// without the grid-wide round trip, which costs more than a tile or two of
+// work.
+constexpr uint32_t SOLO_TILES = 2;  // measured: 1 or 2 tiles best; 4 already slower
+template <int BS, int TPT, uint32_t PM>
+__device__ __forceinline__ bool solo_range(const Conf &c, uint32_t lo, uint32_t hi) {
+    return (PM & (PM_MS | PM_BFS)) == 0u && c.stall_epoch < 0 && hi - lo <= SOLO_TILES * (uint32_t)(BS * TPT);
+}
+
+// Block 0's run of solo epochs, starting at epoch e with its range popped.
+// Returns the epoch whose range is popped when the run ends (a range too
+// large for one tile, the end of the job, an error, or a quarter of the
+// barrier timeout spent, so the waiting blocks never time out); block 0's
+// state (stack, nextFreeCore, popped range, stop) is then published for the
+// other blocks.
+template <int BS, int TPT, uint32_t PM>
+__device__ uint32_t solo_epochs(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t e, Acc &acc, SchedState &st) {
+    const unsigned long long t_start = threadIdx.x == 0 ? globaltimer() : 0ull;
+    for (;;) {
+        const uint32_t cen = sm.cen, lo = sm.lo, hi = sm.hi, base = sm.base, ep = e % 3u;
+        const int mode = sm.rjoin ? LOAD_JOIN : LOAD_FRESH;
+        const uint32_t v0 = acc.valid;
+        TileOut o = {0u, false, false};
+        // the range's tiles in order, each forking after the children of the ones before it
+        TileLoad<TPT> cur, nxt;
+        if (lo < hi) tile_load<BS, TPT, PM>(c, lo, hi, mode, cur);
+        int par = 0;
+        for (uint32_t t0 = lo; t0 < hi; t0 += (uint32_t)(BS * TPT)) {
+            const bool more = t0 + (uint32_t)(BS * TPT) < hi;
+            if (more) tile_load<BS, TPT, PM>(c, t0 + (uint32_t)(BS * TPT), hi, mode, nxt);
+            const TileOut t = epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode, cur,
+                                                      true, o.forks);
+            o.forks += t.forks;
+            o.joined |= t.joined;
+            o.over |= t.over;
+            if (more) cur = nxt;
+            par ^= 1;
+        }
+        trace_valid_add<BS>(c, e, acc.valid - v0, sm);
+        // the whole epoch is this block's tile: its fork total and join flag close the epoch
+        const uint32_t jf = (uint32_t)__syncthreads_or(o.joined);
+        if (threadIdx.x == 0) {
+            if (c.trace_on) st.t_p2 = st.t_pt = st.t_mp = globaltimer();
+            phase3<BS>(c, ctl, sm, e, o.forks, jf, 0ull, 0ull, st);
+            phase1<BS>(c, ctl, sm, e + 1u);
+            if (o.over) sm.stop = 3;  // the capacity error is set; the grid barrier reports it
+            sm.solo_late = globaltimer() - t_start > c.timeout_ns / 4u;
+        }
+        ++e;  // on every thread: the epoch number picks the counter slot and the trace entry
+        __syncthreads();
+        if (sm.stop || sm.solo_late || !solo_range<BS, TPT, PM>(c, sm.lo, sm.hi)) break;
+    }
+    if (threadIdx.x == 0) {
+        ctl->g_e = e;
+        ctl->g_sp = (uint32_t)sm.sp;
+        ctl->g_next = sm.next;
+        ctl->g_cen = sm.cen;
+        ctl->g_lo = sm.lo;
+        ctl->g_hi = sm.hi;
+        ctl->g_base = sm.base;
+        ctl->g_rjoin = sm.rjoin;
+        ctl->g_stop = (uint32_t)sm.stop;
+        for (int i = 0; i < sm.sp; ++i) c.gstack[i] = sm.stk[i];
+    }
+    return e;
+}
+
+// The other blocks take over block 0's published state after the grid
+// barrier that ends the solo run: thread 0 the scalars, then every thread a
+// share of the stack.  Returns the epoch whose range is popped.
+template <int BS>
+__device__ __forceinline__ uint32_t adopt_solo_state(const Conf &c, Ctl *ctl, Smem<BS> &sm) {
+    if (threadIdx.x == 0) {
+        sm.sp = (int)vload(&ctl->g_sp);
+        sm.next = vload(&ctl->g_next);
+        sm.cen = vload(&ctl->g_cen);
+        sm.lo = vload(&ctl->g_lo);
+        sm.hi = vload(&ctl->g_hi);
+        sm.base = vload(&ctl->g_base);
+        sm.rjoin = vload(&ctl->g_rjoin);
+        sm.stop = (int)vload(&ctl->g_stop);
+        sm.bc32[0] = vload(&ctl->g_e);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < sm.sp; i += BS) {
+        const uint4 r = __ldcg(reinterpret_cast<const uint4 *>(c.gstack + i));  // past any stale L1 line
+        sm.stk[i] = Range{r.x, r.y, r.z, r.w};
+    }
+    return sm.bc32[0];
+}
+
 template <int BS, int TPT, uint32_t PM>
 __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM)) k_persistent(Ctl *ctl, Conf c, unsigned long long *blk) {
     __shared__ Smem<BS> sm;
+    __shared__ uint32_t sm_e;
     uint32_t bar = 0;
     Acc acc = {0u, 0u, 0u};
+    SchedState st = {0ull, 1u, 0ull, 0ull, 0ull, 0ull};
     if (threadIdx.x == 0) {
         sm.sp = 1;
         sm.stk[0] = Range{0u, 0u, 1u, 0u};
         sm.next = 1u;
+        if (c.trace_on && blockIdx.x == 0) st.t_prev = globaltimer();
     }
-    unsigned long long forks_total = 0;
-    uint32_t peak = 1u;
-    // trace timestamps (block 0, thread 0): previous epoch's end, end of Phase 2, of partition, of maps
     const bool stamp = c.trace_on && blockIdx.x == 0 && threadIdx.x == 0;
-    unsigned long long t_prev = stamp ? globaltimer() : 0ull, t_p2 = 0ull, t_pt = 0ull, t_mp = 0ull;
+    bool popped = false;  // epoch e's range was popped by a solo run
     uint32_t e = 0;
     for (;; ++e) {
         // Phase 1: pop (CEN, NDRange); oldNextFreeCore = nextFreeCore
-        if (threadIdx.x == 0) {
-            int stop = 0;
-            if (sm.sp == 0) {
-                stop = 1;
-            } else if (e >= c.max_epochs) {
-                stop = 2;
-                set_err(ctl, TREES_ERR_EPOCH_LIMIT, e);
-            } else {
-                const Range r = sm.stk[--sm.sp];
-                sm.cen = r.cen;
-                sm.lo = r.lo;
-                sm.hi = r.hi;
-                sm.rjoin = r.join;
-                sm.base = sm.next;
-            }
-            sm.stop = stop;
-            if (!stop && blockIdx.x == 0) {  // clear the counters epoch e+1 will use
-                const uint32_t q = (e + 1u) % 3u;
-                ctl->cnt[q] = 0u;
-                ctl->join[q] = 0u;
-                ctl->mt_ctr[q] = 0ull;
-                ctl->me_ctr[q] = 0ull;
-            }
-        }
+        if (threadIdx.x == 0 && !popped) phase1<BS>(c, ctl, sm, e);
+        popped = false;
         __syncthreads();
         if (sm.stop) break;
+        if (solo_range<BS, TPT, PM>(c, sm.lo, sm.hi)) {
+            if (blockIdx.x == 0) {
+                const uint32_t ne = solo_epochs<BS, TPT, PM>(c, ctl, sm, e, acc, st);
+                if (threadIdx.x == 0) sm_e = ne;
+            }
+            if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, e % 3u)) break;
+            if (blockIdx.x != 0) {
+                const uint32_t ne = adopt_solo_state<BS>(c, ctl, sm);
+                if (threadIdx.x == 0) sm_e = ne;
+            }
+            __syncthreads();
+            e = sm_e - 1u;  // the loop's ++e lands on the popped epoch
+            popped = true;
+            continue;
+        }
         const uint32_t cen = sm.cen, lo = sm.lo, hi = sm.hi, base = sm.base, ep = e % 3u;
         const int mode = sm.rjoin ? LOAD_JOIN : LOAD_FRESH;
         // Phase 2: every entry of [lo, hi)
@@ -108,74 +275,36 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM)) k_persisten
         for (; t0 < hi; t0 += step) {
             const bool more = t0 + step < hi;
             if (more) tile_load<BS, TPT, PM>(c, t0 + step, hi, mode, nxt);
-            epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode, cur, solo);
+            epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode, cur, solo, 0u);
             if (more) cur = nxt;
             par ^= 1;
         }
         trace_valid_add<BS>(c, e, acc.valid - v0, sm);
         if ((int32_t)e == c.stall_epoch && blockIdx.x == gridDim.x - 1) return;  // test hook: never arrives
         if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, ep)) break;
-        if (stamp) t_p2 = t_pt = t_mp = globaltimer();
+        if (stamp) st.t_p2 = st.t_pt = st.t_mp = globaltimer();
         const unsigned long long mt = sm.ep_mt, me = sm.ep_me;
         if (mt | me) {  // the map operations of this epoch run before the next one (Sec. 5.2.4)
             if constexpr ((PM & PM_MS) != 0u) {
                 if (needs_partition(mt)) {
                     partition_phase<BS>(c, mt, nullptr, 0u);
                     if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, ep)) break;
-                    if (stamp) t_pt = t_mp = globaltimer();
+                    if (stamp) st.t_pt = st.t_mp = globaltimer();
                 }
             }
             map_phase<BS, PM>(c, ctl, sm, ep, e, cen, base, mt, me);
             if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, ep)) break;
-            if (stamp) t_mp = globaltimer();
+            if (stamp) st.t_mp = globaltimer();
         }
         // Phase 3: push the join range, then the fork range; or give the range back
-        if (threadIdx.x == 0) {
-            const uint32_t f = sm.ep_cnt, jf = sm.ep_join;
-            int ok = 1;
-            if (jf) {
-                if (sm.sp < STK_CAP) sm.stk[sm.sp++] = Range{cen, lo, hi, 1u};
-                else ok = 0;
-            }
-            if (f) {
-                if (sm.sp < STK_CAP) sm.stk[sm.sp++] = Range{cen + 1u, base, base + f, 0u};
-                else ok = 0;
-                sm.next = base + f;
-            } else if (!jf) {
-                sm.next = lo;  // neither forks nor joins: nextFreeCore decreases (Sec. 5.3)
-            }
-            if (!ok) {
-                if (blockIdx.x == 0) set_err(ctl, TREES_ERR_STACK, e);
-                sm.sp = 0;
-            }
-            if (blockIdx.x == 0) {
-                forks_total += f;
-                peak = max(peak, base + f);
-                if (c.trace_on && e < c.trace_cap) {
-                    trees_epoch_t r;
-                    r.cen = cen;
-                    r.lo = lo;
-                    r.hi = hi;
-                    r.valid = 0u;
-                    r.forks = f;
-                    r.joined = jf;
-                    r.maps = (uint32_t)(mt >> 40) + (uint32_t)(me >> 40);
-                    r.t_ns = globaltimer();
-                    r.ns_phase2 = (uint32_t)(t_p2 - t_prev);
-                    r.ns_partition = (uint32_t)(t_pt - t_p2);
-                    r.ns_map = (uint32_t)(t_mp - t_pt);
-                    t_prev = r.t_ns;
-                    c.trace[e] = r;
-                }
-            }
-        }
+        if (threadIdx.x == 0) phase3<BS>(c, ctl, sm, e, sm.ep_cnt, sm.ep_join, mt, me, st);
     }
     block_add_stats<BS>(blk, acc, sm);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->epochs = e;
-        ctl->peak = peak;
+        ctl->peak = st.peak;
         ctl->final_next = sm.next;
-        ctl->forks = forks_total;
+        ctl->forks = st.forks_total;
         ctl->t_end = globaltimer();
     }
 }

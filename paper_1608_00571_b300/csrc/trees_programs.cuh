@@ -363,10 +363,19 @@ __device__ __forceinline__ void tile_load(const Conf &c, unsigned long long t0, 
     }
 }
 
+// What one Phase-2 tile tells its block: the forks of the whole tile (the
+// same on every thread), whether this thread's tasks scheduled a join, and
+// whether the fork allocation ran out of slots (the same on every thread).
+struct TileOut {
+    uint32_t forks;
+    bool joined;
+    bool over;
+};
+
 template <int BS, int TPT, uint32_t PM>
-__device__ __forceinline__ void epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, unsigned long long t0, uint32_t hi,
+__device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, unsigned long long t0, uint32_t hi,
                                            uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, Acc &acc, int par,
-                                           int mode, const TileLoad<TPT> &L, bool solo) {
+                                           int mode, const TileLoad<TPT> &L, bool known, uint32_t known_off) {
     constexpr bool fresh_a1 = (PM & (PM_MS | PM_NQ)) != 0u;
     constexpr bool join_a0 = (PM & (PM_MS | PM_NQ | PM_TRAV)) != 0u;
     constexpr bool join_link = (PM & (PM_FIB | PM_NQ)) != 0u;
@@ -404,12 +413,14 @@ __device__ __forceinline__ void epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm
     uint32_t all = 0;
 #pragma unroll
     for (int k = 0; k < TPT; ++k) all += tot[k];
+    TileOut out = {all, false, false};
     if (all) {
-        // solo: this tile is the whole range, so no other block forks this epoch, its children
-        // start at offset 0 and the count is published without waiting for the atomic's answer
-        uint32_t b0 = 0u, over0 = 0u;
-        if (solo) {
-            over0 = (unsigned long long)base + all > c.cap;
+        // known: this block forks every child of the epoch (the range is its own), so the tile's
+        // children start at known_off, the forks of its earlier tiles, and the count is published
+        // without waiting for the atomic's answer
+        uint32_t b0 = known ? known_off : 0u, over0 = 0u;
+        if (known) {
+            over0 = (unsigned long long)base + known_off + all > c.cap;
             if (threadIdx.x == 0) {
                 atomicAdd(&ctl->cnt[ep], all);  // result unused: a fire-and-forget reduction
                 if (over0) set_err(ctl, TREES_ERR_CAPACITY, e);
@@ -437,10 +448,13 @@ __device__ __forceinline__ void epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm
         }
         acc.joins += joined;
         if (__any_sync(0xffffffffu, joined != 0u) && (threadIdx.x & 31) == 0) ctl->join[ep] = 1u;  // joinScheduled
+        out.joined = joined != 0u;
+        out.over = over0 != 0u;
     }
     if constexpr ((PM & (PM_MS | PM_BFS)) != 0u) {
         if (anymap) map_alloc<BS, TPT>(c, ctl, sm, p, cen, ep, e, 0u, acc);
     }
+    return out;
 }
 
 // ------------------------------------------------------------------ map operations
