@@ -43,11 +43,15 @@ __device__ __forceinline__ void trace_valid_add(const Conf &c, uint32_t e, uint3
 }
 
 // The persistent scheduler: the whole epoch loop in one cooperative launch.
-// Blocks per SM the kernel is compiled to fit: the mergesort kernel keeps
-// 1024 threads per SM resident (the warp leaf sort would otherwise take the
-// registers of a whole SM); the others take what they need.
-__host__ __device__ constexpr int persistent_min_blocks(int bs, uint32_t pm) {
-    return (pm == PM_MS || pm == PM_FIB) ? (1024 / bs > 0 ? 1024 / bs : 1) : 1;
+// Blocks per SM the kernel is compiled to fit (its register budget): the
+// mergesort kernel keeps 1024 threads per SM resident (the warp leaf sort
+// would otherwise take the registers of a whole SM); the fib kernel trades
+// threads for registers as its slots per thread grow (1024, 768, 512 threads
+// per SM for 1, 2, 4 slots: measured, each spill-free beats more resident
+// warps that spill); the others take what they need.
+__host__ __device__ constexpr int persistent_min_blocks(int bs, uint32_t pm, int tpt) {
+    const int tps = pm == PM_MS ? 1024 : pm == PM_FIB ? (tpt >= 4 ? 512 : tpt == 2 ? 768 : 1024) : 0;
+    return tps / bs > 0 ? tps / bs : 1;
 }
 
 // Scheduler state a persistent block carries between epochs (thread 0's).
@@ -225,7 +229,7 @@ __device__ __forceinline__ uint32_t adopt_solo_state(const Conf &c, Ctl *ctl, Sm
 }
 
 template <int BS, int TPT, uint32_t PM>
-__global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM)) k_persistent(Ctl *ctl, Conf c, unsigned long long *blk) {
+__global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_persistent(Ctl *ctl, Conf c, unsigned long long *blk) {
     __shared__ Smem<BS> sm;
     __shared__ uint32_t sm_e;
     uint32_t bar = 0;
