@@ -71,7 +71,7 @@ extern "C" {
 #define TREES_SCHED_HOSTLOOP 2   /* the paper's host loop: one launch and one device->host read per epoch (Sec. 5.2.4) */
 
 typedef struct {
-    int32_t block_size;      /* threads per block: 256, 512 or 1024 (default 512) */
+    int32_t block_size;      /* threads per block: 128, 256, 512 or 1024 (default 512) */
     int32_t blocks_per_sm;   /* persistent grid = SMs * this; 0 = as many as fit */
     int32_t scheduler;       /* TREES_SCHED_* */
     int32_t trace;           /* 1 = record the per-epoch trace (trees_trace) */
@@ -210,7 +210,7 @@ typedef struct {
 } trees_tune_entry_t;
 
 /* Picks the configuration that runs `job` fastest on the current device:
- * every block size {256, 512, 1024} x slots per thread {1, 2, 4} x scheduler
+ * every block size {128, 256, 512, 1024} x slots per thread {1, 2, 4} x scheduler
  * {persistent grid barrier, CUDA-graph relaunch}, each on a fresh context of
  * capacity_slots slots built from `base` (NULL = defaults), one warm-up and
  * `reps` timed runs.  A mergesort job's keys are restored from a copy before

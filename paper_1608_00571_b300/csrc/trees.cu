@@ -256,6 +256,9 @@ const void *persistent_kernel(int program, int bs, int tpt) {
 
 bool kern_by(int bs, int tpt, Kern *k) {
     switch (bs * 10 + tpt) {
+    case 1281: *k = kern_for<128, 1>(); return true;
+    case 1282: *k = kern_for<128, 2>(); return true;
+    case 1284: *k = kern_for<128, 4>(); return true;
     case 2561: *k = kern_for<256, 1>(); return true;
     case 2562: *k = kern_for<256, 2>(); return true;
     case 2564: *k = kern_for<256, 4>(); return true;
@@ -442,7 +445,8 @@ static int validate_cfg(const trees_config_t *cfg, trees_config_t *out) {
     if (cfg) *out = *cfg;
     else trees_default_config(out);
     normalize(out);
-    if (out->block_size != 256 && out->block_size != 512 && out->block_size != 1024) return TREES_ERR_INVALID_ARG;
+    if (out->block_size != 128 && out->block_size != 256 && out->block_size != 512 && out->block_size != 1024)
+        return TREES_ERR_INVALID_ARG;
     if (out->scheduler < TREES_SCHED_PERSISTENT || out->scheduler > TREES_SCHED_HOSTLOOP) return TREES_ERR_INVALID_ARG;
     if (out->blocks_per_sm < 0 || out->grid_blocks < 0) return TREES_ERR_INVALID_ARG;
     if (out->tasks_per_thread != 1 && out->tasks_per_thread != 2 && out->tasks_per_thread != 4)
@@ -1180,6 +1184,7 @@ const void *batch_kernel() {
 
 const void *batch_kernel_for(int bs) {
     switch (bs) {
+    case 128: return batch_kernel<128>();
     case 256: return batch_kernel<256>();
     case 512: return batch_kernel<512>();
     default: return batch_kernel<1024>();

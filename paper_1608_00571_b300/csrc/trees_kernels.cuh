@@ -317,6 +317,9 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
 template <uint32_t PM>
 const void *persistent_kernel_for(int bs, int tpt) {
     switch (bs * 10 + tpt) {
+    case 1281: return (const void *)k_persistent<128, 1, PM>;
+    case 1282: return (const void *)k_persistent<128, 2, PM>;
+    case 1284: return (const void *)k_persistent<128, 4, PM>;
     case 2561: return (const void *)k_persistent<256, 1, PM>;
     case 2562: return (const void *)k_persistent<256, 2, PM>;
     case 2564: return (const void *)k_persistent<256, 4, PM>;

@@ -113,12 +113,12 @@ extern "C" int trees_autotune(const trees_job_t *job, size_t capacity_slots, con
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int bss[3] = {256, 512, 1024}, tpts[3] = {1, 2, 4};
+    const int bss[4] = {128, 256, 512, 1024}, tpts[3] = {1, 2, 4};
     const int scheds[2] = {TREES_SCHED_PERSISTENT, TREES_SCHED_GRAPH};
     double bestv = -1.0;
     int first_err = TREES_OK, n = 0;
     for (int si = 0; si < 2; ++si)
-        for (int bi = 0; bi < 3; ++bi)
+        for (int bi = 0; bi < 4; ++bi)
             for (int ti = 0; ti < 3; ++ti) {
                 trees_config_t cfg = b0;
                 cfg.block_size = bss[bi];

@@ -69,7 +69,7 @@ class Mix:
             assert np.array_equal(d.cpu().numpy().view(np.uint32), want), i
 
 
-@pytest.mark.parametrize("bs", [256, 512, 1024])
+@pytest.mark.parametrize("bs", [128, 256, 512, 1024])
 def test_batch_matches_solo_oracle(bs):
     mix = Mix(48)
     ctx = T.trees_create(1 << 22, T.trees_default_config(block_size=bs))

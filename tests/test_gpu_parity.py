@@ -57,7 +57,7 @@ def host_u32(t):
 # ------------------------------------------------------------------ fib
 
 @pytest.mark.parametrize("sched", SCHEDS)
-@pytest.mark.parametrize("bs", [256, 512, 1024])
+@pytest.mark.parametrize("bs", [128, 256, 512, 1024])
 @pytest.mark.parametrize("tpt", [1, 2, 4])
 def test_fib20(sched, bs, tpt):
     sim = oracle.tvm_run(oracle.FIB, fib_n=20)
@@ -129,7 +129,7 @@ def test_mergesort(sched, n):
 
 
 @pytest.mark.parametrize("sched", [T.TREES_SCHED_PERSISTENT, T.TREES_SCHED_GRAPH])
-@pytest.mark.parametrize("bs", [256, 512, 1024])
+@pytest.mark.parametrize("bs", [128, 256, 512, 1024])
 @pytest.mark.parametrize("n", [5000, 100000, (1 << 20) + 3])
 def test_mergesort_block_sizes(sched, bs, n):
     keys = gen.keys_u32(7 * n + bs, n)
