@@ -504,7 +504,8 @@ def main():
     T.trees_destroy(tctx)
     alg = fib_alg_bytes(stats, trace)
     achieved = alg / (ms_step / 1000.0) / 1e9
-    traffic = ncu_traffic("fib34_persistent")
+    traffic = ncu_traffic(f"fib34_persistent_{cfg.block_size}x{cfg.tasks_per_thread}"
+                          if cfg.scheduler == T.TREES_SCHED_PERSISTENT else "none")
 
     # ---------------- end to end through the C ABI: host input, host result
     ectx = T.trees_create(20_000_000, cfg)
