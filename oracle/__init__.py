@@ -68,6 +68,12 @@ def _bind(lib):
     lib.oracle_bfs.restype = ctypes.c_int64
     lib.oracle_bfs.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                ctypes.c_void_p]
+    lib.oracle_sssp_dijkstra.restype = ctypes.c_int64
+    lib.oracle_sssp_dijkstra.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int32, ctypes.c_void_p]
+    lib.oracle_sssp_worklist.restype = ctypes.c_int
+    lib.oracle_sssp_worklist.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int32, ctypes.c_void_p, u64p, u64p]
     lib.oracle_nqueens.restype = ctypes.c_uint64
     lib.oracle_nqueens.argtypes = [ctypes.c_int, u64p, u64p]
     lib.oracle_tvm_run.restype = ctypes.c_int
@@ -118,6 +124,44 @@ def bfs(row_ptr: np.ndarray, col: np.ndarray, src: int = 0):
     reached = _load().oracle_bfs(nv, row_ptr.ctypes.data, col.ctypes.data if col.size else None, src,
                                  level.ctypes.data)
     return level, int(reached)
+
+
+SSSP_INF = np.iinfo(np.uint64).max  # distance of an unreachable vertex
+
+
+def _csr_args(row_ptr, col, weight):
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    weight = np.ascontiguousarray(weight, dtype=np.uint32)
+    assert weight.shape == col.shape
+    return row_ptr, col, weight
+
+
+def sssp_dijkstra(row_ptr: np.ndarray, col: np.ndarray, weight: np.ndarray, src: int = 0):
+    """Dijkstra with a binary heap: ``(dist uint64 array, reached count)``;
+    unreachable vertices hold SSSP_INF."""
+    row_ptr, col, weight = _csr_args(row_ptr, col, weight)
+    nv = row_ptr.shape[0] - 1
+    dist = np.empty(nv, dtype=np.uint64)
+    reached = _load().oracle_sssp_dijkstra(nv, row_ptr.ctypes.data, col.ctypes.data if col.size else None,
+                                           weight.ctypes.data if weight.size else None, src, dist.ctypes.data)
+    if reached < 0:
+        raise MemoryError("oracle_sssp_dijkstra")
+    return dist, int(reached)
+
+
+def sssp_worklist(row_ptr: np.ndarray, col: np.ndarray, weight: np.ndarray, src: int = 0):
+    """The worklist relaxation of Sec. 6.3, sequential: ``(dist, rounds, relaxed vertices)``."""
+    row_ptr, col, weight = _csr_args(row_ptr, col, weight)
+    nv = row_ptr.shape[0] - 1
+    dist = np.empty(nv, dtype=np.uint64)
+    rounds, relaxed = ctypes.c_uint64(), ctypes.c_uint64()
+    rc = _load().oracle_sssp_worklist(nv, row_ptr.ctypes.data, col.ctypes.data if col.size else None,
+                                      weight.ctypes.data if weight.size else None, src, dist.ctypes.data,
+                                      ctypes.byref(rounds), ctypes.byref(relaxed))
+    if rc != 0:
+        raise MemoryError("oracle_sssp_worklist")
+    return dist, int(rounds.value), int(relaxed.value)
 
 
 def nqueens(n: int):

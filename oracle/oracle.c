@@ -117,6 +117,110 @@ int64_t oracle_bfs(int32_t nv, const int32_t *row_ptr, const int32_t *col, int32
     return tail;
 }
 
+/* Single-source shortest paths, Dijkstra's algorithm with a binary heap and
+ * lazy deletion: the plain definition of the distances the SSSP program of
+ * Sec. 6.3 reaches.  Non-negative u32 edge weights aligned with col; dist[v]
+ * = length of a shortest path from src, UINT64_MAX if unreachable.  Returns
+ * the number of reached vertices (-2: out of memory). */
+typedef struct { uint64_t d; int32_t v; } heap_item;
+
+static void heap_push(heap_item *h, int64_t *n, heap_item x) {
+    int64_t i = (*n)++;
+    while (i > 0) {
+        const int64_t p = (i - 1) / 2;
+        if (h[p].d <= x.d) break;
+        h[i] = h[p];
+        i = p;
+    }
+    h[i] = x;
+}
+
+static heap_item heap_pop(heap_item *h, int64_t *n) {
+    const heap_item top = h[0], x = h[--(*n)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t c = 2 * i + 1;
+        if (c >= *n) break;
+        if (c + 1 < *n && h[c + 1].d < h[c].d) c++;
+        if (x.d <= h[c].d) break;
+        h[i] = h[c];
+        i = c;
+    }
+    if (*n > 0) h[i] = x;
+    return top;
+}
+
+int64_t oracle_sssp_dijkstra(int32_t nv, const int32_t *row_ptr, const int32_t *col, const uint32_t *weight,
+                             int32_t src, uint64_t *dist) {
+    for (int32_t v = 0; v < nv; v++) dist[v] = UINT64_MAX;
+    if (src < 0 || src >= nv) return 0;
+    const int64_t m = row_ptr[nv];
+    heap_item *h = (heap_item *)malloc(sizeof(heap_item) * (size_t)(m + 1));
+    uint8_t *done = (uint8_t *)calloc((size_t)nv, 1);
+    if (!h || !done) { free(h); free(done); return -2; }
+    int64_t hn = 0, reached = 0;
+    dist[src] = 0;
+    heap_push(h, &hn, (heap_item){0, src});
+    while (hn > 0) {
+        const heap_item it = heap_pop(h, &hn);
+        if (done[it.v]) continue;  /* a stale entry: the vertex was settled by a shorter one */
+        done[it.v] = 1;
+        reached++;
+        for (int32_t e = row_ptr[it.v]; e < row_ptr[it.v + 1]; e++) {
+            const int32_t u = col[e];
+            const uint64_t nd = it.d + weight[e];
+            if (nd < dist[u]) { dist[u] = nd; heap_push(h, &hn, (heap_item){nd, u}); }
+        }
+    }
+    free(h);
+    free(done);
+    return reached;
+}
+
+/* The worklist relaxation of Sec. 6.3, run sequentially: every vertex of the
+ * input worklist relaxes all its out-edges (dist[u] = min(dist[u], dist[v] +
+ * w)); a vertex whose distance dropped is appended to the output worklist
+ * once per round; the lists swap until a round explores nothing.  Reaches
+ * the same distances as Dijkstra.  *rounds and *relaxed receive the number of
+ * rounds and of vertex relaxations.  Returns 0 (-2: out of memory). */
+int oracle_sssp_worklist(int32_t nv, const int32_t *row_ptr, const int32_t *col, const uint32_t *weight,
+                         int32_t src, uint64_t *dist, uint64_t *rounds, uint64_t *relaxed) {
+    *rounds = 0;
+    *relaxed = 0;
+    for (int32_t v = 0; v < nv; v++) dist[v] = UINT64_MAX;
+    if (src < 0 || src >= nv) return 0;
+    int32_t *in = (int32_t *)malloc(sizeof(int32_t) * (size_t)nv);
+    int32_t *out = (int32_t *)malloc(sizeof(int32_t) * (size_t)nv);
+    int64_t *queued = (int64_t *)malloc(sizeof(int64_t) * (size_t)nv);
+    if (!in || !out || !queued) { free(in); free(out); free(queued); return -2; }
+    for (int32_t v = 0; v < nv; v++) queued[v] = -1;
+    int64_t nin = 0;
+    dist[src] = 0;
+    in[nin++] = src;
+    while (nin > 0) {
+        const int64_t r = (int64_t)(*rounds)++;
+        int64_t nout = 0;
+        for (int64_t i = 0; i < nin; i++) {
+            const int32_t v = in[i];
+            (*relaxed)++;
+            for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; e++) {
+                const int32_t u = col[e];
+                const uint64_t nd = dist[v] + weight[e];
+                if (nd < dist[u]) {
+                    dist[u] = nd;
+                    if (queued[u] != r) { queued[u] = r; out[nout++] = u; }
+                }
+            }
+        }
+        int32_t *t = in; in = out; out = t;
+        nin = nout;
+    }
+    free(in);
+    free(out);
+    free(queued);
+    return 0;
+}
+
 /* N-Queens by backtracking over rows with explicit used-column and
  * used-diagonal arrays.  Counts solutions, the nodes of the backtracking tree
  * (every consistent partial placement, root included: one row task each) and

@@ -52,6 +52,8 @@ def _load():
         lib.trees_gen_rmat.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(_Graph)]
         lib.trees_gen_graph_free.argtypes = [ctypes.POINTER(_Graph)]
+        lib.trees_gen_weights.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_uint32, ctypes.c_void_p]
         lib.trees_gen_jobs.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]
         lib.trees_gen_poisson_arrivals.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_double,
@@ -122,3 +124,14 @@ def binary_tree(seed: int, nnodes: int):
     if nnodes:
         _load().trees_gen_binary_tree(seed, nnodes, left.ctypes.data, right.ctypes.data)
     return left, right
+
+
+def weights(seed: int, row_ptr: np.ndarray, col: np.ndarray, wmax: int = 255) -> np.ndarray:
+    """uint32 edge weights in [1, wmax] aligned with col, symmetric in (v, u)."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    out = np.empty(col.shape[0], dtype=np.uint32)
+    if col.size:
+        _load().trees_gen_weights(seed, row_ptr.shape[0] - 1, row_ptr.ctypes.data, col.ctypes.data, wmax,
+                                  out.ctypes.data)
+    return out

@@ -210,3 +210,17 @@ void trees_gen_binary_tree(uint64_t seed, int32_t nnodes, int32_t *left, int32_t
         }
     }
 }
+
+/* Edge weights for a CSR graph, aligned with col: the weight of edge (v, u)
+ * is 1 + splitmix64(seed, min(v,u) * 2^32 + max(v,u)) mod wmax, so both
+ * directions of an undirected edge weigh the same.  wmax >= 1. */
+void trees_gen_weights(uint64_t seed, int32_t nv, const int32_t *row_ptr, const int32_t *col, uint32_t wmax,
+                       uint32_t *out) {
+    for (int32_t v = 0; v < nv; v++) {
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; e++) {
+            const uint64_t u = (uint64_t)(uint32_t)col[e], w = (uint64_t)(uint32_t)v;
+            const uint64_t lo = u < w ? u : w, hi = u < w ? w : u;
+            out[e] = 1u + (uint32_t)(trees_gen_splitmix64(seed, (lo << 32) | hi) % wmax);
+        }
+    }
+}

@@ -296,3 +296,116 @@ def test_traversal_orders_random_tree():
         for c in (left[v], right[v]):
             if c >= 0:
                 assert post[v] > post[c]
+
+
+# ----------------------------------------------------------------- SSSP (Sec. 6.3)
+
+def floyd_warshall_weighted(nv, row_ptr, col, weight):
+    """All-pairs shortest path lengths by Floyd-Warshall (brute force, int64,
+    -1 = unreachable); the minimum weight is kept for parallel edges."""
+    inf = np.int64(1) << 60  # inf + inf stays inside int64
+    d = np.full((nv, nv), inf, dtype=np.int64)
+    for v in range(nv):
+        for e in range(row_ptr[v], row_ptr[v + 1]):
+            d[v, col[e]] = min(d[v, col[e]], int(weight[e]))
+    np.fill_diagonal(d, 0)
+    for k in range(nv):
+        d = np.minimum(d, d[:, k:k + 1] + d[k:k + 1, :])
+    return d, inf
+
+
+def weighted_random_graph(nv, p, seed, wmax, directed):
+    """Erdos-Renyi graph in CSR with weights in [0, wmax] (zero weights included)."""
+    rng = np.random.default_rng(seed)
+    a = rng.random((nv, nv)) < p
+    np.fill_diagonal(a, False)
+    if not directed:
+        a = np.triu(a, 1)
+        a = a | a.T
+    wm = rng.integers(0, wmax + 1, size=(nv, nv)).astype(np.uint32)
+    if not directed:
+        wm = np.triu(wm, 1)
+        wm = wm + wm.T
+    row_ptr = np.zeros(nv + 1, dtype=np.int32)
+    row_ptr[1:] = np.cumsum(a.sum(1))
+    cols = [np.nonzero(a[i])[0] for i in range(nv)]
+    col = np.concatenate(cols + [np.zeros(0, int)]).astype(np.int32)
+    weight = np.concatenate([wm[i, cols[i]] for i in range(nv)] + [np.zeros(0, np.uint32)]).astype(np.uint32)
+    return row_ptr, col, weight
+
+
+def check_sssp_invariants(row_ptr, col, weight, src, dist):
+    """dist[src] = 0; no edge can shorten a distance; every other reached vertex
+    has an incoming edge that attains its distance (the shortest-path tree)."""
+    nv = row_ptr.shape[0] - 1
+    inf = oracle.SSSP_INF
+    assert dist[src] == 0
+    src_of = np.repeat(np.arange(nv), np.diff(row_ptr))
+    ds, du = dist[src_of], dist[col]
+    ok = ds != inf
+    cand = ds[ok] + weight[ok].astype(np.uint64)
+    assert (du[ok] <= cand).all()
+    tight = np.zeros(nv, dtype=bool)
+    tight[col[ok][du[ok] == cand]] = True
+    reached = dist != inf
+    reached[src] = False
+    assert tight[reached].all()
+
+
+@pytest.mark.parametrize("nv,p,seed,wmax,directed", [(1, 0.0, 0, 5, False), (6, 0.0, 1, 5, True),
+                                                     (12, 0.25, 2, 9, True), (40, 0.08, 3, 100, False),
+                                                     (64, 0.05, 4, 1, True), (64, 0.2, 5, 1000, False)])
+def test_sssp_floyd_warshall(nv, p, seed, wmax, directed):
+    row_ptr, col, weight = weighted_random_graph(nv, p, seed, wmax, directed)
+    d, inf = floyd_warshall_weighted(nv, row_ptr, col, weight)
+    for src in {0, nv - 1}:
+        want = d[src].astype(np.uint64)
+        want[d[src] >= inf] = oracle.SSSP_INF
+        dist, reached = oracle.sssp_dijkstra(row_ptr, col, weight, src)
+        assert np.array_equal(dist, want)
+        assert reached == int((d[src] < inf).sum())
+        wl, rounds, relaxed = oracle.sssp_worklist(row_ptr, col, weight, src)
+        assert np.array_equal(wl, want)
+        assert relaxed >= reached and rounds >= 1
+        check_sssp_invariants(row_ptr, col, weight, src, dist)
+
+
+def test_sssp_rmat_scipy_and_worklist():
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import dijkstra
+    row_ptr, col, info = gen.rmat(10, 16, seed=2)
+    nv = info["nv"]
+    weight = gen.weights(3, row_ptr, col)
+    assert weight.min() >= 1 and weight.max() <= 255
+    m = csr_matrix((weight.astype(np.float64), col, row_ptr), shape=(nv, nv))
+    d = dijkstra(m, indices=[0])[0]
+    want = np.where(np.isinf(d), 0, d).astype(np.uint64)
+    want[np.isinf(d)] = oracle.SSSP_INF
+    dist, reached = oracle.sssp_dijkstra(row_ptr, col, weight, 0)
+    assert np.array_equal(dist, want)
+    wl, rounds, relaxed = oracle.sssp_worklist(row_ptr, col, weight, 0)
+    assert np.array_equal(wl, want)
+    assert rounds > int(oracle.bfs(row_ptr, col, 0)[0].max())   # weights make paths longer than hops
+    check_sssp_invariants(row_ptr, col, weight, 0, dist)
+
+
+def test_sssp_unit_weights_are_bfs_levels():
+    row_ptr, col, info = gen.rmat(11, 8, seed=7)
+    level, _ = oracle.bfs(row_ptr, col, 3)
+    dist, _ = oracle.sssp_dijkstra(row_ptr, col, np.ones(col.shape[0], np.uint32), 3)
+    want = np.maximum(level, 0).astype(np.uint64)
+    want[level < 0] = oracle.SSSP_INF
+    assert np.array_equal(dist, want)
+    wl, rounds, relaxed = oracle.sssp_worklist(row_ptr, col, np.ones(col.shape[0], np.uint32), 3)
+    assert np.array_equal(wl, want)
+    assert rounds == int(level.max()) + 1 and relaxed == int((level >= 0).sum())  # BFS levels, each once
+
+
+def test_sssp_source_out_of_range_and_isolated():
+    row_ptr = np.array([0, 1, 2, 2], np.int32)
+    col = np.array([1, 0], np.int32)
+    w = np.array([4, 4], np.uint32)
+    dist, reached = oracle.sssp_dijkstra(row_ptr, col, w, 5)
+    assert reached == 0 and (dist == oracle.SSSP_INF).all()
+    dist, reached = oracle.sssp_dijkstra(row_ptr, col, w, 2)
+    assert reached == 1 and dist[2] == 0 and dist[0] == dist[1] == oracle.SSSP_INF

@@ -35,6 +35,13 @@ MUTANTS = {
     "encoding_upper_bound": ("if (c < lo_code || c > hi_code) continue;", "if (c < lo_code || c >= hi_code) continue;"),
     # a join reads the wrong sibling
     "nq_sum_wrong_index": ("sum += m->result[m->link[s] + i];", "sum += m->result[m->link[s] + i + 1];"),
+    # Dijkstra's heap keeps the wrong end on top
+    "sssp_heap_order": ("        if (h[p].d <= x.d) break;", "        if (h[p].d >= x.d) break;"),
+    # a relaxation adds one to every path
+    "sssp_relax_plus_one": ("const uint64_t nd = it.d + weight[e];", "const uint64_t nd = it.d + weight[e] + 1u;"),
+    # the worklist never revisits a vertex whose distance dropped again
+    "sssp_worklist_no_requeue": ("if (queued[u] != r) { queued[u] = r; out[nout++] = u; }",
+                                 "if (queued[u] < 0) { queued[u] = r; out[nout++] = u; }"),
     # the plain recursion counts calls wrongly
     "fib_calls_skip": ("    (*calls)++;\n    if (n < 2) return n;", "    if (n < 2) return n;\n    (*calls)++;"),
 }
@@ -53,6 +60,8 @@ def run_pins():
     pins.test_mergesort_matches_numpy(3000)
     pins.test_mergesort_brute_force_small(2)
     pins.test_bfs_floyd_warshall(40, 0.05, 3)
+    pins.test_sssp_floyd_warshall(40, 0.08, 3, 100, False)
+    pins.test_sssp_rmat_scipy_and_worklist()
     pins.test_fig3_postorder_trace("B")
     pins.test_traversal_orders_random_tree()
 
