@@ -55,7 +55,9 @@ extern "C" {
 #define TREES_TASK_PO 8          /* postorder(node) of Fig. 2 */
 #define TREES_TASK_PO_AFTER 9    /* visitAfter(node) of Fig. 2 (join) */
 #define TREES_TASK_PRE 10        /* preorder(node) of Fig. 2 */
-#define TREES_NUM_TASK_TYPES 10
+#define TREES_TASK_SSSP_RELAX 11 /* SSSP vertex (Sec. 6.3's worklist relaxation as tasks): map over its
+                                    out-edges; a neighbour whose distance it shortens is forked once per epoch */
+#define TREES_NUM_TASK_TYPES 11
 
 /* ------------------------------------------------------------ programs */
 #define TREES_PROG_FIB 1
@@ -64,6 +66,7 @@ extern "C" {
 #define TREES_PROG_BFS 4
 #define TREES_PROG_POSTORDER 5
 #define TREES_PROG_PREORDER 6
+#define TREES_PROG_SSSP 7
 
 /* ------------------------------------------------------------ schedulers */
 #define TREES_SCHED_PERSISTENT 0 /* one cooperative launch; one grid barrier per epoch */
@@ -121,18 +124,22 @@ int trees_geometry(const trees_ctx *ctx, int32_t *grid_blocks, int32_t *block_si
 typedef struct {
     int32_t program;          /* TREES_PROG_* */
     uint32_t n;               /* fib: n; N-Queens: board size (1..16); mergesort: number of keys;
-                                 BFS: source vertex; traversal: number of nodes */
+                                 BFS, SSSP: source vertex; traversal: number of nodes */
     uint32_t cutoff;          /* fib: a call with n <= cutoff is a leaf computed in its task (0 = none) */
     uint32_t leaf;            /* mergesort: leaf size, 1..1024 (0 = 1024) */
     uint32_t *keys;           /* mergesort: device keys, sorted in place */
     uint32_t *scratch;        /* mergesort: device buffer of n keys (NULL = the context's own) */
-    const int32_t *row_ptr;   /* BFS: device CSR row offsets [nv+1] */
-    const int32_t *col;       /* BFS: device CSR columns */
+    const int32_t *row_ptr;   /* BFS, SSSP: device CSR row offsets [nv+1] */
+    const int32_t *col;       /* BFS, SSSP: device CSR columns */
     int32_t *level;           /* BFS: device output [nv], -1 = unreachable */
-    int32_t nv;               /* BFS: vertex count */
+    int32_t nv;               /* BFS, SSSP: vertex count */
     const int32_t *left;      /* traversal: device child arrays [n], -1 = nil; node 0 is the root */
     const int32_t *right;
     int32_t *visit_epoch;     /* traversal: device output [n], index of the epoch that visited the node */
+    const uint32_t *weight;   /* SSSP: device edge weights aligned with col */
+    uint64_t *dist;           /* SSSP: device output [nv], shortest distance from the source,
+                                 UINT64_MAX = unreachable */
+    uint32_t *sched;          /* SSSP: device scratch [nv]: the last epoch each vertex was forked for */
 } trees_job_t;
 
 /* Sec. 5.2.1 initialisation + the epoch loop: writes the job's root task
@@ -192,6 +199,18 @@ int trees_nqueens(trees_ctx *ctx, uint32_t n, void *stream);
 int trees_mergesort_u32(trees_ctx *ctx, uint32_t *dev_keys, uint32_t *dev_scratch, uint32_t n, void *stream);
 int trees_bfs(trees_ctx *ctx, const int32_t *dev_row_ptr, const int32_t *dev_col, int32_t nv, int32_t src,
               int32_t *dev_level, void *stream);
+/* Single-source shortest paths as tasks (Sec. 6.3): relax(v) maps over v's
+ * out-edges (dist[u] = min(dist[u], dist[v] + w) by atomic minimum) and forks
+ * relax(u) for the next epoch for every u it shortened, once per epoch per
+ * vertex (dev_sched dedupes); the run ends when an epoch shortens nothing.
+ * Distances are u64 (no overflow for u32 weights); the task and epoch counts
+ * depend on the order of the races, the distances do not.  Every task slot
+ * stays in use until the run ends (no joins), so the context needs one slot
+ * per relax task (at least the reachable vertices, more when vertices are
+ * shortened again).  Errors: INVALID_ARG (null arrays, nv < 1, src out of
+ * range), CAPACITY at run time. */
+int trees_sssp(trees_ctx *ctx, const int32_t *dev_row_ptr, const int32_t *dev_col, const uint32_t *dev_weight,
+               int32_t nv, int32_t src, uint64_t *dev_dist, uint32_t *dev_sched, void *stream);
 
 /* ------------------------------------------------------------ measurement */
 
@@ -246,7 +265,9 @@ typedef struct {
 /* Task-vector slots a job needs at its peak.  *exact (may be NULL) is set to
  * 1 when the count is exact (fib, mergesort, traversal upper bound, BFS) and
  * 0 when it is an estimate (N-Queens: the backtracking tree is not known
- * before it is explored; a job that outgrows it ends with CAPACITY). */
+ * before it is explored; SSSP: one slot per relax task, at least the vertex
+ * count, more when distances drop again; a job that outgrows it ends with
+ * CAPACITY). */
 uint64_t trees_job_slots(const trees_job_t *job, int32_t *exact);
 
 /* Runs njobs jobs in one persistent launch on the context's task vector.

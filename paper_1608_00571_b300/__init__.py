@@ -35,6 +35,7 @@ TREES_PROG_NQUEENS = 3
 TREES_PROG_BFS = 4
 TREES_PROG_POSTORDER = 5
 TREES_PROG_PREORDER = 6
+TREES_PROG_SSSP = 7
 
 # schedulers
 TREES_SCHED_PERSISTENT = 0
@@ -61,7 +62,8 @@ class trees_job_t(ctypes.Structure):
                 ("leaf", ctypes.c_uint32), ("keys", ctypes.c_void_p), ("scratch", ctypes.c_void_p),
                 ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("level", ctypes.c_void_p),
                 ("nv", ctypes.c_int32), ("left", ctypes.c_void_p), ("right", ctypes.c_void_p),
-                ("visit_epoch", ctypes.c_void_p)]
+                ("visit_epoch", ctypes.c_void_p), ("weight", ctypes.c_void_p), ("dist", ctypes.c_void_p),
+                ("sched", ctypes.c_void_p)]
 
 
 class trees_stats_t(ctypes.Structure):
@@ -120,6 +122,7 @@ _SIGNATURES = [
     ("trees_nqueens", ctypes.c_int, [_ctxp, ctypes.c_uint32, _vp]),
     ("trees_mergesort_u32", ctypes.c_int, [_ctxp, _vp, _vp, ctypes.c_uint32, _vp]),
     ("trees_bfs", ctypes.c_int, [_ctxp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
+    ("trees_sssp", ctypes.c_int, [_ctxp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]),
     ("trees_barrier_floor", ctypes.c_int, [_ctxp, ctypes.c_uint32, _vp, ctypes.POINTER(ctypes.c_double)]),
     ("trees_fib_noalloc", ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, _vp, _vp, _vp]),
     ("trees_autotune", ctypes.c_int, [ctypes.POINTER(trees_job_t), ctypes.c_size_t, ctypes.POINTER(trees_config_t),
@@ -227,7 +230,8 @@ def trees_geometry(ctx):
 
 
 def make_job(program: int, n: int = 0, cutoff: int = 0, leaf: int = 0, keys=None, scratch=None, row_ptr=None,
-             col=None, level=None, nv: int = 0, left=None, right=None, visit_epoch=None) -> trees_job_t:
+             col=None, level=None, nv: int = 0, left=None, right=None, visit_epoch=None, weight=None, dist=None,
+             sched=None) -> trees_job_t:
     j = trees_job_t()
     j.program = program
     j.n = n
@@ -242,6 +246,9 @@ def make_job(program: int, n: int = 0, cutoff: int = 0, leaf: int = 0, keys=None
     j.left = _ptr(left)
     j.right = _ptr(right)
     j.visit_epoch = _ptr(visit_epoch)
+    j.weight = _ptr(weight)
+    j.dist = _ptr(dist)
+    j.sched = _ptr(sched)
     return j
 
 
@@ -289,6 +296,11 @@ def trees_mergesort_u32(ctx, keys, scratch, n: int, stream=None) -> int:
 def trees_bfs(ctx, row_ptr, col, nv: int, src: int, level, stream=None) -> int:
     return _check("trees_bfs", lib().trees_bfs(ctx, _ptr(row_ptr), _ptr(col), nv, src, _ptr(level),
                                                _stream(stream)))
+
+
+def trees_sssp(ctx, row_ptr, col, weight, nv: int, src: int, dist, sched, stream=None) -> int:
+    return _check("trees_sssp", lib().trees_sssp(ctx, _ptr(row_ptr), _ptr(col), _ptr(weight), nv, src, _ptr(dist),
+                                                 _ptr(sched), _stream(stream)))
 
 
 def trees_barrier_floor(ctx, iters: int = 1000, stream=None) -> float:

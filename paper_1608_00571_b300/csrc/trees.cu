@@ -69,6 +69,15 @@ __global__ void k_bfs_init(int32_t *level, int32_t nv, int32_t src) {
         level[v] = (v == src) ? 0 : -1;
 }
 
+// SSSP start: every distance unknown but the source's; no vertex forked yet
+// (the root task relaxes the source in epoch 0).
+__global__ void k_sssp_init(unsigned long long *dist, uint32_t *sched, int32_t nv, int32_t src) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+        dist[v] = (v == src) ? 0ull : ~0ull;
+        sched[v] = 0u;
+    }
+}
+
 // Phase 2 of one epoch as its own kernel (graph and host-loop schedulers).
 // from_ctl = 1: the epoch comes from the control block (graph); 0: from the
 // arguments (host loop, grid sized to the NDRange as in Sec. 5.1.1).
@@ -250,6 +259,7 @@ const void *persistent_kernel(int program, int bs, int tpt) {
     case TREES_PROG_MERGESORT: return persistent_kernel_ms(bs, tpt);
     case TREES_PROG_NQUEENS: return persistent_kernel_nq(bs, tpt);
     case TREES_PROG_BFS: return persistent_kernel_bfs(bs, tpt);
+    case TREES_PROG_SSSP: return persistent_kernel_sssp(bs, tpt);
     default: return persistent_kernel_trav(bs, tpt);
     }
 }
@@ -275,10 +285,11 @@ bool kern_by(int bs, int tpt, Kern *k) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 constexpr int NMT = 7;  // tiled-map descriptor columns: kind, a, b, c, job, first tile, split
+constexpr int NME = 5;  // element-map columns: first adjacency index, first element, job, tile's first descriptor, vertex
 
 struct Layout {
     size_t off_dev, off_code, off_a0, off_a1, off_link, off_result;
-    size_t off_mt[NMT], off_me[4], off_trace, off_tvalid, off_gstack, off_blk, total;
+    size_t off_mt[NMT], off_me[NME], off_trace, off_tvalid, off_gstack, off_blk, total;
 };
 
 Layout make_layout(size_t cap, size_t mcap, size_t trace_cap, size_t gstack_cap) {
@@ -296,7 +307,7 @@ Layout make_layout(size_t cap, size_t mcap, size_t trace_cap, size_t gstack_cap)
     L.off_link = take(cap * 4);
     L.off_result = take(cap * 8);
     for (int i = 0; i < NMT; ++i) L.off_mt[i] = take(mcap * 4);
-    for (int i = 0; i < 4; ++i) L.off_me[i] = take(mcap * 4);
+    for (int i = 0; i < NME; ++i) L.off_me[i] = take(mcap * 4);
     L.off_trace = take(trace_cap * sizeof(trees_epoch_t));
     L.off_tvalid = take(trace_cap * 4);
     L.off_gstack = take(gstack_cap * sizeof(Range));
@@ -409,8 +420,8 @@ static int finish_create(trees_ctx *x) {
     c.cap = x->cap;
     uint32_t **mt[NMT] = {&c.mt_kind, &c.mt_a, &c.mt_b, &c.mt_c, &c.mt_job, &c.mt_tilebase, &c.mt_split};
     for (int i = 0; i < NMT; ++i) *mt[i] = reinterpret_cast<uint32_t *>(m + L.off_mt[i]);
-    uint32_t **me[4] = {&c.me_v, &c.me_base, &c.me_job, &c.me_tfd};
-    for (int i = 0; i < 4; ++i) *me[i] = reinterpret_cast<uint32_t *>(m + L.off_me[i]);
+    uint32_t **me[NME] = {&c.me_v, &c.me_base, &c.me_job, &c.me_tfd, &c.me_src};
+    for (int i = 0; i < NME; ++i) *me[i] = reinterpret_cast<uint32_t *>(m + L.off_me[i]);
     c.mcap = x->mcap;
     c.trace = reinterpret_cast<trees_epoch_t *>(m + L.off_trace);
     c.trace_valid = reinterpret_cast<uint32_t *>(m + L.off_tvalid);
@@ -764,6 +775,19 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
         type = TREES_TASK_BFS_VISIT;
         a0 = job->n;
         break;
+    case TREES_PROG_SSSP:
+        if (!job->row_ptr || !job->col || !job->weight || !job->dist || !job->sched || job->nv < 1 ||
+            (int32_t)job->n < 0 || (int32_t)job->n >= job->nv)
+            return TREES_ERR_INVALID_ARG;
+        rp.row_ptr = job->row_ptr;
+        rp.col = job->col;
+        rp.weight = job->weight;
+        rp.dist = reinterpret_cast<unsigned long long *>(job->dist);
+        rp.sched = job->sched;
+        rp.nv = job->nv;
+        type = TREES_TASK_SSSP_RELAX;
+        a0 = job->n;
+        break;
     case TREES_PROG_POSTORDER:
     case TREES_PROG_PREORDER:
         if (job->n && (!job->left || !job->right || !job->visit_epoch)) return TREES_ERR_INVALID_ARG;
@@ -785,6 +809,10 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
     if (job->program == TREES_PROG_BFS) {
         const int nb = std::min<int64_t>((job->nv + 255) / 256, 65536);
         k_bfs_init<<<nb, 256, 0, st>>>(job->level, job->nv, (int32_t)job->n);
+    }
+    if (job->program == TREES_PROG_SSSP) {
+        const int nb = std::min<int64_t>((job->nv + 255) / 256, 65536);
+        k_sssp_init<<<nb, 256, 0, st>>>(rp.dist, job->sched, job->nv, (int32_t)job->n);
     }
     if (job->program == TREES_PROG_POSTORDER || job->program == TREES_PROG_PREORDER) {
         if (job->n && cudaMemsetAsync(job->visit_epoch, 0xFF, (size_t)job->n * 4, st) != cudaSuccess)
@@ -926,6 +954,21 @@ int trees_bfs(trees_ctx *x, const int32_t *row_ptr, const int32_t *col, int32_t 
     return trees_run(x, &j, stream);
 }
 
+int trees_sssp(trees_ctx *x, const int32_t *row_ptr, const int32_t *col, const uint32_t *weight, int32_t nv,
+               int32_t src, uint64_t *dist, uint32_t *sched, void *stream) {
+    trees_job_t j;
+    std::memset(&j, 0, sizeof(j));
+    j.program = TREES_PROG_SSSP;
+    j.n = (uint32_t)src;
+    j.row_ptr = row_ptr;
+    j.col = col;
+    j.weight = weight;
+    j.nv = nv;
+    j.dist = dist;
+    j.sched = sched;
+    return trees_run(x, &j, stream);
+}
+
 int trees_barrier_floor(trees_ctx *x, uint32_t iters, void *stream, double *us) {
     if (!x || !us || iters == 0) return TREES_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1046,8 +1089,8 @@ extern "C" int trees_fib_noalloc(uint32_t n, uint32_t cutoff, uint64_t *dev_resu
     c.cap = (uint32_t)NOALLOC_CAP;
     uint32_t **mt[NMT] = {&c.mt_kind, &c.mt_a, &c.mt_b, &c.mt_c, &c.mt_job, &c.mt_tilebase, &c.mt_split};
     for (int i = 0; i < NMT; ++i) *mt[i] = reinterpret_cast<uint32_t *>(m0 + L.off_mt[i]);
-    uint32_t **me[4] = {&c.me_v, &c.me_base, &c.me_job, &c.me_tfd};
-    for (int i = 0; i < 4; ++i) *me[i] = reinterpret_cast<uint32_t *>(m0 + L.off_me[i]);
+    uint32_t **me[NME] = {&c.me_v, &c.me_base, &c.me_job, &c.me_tfd, &c.me_src};
+    for (int i = 0; i < NME; ++i) *me[i] = reinterpret_cast<uint32_t *>(m0 + L.off_me[i]);
     c.mcap = 1;
     c.trace = reinterpret_cast<trees_epoch_t *>(m0 + L.off_trace);
     c.trace_valid = reinterpret_cast<uint32_t *>(m0 + L.off_tvalid);
@@ -1124,6 +1167,10 @@ uint64_t job_slots(const trees_job_t *j, int32_t *exact) {
         break;
     case TREES_PROG_BFS:
         need = (uint64_t)std::max(j->nv, 1);
+        break;
+    case TREES_PROG_SSSP:  // at least one relax task per reachable vertex; more when distances drop again
+        need = (uint64_t)std::max(j->nv, 1);
+        ex = 0;
         break;
     default:
         need = 0;

@@ -59,6 +59,9 @@ struct RunParams {
     int32_t nv;
     const int32_t *left, *right;
     int32_t *visit_epoch;
+    const uint32_t *weight;    // SSSP edge weights (aligned with col)
+    unsigned long long *dist;  // SSSP distances
+    uint32_t *sched;           // SSSP: the last epoch each vertex was forked for
 };
 
 // Read-only during a run: where everything lives.
@@ -68,8 +71,9 @@ struct Conf {
     uint32_t cap;
     // tiled map list: one descriptor per map operation, `units` tiles each
     uint32_t *mt_kind, *mt_a, *mt_b, *mt_c, *mt_job, *mt_tilebase, *mt_split;
-    // element map list (BFS expansion): one descriptor per vertex, one unit per edge
-    uint32_t *me_v, *me_base, *me_job, *me_tfd;
+    // element map list (BFS / SSSP expansion): one descriptor per vertex, one unit per edge;
+    // me_v = the vertex's first adjacency index, me_src = the vertex
+    uint32_t *me_v, *me_base, *me_job, *me_tfd, *me_src;
     uint32_t mcap;
     trees_epoch_t *trace;
     uint32_t *trace_valid;
@@ -178,6 +182,7 @@ struct Smem {
         struct {
             uint32_t base[EXPAND_TILE + 2];
             uint32_t v[EXPAND_TILE + 2];
+            uint32_t src[EXPAND_TILE + 2];
         } ex;
     } u;
 };

@@ -1,0 +1,9 @@
+// Persistent epoch-loop kernels for one program (PM_SSSP), every block size
+// and slots-per-thread setting.
+#include "trees_kernels.cuh"
+
+namespace trees {
+
+const void *persistent_kernel_sssp(int bs, int tpt) { return persistent_kernel_for<PM_SSSP>(bs, tpt); }
+
+}  // namespace trees

@@ -143,7 +143,7 @@ __device__ __forceinline__ void phase3(const Conf &c, Ctl *ctl, Smem<BS> &sm, ui
 constexpr uint32_t SOLO_TILES = 2;  // measured: 1 or 2 tiles best; 4 already slower
 template <int BS, int TPT, uint32_t PM>
 __device__ __forceinline__ bool solo_range(const Conf &c, uint32_t lo, uint32_t hi) {
-    return (PM & (PM_MS | PM_BFS)) == 0u && c.stall_epoch < 0 && hi - lo <= SOLO_TILES * (uint32_t)(BS * TPT);
+    return (PM & PM_MAPS) == 0u && c.stall_epoch < 0 && hi - lo <= SOLO_TILES * (uint32_t)(BS * TPT);
 }
 
 // Block 0's run of solo epochs, starting at epoch e with its range popped.
@@ -339,5 +339,6 @@ const void *persistent_kernel_ms(int bs, int tpt);
 const void *persistent_kernel_nq(int bs, int tpt);
 const void *persistent_kernel_bfs(int bs, int tpt);
 const void *persistent_kernel_trav(int bs, int tpt);
+const void *persistent_kernel_sssp(int bs, int tpt);
 
 }  // namespace trees

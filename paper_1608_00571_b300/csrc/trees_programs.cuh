@@ -25,14 +25,16 @@ struct Acc {
 // Program masks: which task types (and maps) a kernel is compiled for.  A
 // kernel built for one program carries only that program's dispatch cases,
 // as the paper's compiler emits one kernel per program (Sec. 5).
-constexpr uint32_t PM_FIB = 1u, PM_MS = 2u, PM_NQ = 4u, PM_BFS = 8u, PM_TRAV = 16u;
-constexpr uint32_t PM_ALL = PM_FIB | PM_MS | PM_NQ | PM_BFS | PM_TRAV;
+constexpr uint32_t PM_FIB = 1u, PM_MS = 2u, PM_NQ = 4u, PM_BFS = 8u, PM_TRAV = 16u, PM_SSSP = 32u;
+constexpr uint32_t PM_ALL = PM_FIB | PM_MS | PM_NQ | PM_BFS | PM_TRAV | PM_SSSP;
+constexpr uint32_t PM_MAPS = PM_MS | PM_BFS | PM_SSSP;  // programs that schedule map operations
 
 __host__ __device__ constexpr uint32_t program_mask(int program) {
     return program == TREES_PROG_FIB         ? PM_FIB
            : program == TREES_PROG_MERGESORT ? PM_MS
            : program == TREES_PROG_NQUEENS   ? PM_NQ
            : program == TREES_PROG_BFS       ? PM_BFS
+           : program == TREES_PROG_SSSP      ? PM_SSSP
                                              : PM_TRAV;
 }
 
@@ -151,6 +153,19 @@ __device__ __forceinline__ void plan_task(const Conf &c, const RunParams &rp, Pl
             if (re > rb) {
                 p.m = MAP_EXPAND;
                 p.a0 = (uint32_t)rb;
+                p.n = (uint32_t)(re - rb);
+            }
+            c.code[s] = 0u;
+            return;
+        }
+    }
+    if constexpr ((PM & PM_SSSP) != 0u) {
+        if (p.t == TREES_TASK_SSSP_RELAX) {  // relax(v): a map over v's out-edges (Sec. 6.3)
+            const int32_t rb = __ldg(rp.row_ptr + a0), re = __ldg(rp.row_ptr + a0 + 1);
+            if (re > rb) {
+                p.m = MAP_EXPAND;
+                p.a0 = (uint32_t)rb;
+                p.a1 = a0;
                 p.n = (uint32_t)(re - rb);
             }
             c.code[s] = 0u;
@@ -315,6 +330,7 @@ __device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan (&p)
                 c.me_v[di] = p[k].a0;
                 c.me_base[di] = b;
                 c.me_job[di] = job;
+                c.me_src[di] = p[k].a1;  // the vertex (SSSP reads its distance)
                 for (uint32_t t = (b + EXPAND_TILE - 1u) / EXPAND_TILE; t * EXPAND_TILE < b + p[k].n; ++t)
                     c.me_tfd[t] = di;
                 acc.maps++;
@@ -451,7 +467,7 @@ __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> 
         out.joined = joined != 0u;
         out.over = over0 != 0u;
     }
-    if constexpr ((PM & (PM_MS | PM_BFS)) != 0u) {
+    if constexpr ((PM & PM_MAPS) != 0u) {
         if (anymap) map_alloc<BS, TPT>(c, ctl, sm, p, cen, ep, e, 0u, acc);
     }
     return out;
@@ -1006,6 +1022,97 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
     __syncthreads();
 }
 
+// One SSSP relaxation tile (Sec. 6.3's worklist relaxation as a map): the
+// same element-balanced layout as a BFS expansion tile.  For each out-edge
+// (v, u, w) of the epoch's frontier, nd = dist[v] + w; an atomic minimum
+// shortens dist[u] if nd is smaller, and the thread whose minimum took
+// effect forks relax(u) for epoch CEN+1 unless another already did this
+// epoch (an atomic maximum on sched[u]).  dist[v] may be read after another
+// relaxation in this epoch has shortened it further; v is then forked again
+// for the next epoch, so the final distances are the shortest ones.
+template <int BS>
+__device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, uint32_t nd, uint32_t ne, uint32_t nt,
+                           uint32_t cen, uint32_t base, uint32_t ep, uint32_t e) {
+    constexpr uint32_t EPT = EXPAND_TILE / BS;
+    const uint32_t g0 = t * EXPAND_TILE, g1 = min(g0 + EXPAND_TILE, ne);
+    const uint32_t dfirst = c.me_tfd[t];
+    const uint32_t dlast = (t + 1u < nt) ? c.me_tfd[t + 1u] : nd - 1u;
+    const uint32_t nloc = dlast - dfirst + 1u;
+    for (uint32_t k = threadIdx.x; k < nloc; k += BS) {
+        sm.u.ex.base[k] = c.me_base[dfirst + k];
+        sm.u.ex.v[k] = c.me_v[dfirst + k];
+        sm.u.ex.src[k] = c.me_src[dfirst + k];
+    }
+    __syncthreads();
+    // stage 1: every element's adjacency index and source vertex (load-balanced search)
+    uint32_t ed[EPT], sv[EPT];
+#pragma unroll
+    for (uint32_t j = 0; j < EPT; ++j) {
+        const uint32_t g = g0 + j * BS + threadIdx.x;
+        ed[j] = 0xFFFFFFFFu;
+        sv[j] = 0u;
+        if (g < g1) {
+            uint32_t lo = 0, hi = nloc;
+            while (hi - lo > 1u) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (sm.u.ex.base[mid] <= g) lo = mid;
+                else hi = mid;
+            }
+            ed[j] = sm.u.ex.v[lo] + (g - sm.u.ex.base[lo]);
+            sv[j] = sm.u.ex.src[lo];
+        }
+    }
+    // stage 2: neighbours, weights and both distances in flight together
+    int32_t uu[EPT];
+    unsigned long long cand[EPT], du[EPT];
+#pragma unroll
+    for (uint32_t j = 0; j < EPT; ++j) uu[j] = ed[j] != 0xFFFFFFFFu ? __ldg(c.rp.col + ed[j]) : -1;
+#pragma unroll
+    for (uint32_t j = 0; j < EPT; ++j) {
+        cand[j] = ~0ull;
+        du[j] = 0ull;
+        if (uu[j] >= 0) {
+            cand[j] = c.rp.dist[sv[j]] + (unsigned long long)__ldg(c.rp.weight + ed[j]);
+            du[j] = c.rp.dist[uu[j]];
+        }
+    }
+    // stage 3: shorten, and fork the neighbours this thread shortened first this epoch
+    uint32_t cmask = 0u;
+#pragma unroll
+    for (uint32_t j = 0; j < EPT; ++j) {
+        if (uu[j] >= 0 && cand[j] < du[j] && cand[j] < atomicMin(c.rp.dist + uu[j], cand[j]) &&
+            atomicMax(c.rp.sched + uu[j], cen + 1u) < cen + 1u)
+            cmask |= 1u << j;
+    }
+    const uint32_t nc = (uint32_t)__popc(cmask);
+    uint32_t ftot;
+    int any;
+    const uint32_t off = block_scan_u32<BS>(nc, 0, &ftot, &any, sm);
+    if (ftot) {
+        if (threadIdx.x == 0) {
+            const uint32_t b = atomicAdd(&ctl->cnt[ep], ftot);
+            const bool over = (unsigned long long)base + b + ftot > c.cap;
+            if (over) set_err(ctl, TREES_ERR_CAPACITY, e);
+            sm.bc32[0] = b;
+            sm.bc32[1] = over;
+        }
+        __syncthreads();
+        if (!sm.bc32[1]) {
+            const uint32_t code = enc(cen + 1u, TREES_TASK_SSSP_RELAX);
+            uint32_t slot = base + sm.bc32[0] + off;
+#pragma unroll
+            for (uint32_t j = 0; j < EPT; ++j) {
+                if ((cmask >> j) & 1u) {
+                    c.code[slot] = code;
+                    c.a0[slot] = (uint32_t)uu[j];
+                    ++slot;
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
 // The map phase of epoch e, after the partition sub-phase: leaf sorts one
 // warp per leaf, merge tiles one block per tile, then the expansion tiles.
 template <int BS, uint32_t PM>
@@ -1031,9 +1138,12 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
         merge_phase<BS>(c, ctl, sm, nt1, nd1, job_params, job_stride);
       }
     }
-    if constexpr ((PM & PM_BFS) != 0u) {
-        for (uint32_t t = blockIdx.x; t < nt2; t += gridDim.x)
-            expand_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e);
+    if constexpr ((PM & (PM_BFS | PM_SSSP)) != 0u) {
+        const bool sssp = (PM & PM_BFS) == 0u || ((PM & PM_SSSP) != 0u && c.rp.program == TREES_PROG_SSSP);
+        for (uint32_t t = blockIdx.x; t < nt2; t += gridDim.x) {
+            if (sssp) relax_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e);
+            else expand_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e);
+        }
     }
 }
 
