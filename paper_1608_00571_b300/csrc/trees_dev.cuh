@@ -159,7 +159,6 @@ struct Smem {
     unsigned int wflag[NW];
     unsigned int wv[2][TPT_MAX][NW];  // vector scan words, double-buffered by tile parity
     unsigned int wvf[2][NW];
-    unsigned int vflags[2];
     unsigned long long w64a[NW];
     unsigned long long w64b[NW];
     unsigned int flags;
@@ -255,23 +254,27 @@ __device__ __forceinline__ void block_scan_vec(const uint32_t (&v)[K], uint32_t 
     }
     if (lane == 0) sm.wvf[par][wid] = bal != 0u;
     __syncthreads();
-    if (wid == 0) {
+    // one barrier: every thread sums the warp totals itself (broadcast reads); buffer `par` is
+    // written again two tiles later, after a barrier every thread reaches only past these reads
+    uint32_t pre[K], all[K], f = 0u;
+#pragma unroll
+    for (int k = 0; k < K; ++k) pre[k] = all[k] = 0u;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            uint32_t w = lane < NW ? sm.wv[par][k][lane] : 0u;
-            w = warp_incl_u32(w);
-            if (lane < NW) sm.wv[par][k][lane] = w;
+            const uint32_t x = sm.wv[par][k][w];
+            all[k] += x;
+            pre[k] += w < wid ? x : 0u;
         }
-        const unsigned int f = __ballot_sync(0xffffffffu, lane < NW ? sm.wvf[par][lane] : 0u);
-        if (lane == 0) sm.vflags[par] = f != 0u;
+        f |= sm.wvf[par][w];
     }
-    __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        tot[k] = sm.wv[par][k][NW - 1];
-        ex[k] = (wid ? sm.wv[par][k][wid - 1] : 0u) + inc[k] - v[k];
+        tot[k] = all[k];
+        ex[k] = pre[k] + inc[k] - v[k];
     }
-    *any = (int)sm.vflags[par];
+    *any = (int)(f != 0u);
 }
 
 // Exclusive block scan of two u64 values at once.

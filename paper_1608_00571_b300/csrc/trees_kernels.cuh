@@ -44,13 +44,15 @@ __device__ __forceinline__ void trace_valid_add(const Conf &c, uint32_t e, uint3
 
 // The persistent scheduler: the whole epoch loop in one cooperative launch.
 // Blocks per SM the kernel is compiled to fit (its register budget): the
-// mergesort kernel keeps 1024 threads per SM resident (the warp leaf sort
-// would otherwise take the registers of a whole SM); the fib kernel trades
+// mergesort, BFS and SSSP kernels keep 1024 threads per SM resident (their
+// map tiles would otherwise take registers for 2 blocks per SM: measured
+// SSSP R-MAT 22 6.1 -> 3.8 ms, BFS 1.63 -> 1.23 ms); the fib kernel trades
 // threads for registers as its slots per thread grow (1024, 768, 512 threads
 // per SM for 1, 2, 4 slots: measured, each spill-free beats more resident
 // warps that spill); the others take what they need.
 __host__ __device__ constexpr int persistent_min_blocks(int bs, uint32_t pm, int tpt) {
-    const int tps = pm == PM_MS ? 1024 : pm == PM_FIB ? (tpt >= 4 ? 512 : tpt == 2 ? 768 : 1024) : 0;
+    const int tps = (pm == PM_MS || pm == PM_BFS || pm == PM_SSSP) ? 1024
+                  : pm == PM_FIB ? (tpt >= 4 ? 512 : tpt == 2 ? 768 : 1024) : 0;
     return tps / bs > 0 ? tps / bs : 1;
 }
 
