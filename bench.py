@@ -655,8 +655,8 @@ def main():
         t5 = timed_runs(T, torch, c5, j5, 5, 1, stream, flush)
         s5 = T.trees_stats(c5)
         T.trees_destroy(c5)
-        dist = dist_t.cpu().numpy().view(np.uint64)
-        ok5 = sssp_certificate(row_ptr, col, weight, 0, dist, level)
+        sssp_dist = dist_t.cpu().numpy().view(np.uint64)
+        ok5 = sssp_certificate(row_ptr, col, weight, 0, sssp_dist, level)
         m5 = statistics.mean(t5)
         ab5, edges5 = sssp_alg_bytes(row_ptr, level >= 0, s5["tasks"])
         workloads["sssp_rmat22"] = {"ms": m5, "tasks": s5["tasks"], "epochs": s5["epochs"],
