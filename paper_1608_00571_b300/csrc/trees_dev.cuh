@@ -36,6 +36,7 @@ __host__ __device__ constexpr uint32_t merge_stage(int bs) { return merge_tile(b
 // next streams in.
 __host__ __device__ constexpr int merge_nst(int) { return 2; }
 constexpr uint32_t EXPAND_TILE = 2048;          // adjacency entries of one BFS expansion tile
+constexpr uint32_t JR_SLOTS = 1024;             // tile slots whose join operands can be prefetched
 constexpr int MCHUNK = 64;                      // merge tiles a block resolves at once
 constexpr unsigned long long CTR_LOW_MASK = (1ull << 40) - 1;  // map counters: (descs << 40) | units
 
@@ -183,6 +184,7 @@ struct Smem {
             uint32_t v[EXPAND_TILE + 2];
             uint32_t src[EXPAND_TILE + 2];
         } ex;
+        unsigned long long jr[2][JR_SLOTS][2];  // fib joins: the next tile's children's results, prefetched
     } u;
 };
 
@@ -391,6 +393,15 @@ __device__ __forceinline__ void tma_load_1d(void *dst_smem, const void *src, uin
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
+
+// 8-byte asynchronous copy global -> shared (no register holds the data);
+// this thread's copies since the last commit form one group.
+__device__ __forceinline__ void cp_async_8(void *dst_smem, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// This thread's committed copies have landed.
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -278,10 +278,14 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
         unsigned long long t0 = (unsigned long long)lo + (unsigned long long)blockIdx.x * (BS * TPT);
         TileLoad<TPT> cur, nxt;
         if (t0 < hi) tile_load<BS, TPT, PM>(c, t0, hi, mode, cur);
+        const bool jr = mode == LOAD_JOIN;  // fib: prefetch the successor tile's join operands
+        bool jr_use = false;
         for (; t0 < hi; t0 += step) {
             const bool more = t0 + step < hi;
             if (more) tile_load<BS, TPT, PM>(c, t0 + step, hi, mode, nxt);
-            epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode, cur, solo, 0u);
+            epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode, cur, solo, 0u, jr_use,
+                                    jr && more ? &nxt : nullptr);
+            jr_use = jr && more;
             if (more) cur = nxt;
             par ^= 1;
         }

@@ -388,10 +388,22 @@ struct TileOut {
     bool over;
 };
 
+// Join-operand prefetch for fib (Sec. 4.1's continuation reads its children's
+// results through `link`): while a join tile runs, the results its successor
+// tile's sums will read are copied into shared memory asynchronously, so the
+// successor's sums need no dependent round trip.  jr_use: this tile's
+// operands were prefetched into jr[par]; pf: the successor tile's columns
+// (its operands go to jr[par ^ 1]), or null.
+template <int BS, int TPT, uint32_t PM>
+__device__ __forceinline__ constexpr bool join_prefetch() {
+    return (PM & PM_FIB) != 0u && BS * TPT <= (int)JR_SLOTS;
+}
+
 template <int BS, int TPT, uint32_t PM>
 __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, unsigned long long t0, uint32_t hi,
                                            uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, Acc &acc, int par,
-                                           int mode, const TileLoad<TPT> &L, bool known, uint32_t known_off) {
+                                           int mode, const TileLoad<TPT> &L, bool known, uint32_t known_off,
+                                           bool jr_use = false, const TileLoad<TPT> *pf = nullptr) {
     constexpr bool fresh_a1 = (PM & (PM_MS | PM_NQ)) != 0u;
     constexpr bool join_a0 = (PM & (PM_MS | PM_NQ | PM_TRAV)) != 0u;
     constexpr bool join_link = (PM & (PM_FIB | PM_NQ)) != 0u;
@@ -414,14 +426,39 @@ __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> 
     }
     uint32_t nf[TPT];
     int hasmap = 0;
+    if constexpr (join_prefetch<BS, TPT, PM>()) {
+        if (jr_use) cp_async_wait_all();  // this thread's operands for this tile have landed
+    }
 #pragma unroll
     for (int k = 0; k < TPT; ++k) {
         if (p[k].t) {
             acc.valid++;
-            plan_task<PM, merge_tile(BS)>(c, c.rp, p[k], cen, e, a0v[k], a1v[k], lkv[k]);
+            bool done = false;
+            if constexpr (join_prefetch<BS, TPT, PM>()) {
+                if (jr_use && p[k].t == TREES_TASK_FIB_SUM) {
+                    const unsigned long long *r = sm.u.jr[par][k * BS + threadIdx.x];
+                    c.result[p[k].s] = r[0] + r[1];
+                    c.code[p[k].s] = 0u;
+                    done = true;
+                }
+            }
+            if (!done) plan_task<PM, merge_tile(BS)>(c, c.rp, p[k], cen, e, a0v[k], a1v[k], lkv[k]);
         }
         nf[k] = forks_of(p[k]);
         hasmap |= p[k].m != 0u;
+    }
+    if constexpr (join_prefetch<BS, TPT, PM>()) {
+        if (pf) {  // the successor tile's sums: copy their operands now (its links have arrived by now)
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                if (task_type(pf->cd[k], cen) == TREES_TASK_FIB_SUM) {
+                    unsigned long long *r = sm.u.jr[par ^ 1][k * BS + threadIdx.x];
+                    cp_async_8(r, c.result + pf->lk[k]);
+                    cp_async_8(r + 1, c.result + pf->lk[k] + 1);
+                }
+            }
+            cp_async_commit();
+        }
     }
     uint32_t ex[TPT], tot[TPT];
     int anymap;
