@@ -47,7 +47,7 @@ def parse_args():
                     help="JSON file for the autotuner's choices (default: tune afresh every run)")
     ap.add_argument("--profile-case", default=None,
                     help="PROGRAM:SIZE[:BLOCK[:SLOTS_PER_THREAD[:SCHEDULER]]] -- run one small case twice and exit "
-                         "(for ncu): fib:N, sort:LOG2KEYS, bfs:RMAT_SCALE")
+                         "(for ncu): fib:N, sort:LOG2KEYS, bfs:RMAT_SCALE, sssp:RMAT_SCALE")
     return ap.parse_args()
 
 
@@ -87,6 +87,18 @@ def profile_case(spec):
         ctx = T.trees_create(row_ptr.size + 1024,
                              T.trees_default_config(block_size=bs, tasks_per_thread=tpt, scheduler=sched))
         job = T.make_job(T.TREES_PROG_BFS, n=0, row_ptr=rp, col=cl, level=lv, nv=row_ptr.size - 1)
+    elif prog == "sssp":
+        row_ptr, col, _ = gen.rmat(size, 16, seed=2)
+        w = gen.weights(3, row_ptr, col)
+        nv = row_ptr.size - 1
+        rp, cl = torch.from_numpy(row_ptr).cuda(), torch.from_numpy(col).cuda()
+        wt = torch.from_numpy(w.view(np.int32)).cuda()
+        dist = torch.empty(nv, dtype=torch.int64, device="cuda")
+        sched_t = torch.empty(nv, dtype=torch.int32, device="cuda")
+        keep += [rp, cl, wt, dist, sched_t]
+        ctx = T.trees_create(3 * nv + 1024,
+                             T.trees_default_config(block_size=bs, tasks_per_thread=tpt, scheduler=sched))
+        job = T.make_job(T.TREES_PROG_SSSP, n=0, row_ptr=rp, col=cl, weight=wt, nv=nv, dist=dist, sched=sched_t)
     else:
         raise SystemExit(f"unknown profile case {spec}")
     for _ in range(2):
