@@ -344,6 +344,8 @@ struct trees_ctx {
     std::map<const void *, int> grid_cache;
     uint32_t *own_scratch = nullptr;
     size_t own_scratch_n = 0;
+    uint32_t *own_smp = nullptr;  // mergesort splitter samples (n/64 + 1 keys)
+    size_t own_smp_n = 0;
     // graph scheduler
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -540,6 +542,7 @@ void trees_destroy(trees_ctx *x) {
     if (x->gexec) cudaGraphExecDestroy(x->gexec);
     if (x->graph) cudaGraphDestroy(x->graph);
     if (x->own_scratch) cudaFree(x->own_scratch);
+    if (x->own_smp) cudaFree(x->own_smp);
     if (x->pinned_ctl) cudaFreeHost(x->pinned_ctl);
     if (x->d_jobs) cudaFree(x->d_jobs);
     if (x->d_joff) cudaFree(x->d_joff);
@@ -732,6 +735,7 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     RunParams &rp = x->conf.rp;
     std::memset(&rp, 0, sizeof(rp));
+    x->conf.smp = nullptr;
     rp.program = job->program;
     rp.n = job->n;
     rp.cutoff = job->cutoff;
@@ -760,6 +764,17 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
                 x->own_scratch_n = job->n;
             }
             rp.scratch = x->own_scratch;
+        }
+        if (job->n >= (1u << 16)) {  // splitter samples for the partition searches of long runs
+            const size_t ns = ((size_t)job->n >> SMP_SHIFT) + 1;
+            if (x->own_smp_n < ns) {
+                if (x->own_smp) cudaFree(x->own_smp);
+                x->own_smp = nullptr;
+                x->own_smp_n = 0;
+                if (cudaMalloc(&x->own_smp, ns * 4) != cudaSuccess) return TREES_ERR_CUDA;
+                x->own_smp_n = ns;
+            }
+            x->conf.smp = x->own_smp;
         }
         type = TREES_TASK_MS_SPLIT;
         a0 = 0;

@@ -37,6 +37,7 @@ __host__ __device__ constexpr uint32_t merge_stage(int bs) { return merge_tile(b
 __host__ __device__ constexpr int merge_nst(int) { return 2; }
 constexpr uint32_t EXPAND_TILE = 2048;          // adjacency entries of one BFS expansion tile
 constexpr uint32_t JR_SLOTS = 1024;             // tile slots whose join operands can be prefetched
+constexpr uint32_t SMP_SHIFT = 6;               // mergesort splitter samples: every 64th key of a run
 constexpr int MCHUNK = 64;                      // merge tiles a block resolves at once
 constexpr unsigned long long CTR_LOW_MASK = (1ull << 40) - 1;  // map counters: (descs << 40) | units
 
@@ -85,6 +86,9 @@ struct Conf {
     unsigned long long timeout_ns;
     Range *gstack;
     uint32_t gstack_cap;
+    // single-job mergesort: smp[p >> SMP_SHIFT] = the key at position p (p a multiple of 64) of the
+    // runs the last map phase wrote, for the next partition's searches; null otherwise
+    uint32_t *smp;
     RunParams rp;
 };
 

@@ -518,7 +518,8 @@ __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> 
 // bitonic network in registers, then five bitonic merge levels join runs of
 // 32, 64, ..., 512 keys across lanes (a flip stage pairing rank p with
 // 2R-1-p, then half-cleaners), so no block barrier is needed.
-__device__ __forceinline__ void warp_leaf_sort(const uint32_t *in, uint32_t *out, uint32_t lo, uint32_t hi) {
+__device__ __forceinline__ void warp_leaf_sort(const uint32_t *in, uint32_t *out, uint32_t lo, uint32_t hi,
+                                               uint32_t *smp) {
     const uint32_t lane = threadIdx.x & 31u, n = hi - lo;
     uint32_t x[32];
 #pragma unroll
@@ -593,6 +594,12 @@ __device__ __forceinline__ void warp_leaf_sort(const uint32_t *in, uint32_t *out
             if (i < n) out[lo + i] = x[r];
         }
     }
+    if (smp) {  // keys at positions that are multiples of 64 become samples, read back after the stores
+        __syncwarp();
+        const uint32_t first = (lo + 63u) & ~63u;  // at most 16 sample positions in a leaf
+        const uint32_t p = first + 64u * lane;
+        if (lane < 16u && p < hi) smp[p >> SMP_SHIFT] = out[p];
+    }
 }
 
 // The sorted runs a merge at depth d reads (depth d+1) and writes (depth d):
@@ -635,6 +642,55 @@ __device__ __forceinline__ uint32_t tile_owner(const Conf &c, uint32_t t, uint32
     return lo;
 }
 
+// Narrows a merge-path search with the splitter samples of the runs (every
+// 64th key, in L2): for the merge of A = in[a, mid) and B = in[mid, b) at
+// diagonal d, whose split s (A keys among the first d outputs, A winning
+// ties) lies in [*lo, *hi].  At a sampled A index i (a + i a multiple of 64)
+// the merge-path test A[i] <= B[d-1-i] is certainly true when A[i] is at most
+// the sample at or below B's position, and certainly false when A[i] exceeds
+// the sample above it (both runs are sorted).  Certain-true holds on a prefix
+// of the sampled indices and certain-false on a suffix, so two searches over
+// the samples give s > (last certain-true i) and s <= (first certain-false
+// i).  The group's G lanes probe G samples per step for each search.
+template <uint32_t G>
+__device__ __forceinline__ void sample_bracket(const uint32_t *smp, uint32_t a, uint32_t mid, uint32_t b, uint32_t d,
+                                               uint32_t *lo, uint32_t *hi, uint32_t gmask, uint32_t glane) {
+    const uint32_t ilo = *lo, ihi = *hi;
+    if (ihi - ilo < 256u) return;  // a short search needs no help
+    // sampled candidates: global A positions 64 k in [a + ilo, a + ihi)
+    const uint32_t ka = (a + ilo + 63u) >> SMP_SHIFT, kb = (a + ihi + 63u) >> SMP_SHIFT;
+    auto sure_true = [&](uint32_t k) {  // A[i] <= B[q] known from the sample at or below q
+        const uint32_t i = (k << SMP_SHIFT) - a, q = mid + d - 1u - i;
+        return (q & ~63u) >= mid && smp[k] <= smp[q >> SMP_SHIFT];
+    };
+    auto sure_false = [&](uint32_t k) {  // A[i] > B[q] known from the sample above q
+        const uint32_t i = (k << SMP_SHIFT) - a, q = mid + d - 1u - i;
+        return (q | 63u) + 1u < b && smp[k] > smp[(q >> SMP_SHIFT) + 1u];
+    };
+    // first candidate that is not sure-true, first that is sure-false (kb when none)
+    uint32_t tl = ka, th = kb, fl = ka, fh = kb;
+    while (th > tl || fh > fl) {
+        const uint32_t ts = (th - tl + G - 1u) / G, fs = (fh - fl + G - 1u) / G;
+        const uint32_t tm = tl + glane * ts, fm = fl + glane * fs;
+        const bool pt = th > tl && tm < th && sure_true(tm);
+        const bool pf = fh > fl && fm < fh && !sure_false(fm);
+        const uint32_t ct = (uint32_t)__popc(__ballot_sync(gmask, pt) & gmask);
+        const uint32_t cf = (uint32_t)__popc(__ballot_sync(gmask, pf) & gmask);
+        if (th > tl) {
+            const uint32_t nl = ct ? tl + (ct - 1u) * ts + 1u : tl, cap = tl + ct * ts;
+            th = cap < th ? cap : th;
+            tl = nl;
+        }
+        if (fh > fl) {
+            const uint32_t nl = cf ? fl + (cf - 1u) * fs + 1u : fl, cap = fl + cf * fs;
+            fh = cap < fh ? cap : fh;
+            fl = nl;
+        }
+    }
+    if (tl > ka) *lo = max(*lo, ((tl - 1u) << SMP_SHIFT) - a + 1u);
+    if (fl < kb) *hi = min(*hi, (fl << SMP_SHIFT) - a);
+}
+
 // Partition sub-phase of a map epoch: the merge-path split at the first
 // output of every merge tile that does not start its merge, computed in
 // parallel by groups of 4 lanes for all tiles at once.  A group runs the
@@ -675,6 +731,7 @@ __device__ void partition_phase(const Conf &c, unsigned long long mt, const RunP
             diag[q] = d;
             lo[q] = d > lb ? d - lb : 0u;
             hi[q] = d < la ? d : la;
+            if (!job_params && c.smp) sample_bracket<G>(c.smp, a, mid, b, d, &lo[q], &hi[q], gmask, glane);
         }
         // merge path (Odeh et al., "Merge Path -- parallel merging made simple", IPDPSW 2012):
         // the split is the number of A keys among the first diag outputs, A winning ties; G probes
@@ -852,7 +909,8 @@ __device__ __forceinline__ void merge_compute(const MergeTile &m, const uint32_t
 // output with one bulk copy; without 16-byte alignment the block copies it
 // out with coalesced stores instead.
 template <int BS, uint32_t MPT>
-__device__ __forceinline__ void merge_write(const MergeTile &m, uint32_t *buf, const uint32_t (&v)[MPT], uint32_t dd) {
+__device__ __forceinline__ void merge_write(const MergeTile &m, uint32_t *buf, const uint32_t (&v)[MPT], uint32_t dd,
+                                            uint32_t *smp) {
     const uint32_t nt = (m.i1 - m.i0) + (m.j1 - m.j0);
 #pragma unroll
     for (uint32_t k = 0; k < MPT; ++k)
@@ -861,6 +919,11 @@ __device__ __forceinline__ void merge_write(const MergeTile &m, uint32_t *buf, c
     const bool bulk = ((reinterpret_cast<uintptr_t>(o) & 15u) == 0u) && (nt & 3u) == 0u;
     if (bulk) fence_proxy_async_smem();  // these generic writes come before the bulk copy's reads
     __syncthreads();
+    if (smp && threadIdx.x < 32u) {  // warp 0 copies the tile's samples (outputs at multiples of 64)
+        const uint32_t p0 = m.lo + m.d0, first = ((p0 + 63u) & ~63u) - p0;
+        for (uint32_t i = first + 64u * threadIdx.x; i < nt; i += 64u * 32u) smp[(p0 + i) >> SMP_SHIFT] = buf[i];
+        __syncwarp();  // these reads of buf come before thread 0 (this warp) stages into it again
+    }
     if (bulk) {
         if (threadIdx.x == 0 && nt) tma_store_1d(o, buf, nt * 4u);
     } else {
@@ -872,13 +935,13 @@ __device__ __forceinline__ void merge_write(const MergeTile &m, uint32_t *buf, c
 // One staged tile, start to end, with MPT outputs per thread; false (and
 // nothing written) when the tile's copy did not land on some thread.
 template <int BS, uint32_t MPT>
-__device__ __forceinline__ bool merge_run(const MergeTile &m, uint32_t *buf, bool landed) {
+__device__ __forceinline__ bool merge_run(const MergeTile &m, uint32_t *buf, bool landed, uint32_t *smp) {
     uint32_t v[MPT], dd;
     merge_compute<BS, MPT>(m, buf, v, dd);
     // every thread has read buf and the tails staged for later tiles are visible; a wait that ran
     // out anywhere in the block is seen by every thread here, so all leave together
     if (__syncthreads_or(!landed)) return false;
-    merge_write<BS, MPT>(m, buf, v, dd);
+    merge_write<BS, MPT>(m, buf, v, dd, smp);
     return true;
 }
 
@@ -965,8 +1028,8 @@ __device__ void merge_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t nt1,
             get_merge_tile(sm.mtab[k], cur);
             const uint32_t nt = (cur.i1 - cur.i0) + (cur.j1 - cur.j0);
             const bool ok = nt <= (uint32_t)BS * merge_mpt_small(BS)
-                                ? merge_run<BS, merge_mpt_small(BS)>(cur, sm.u.mg[b], landed)
-                                : merge_run<BS, merge_mpt(BS)>(cur, sm.u.mg[b], landed);
+                                ? merge_run<BS, merge_mpt_small(BS)>(cur, sm.u.mg[b], landed, jp ? nullptr : c.smp)
+                                : merge_run<BS, merge_mpt(BS)>(cur, sm.u.mg[b], landed, jp ? nullptr : c.smp);
             ++gc;
             if (!ok) {
                 if (threadIdx.x == 0) set_err(ctl, TREES_ERR_TIMEOUT, 0x80000000u | (c0 + (uint32_t)k * gridDim.x));
@@ -1169,7 +1232,7 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
             if (c.mt_kind[di] != MAP_LEAF_SORT) continue;
             job_buffers(c, job_params, job_stride, c.mt_job[di], &keys, &scratch);
             const uint32_t cc = c.mt_c[di];
-            warp_leaf_sort(keys, (cc & 1u) ? scratch : keys, c.mt_a[di], c.mt_b[di]);
+            warp_leaf_sort(keys, (cc & 1u) ? scratch : keys, c.mt_a[di], c.mt_b[di], job_params ? nullptr : c.smp);
         }
         // merge tiles: one block each, pipelined
         merge_phase<BS>(c, ctl, sm, nt1, nd1, job_params, job_stride);
