@@ -21,7 +21,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
-FIB, MERGESORT, BFS, NQUEENS, POSTORDER, PREORDER = 0, 1, 2, 3, 4, 5
+FIB, MERGESORT, BFS, NQUEENS, POSTORDER, PREORDER, FFT = 0, 1, 2, 3, 4, 5, 6
 
 
 def build(force: bool = False) -> str:
@@ -30,7 +30,7 @@ def build(force: bool = False) -> str:
         fcntl.flock(lf, fcntl.LOCK_EX)
         if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
             tmp = _SO + ".tmp"
-            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", _SRC, "-o", tmp])
+            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
             os.replace(tmp, _SO)
     return _SO
 
@@ -47,7 +47,9 @@ class _Params(ctypes.Structure):
                 ("nv", ctypes.c_int32), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
                 ("level", ctypes.c_void_p), ("src", ctypes.c_int32), ("nq_n", ctypes.c_int32),
                 ("nnodes", ctypes.c_int32), ("left", ctypes.c_void_p), ("right", ctypes.c_void_p),
-                ("visit_epoch", ctypes.c_void_p), ("max_epochs", ctypes.c_uint64)]
+                ("visit_epoch", ctypes.c_void_p), ("max_epochs", ctypes.c_uint64),
+                ("fft_n", ctypes.c_int64), ("fft_leaf", ctypes.c_int64), ("fft_cutoff", ctypes.c_int64),
+                ("fft_x", ctypes.c_void_p), ("fft_X", ctypes.c_void_p)]
 
 
 class _Stats(ctypes.Structure):
@@ -76,6 +78,8 @@ def _bind(lib):
                                          ctypes.c_int32, ctypes.c_void_p, u64p, u64p]
     lib.oracle_nqueens.restype = ctypes.c_uint64
     lib.oracle_nqueens.argtypes = [ctypes.c_int, u64p, u64p]
+    lib.oracle_dft.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    lib.oracle_dft_at.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
     lib.oracle_tvm_run.restype = ctypes.c_int
     lib.oracle_tvm_run.argtypes = [ctypes.POINTER(_Params), ctypes.POINTER(Epoch), ctypes.c_uint64,
                                    ctypes.POINTER(_Stats)]
@@ -171,17 +175,45 @@ def nqueens(n: int):
     return int(v), int(r.value), int(j.value)
 
 
+def _complex_in(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+
+
+def dft(x) -> np.ndarray:
+    """The discrete Fourier transform by its definition, O(n^2), fp64:
+    ``X[k] = sum_j x[j] exp(-2 pi i j k / n)``."""
+    x = _complex_in(x)
+    X = np.empty_like(x)
+    if x.size:
+        _load().oracle_dft(x.shape[0], x.ctypes.data, X.ctypes.data)
+    return X
+
+
+def dft_at(x, ks) -> np.ndarray:
+    """Outputs ``X[k]`` of the definition for the indices ``ks`` only, O(n) each."""
+    x = _complex_in(x)
+    ks = np.asarray(ks, dtype=np.int64).reshape(-1)
+    out = np.empty(ks.shape[0], dtype=np.complex128)
+    buf = np.empty(2, dtype=np.float64)
+    for i, k in enumerate(ks):
+        _load().oracle_dft_at(x.shape[0], x.ctypes.data, int(k), buf.ctypes.data)
+        out[i] = complex(buf[0], buf[1])
+    return out
+
+
 # ------------------------------------------------------------ TVM simulator
 
 def tvm_run(program: int, *, fib_n: int = 0, fib_cutoff: int = 0, keys: np.ndarray | None = None,
             leaf: int = 1024, row_ptr=None, col=None, src: int = 0, nq_n: int = 0, left=None, right=None,
-            max_epochs: int = 1 << 20, trace_cap: int = 1 << 16):
+            x=None, fft_leaf: int = 16, fft_cutoff: int = 0, max_epochs: int = 1 << 20,
+            trace_cap: int = 1 << 16):
     """Runs one program on the sequential TVM simulator.
 
     Returns a dict with ``stats`` (epochs, tasks, forks, joins, maps,
     peak_slots, root_result), ``trace`` (structured array, one row per epoch:
     cen, lo, hi, valid, forks, joined, maps) and the program's output
-    (``keys`` sorted in place on a copy, ``level`` or ``visit_epoch``).
+    (``keys`` sorted in place on a copy, ``level``, ``visit_epoch``, or the
+    FFT's output ``X`` as complex128).
     """
     lib = _load()
     p = _Params()
@@ -221,6 +253,16 @@ def tvm_run(program: int, *, fib_n: int = 0, fib_cutoff: int = 0, keys: np.ndarr
         p.right = rt.ctypes.data if rt.size else None
         p.visit_epoch = ve.ctypes.data if ve.size else None
         out["visit_epoch"] = ve
+    if program == FFT:
+        xi = _complex_in(x)
+        Xo = np.zeros_like(xi)
+        keep += [xi, Xo]
+        p.fft_n = xi.shape[0]
+        p.fft_leaf = fft_leaf
+        p.fft_cutoff = fft_cutoff
+        p.fft_x = xi.ctypes.data
+        p.fft_X = Xo.ctypes.data
+        out["X"] = Xo
     trace = (Epoch * trace_cap)()
     st = _Stats()
     rc = lib.oracle_tvm_run(ctypes.byref(p), trace, trace_cap, ctypes.byref(st))

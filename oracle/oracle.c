@@ -9,8 +9,9 @@
  *
  * Two parts:
  *  1. Plain definitions of what each task program computes (the method
- *     reaches these exactly): recursive Fibonacci with call counts, top-down
- *     mergesort, FIFO-queue BFS, backtracking N-Queens.
+ *     reaches these exactly, or up to rounding for the FFT): recursive
+ *     Fibonacci with call counts, top-down mergesort, FIFO-queue BFS,
+ *     backtracking N-Queens, Dijkstra, the discrete Fourier transform.
  *  2. A sequential Task Vector Machine simulator that runs the same programs
  *     as fork/join/emit/map tasks, one epoch at a time, in the order the paper
  *     gives: Phase 1 pops the epoch number and NDRange (Sec. 4.3.1, 5.2.2),
@@ -27,6 +28,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <math.h>
 
 /* ================================================================ part 1 */
 
@@ -255,18 +257,41 @@ uint64_t oracle_nqueens(int n, uint64_t *row_tasks, uint64_t *join_tasks) {
     return v;
 }
 
+/* The discrete Fourier transform by its definition (the FFT of Sec. 6.2
+ * computes it):  X[k] = sum_{j<n} x[j] * exp(-2*pi*i*j*k/n),  k < n,
+ * complex numbers stored as interleaved (re, im) doubles.  The angle is taken
+ * from (j*k mod n), which keeps it in [0, 2*pi) without changing its value.
+ * O(n^2); any n >= 1 (not only powers of two). */
+static void dft_term(int64_t n, const double *x, int64_t j, int64_t k, double *re, double *im) {
+    const double ang = -2.0 * M_PI * (double)((j * k) % n) / (double)n;
+    const double c = cos(ang), sn = sin(ang);
+    *re += x[2 * j] * c - x[2 * j + 1] * sn;
+    *im += x[2 * j] * sn + x[2 * j + 1] * c;
+}
+
+void oracle_dft_at(int64_t n, const double *x, int64_t k, double *out) {
+    double re = 0.0, im = 0.0;
+    for (int64_t j = 0; j < n; j++) dft_term(n, x, j, k, &re, &im);
+    out[0] = re;
+    out[1] = im;
+}
+
+void oracle_dft(int64_t n, const double *x, double *X) {
+    for (int64_t k = 0; k < n; k++) oracle_dft_at(n, x, k, X + 2 * k);
+}
+
 /* ================================================================ part 2 */
 
 enum {
     T_FIB = 1, T_FIB_SUM, T_MS_SPLIT, T_MS_MERGE, T_NQ_ROW, T_NQ_SUM,
-    T_BFS_VISIT, T_PO, T_PO_AFTER, T_PRE,
-    NUM_TASK_TYPES = T_PRE
+    T_BFS_VISIT, T_PO, T_PO_AFTER, T_PRE, T_FFT, T_FFT_COMBINE,
+    NUM_TASK_TYPES = T_FFT_COMBINE
 };
 
 enum { ORACLE_FIB = 0, ORACLE_MERGESORT = 1, ORACLE_BFS = 2, ORACLE_NQUEENS = 3,
-       ORACLE_POSTORDER = 4, ORACLE_PREORDER = 5 };
+       ORACLE_POSTORDER = 4, ORACLE_PREORDER = 5, ORACLE_FFT = 6 };
 
-enum { MAP_LEAF_SORT = 1, MAP_MERGE = 2 };
+enum { MAP_LEAF_SORT = 1, MAP_MERGE = 2, MAP_FFT_COMBINE = 3 };
 
 typedef struct {
     uint32_t cen, lo, hi;   /* epoch number and NDRange [lo, hi) */
@@ -284,6 +309,10 @@ typedef struct {
     int32_t nq_n;
     int32_t nnodes; const int32_t *left; const int32_t *right; int32_t *visit_epoch;
     uint64_t max_epochs;
+    /* FFT: n points (a power of two), leaf size, largest combine run inside its
+     * task (larger ones are maps), input and output as interleaved (re, im) */
+    int64_t fft_n, fft_leaf, fft_cutoff;
+    const double *fft_x; double *fft_X;
 } oracle_tvm_params;
 
 typedef struct {
@@ -382,6 +411,54 @@ static void prim_map(tvm *m, int kind, int64_t a, int64_t b, int64_t c) {
     m->n_maps++;
 }
 
+/* --- the FFT program (Sec. 6.2): radix-2 Cooley-Tukey by decimation in time.
+ * Task FFT(o, d) transforms the N >> d points x[o], x[o + 2^d], x[o + 2*2^d],
+ * ... (the points whose index is o modulo 2^d).  It forks FFT(o, d+1) (the
+ * even-numbered of its points) and FFT(o + 2^d, d+1) (the odd-numbered) and
+ * joins into COMBINE(o, d), which merges their two half-size transforms into
+ * its own.  The transform of the even half occupies the first half of the
+ * parent's output block and the odd half the second, so the block of FFT(o, d)
+ * starts at the sum, over the bits b < d set in o, of N >> (b + 1). */
+static int64_t fft_block(uint32_t o, uint32_t d, int64_t N) {
+    int64_t pos = 0;
+    for (uint32_t b = 0; b < d; b++)
+        if ((o >> b) & 1u) pos += N >> (b + 1);
+    return pos;
+}
+
+/* A leaf: the n-point DFT of its points by the definition, into its block. */
+static void fft_leaf(const oracle_tvm_params *p, uint32_t o, uint32_t d, int64_t n) {
+    const int64_t dst = fft_block(o, d, p->fft_n);
+    for (int64_t k = 0; k < n; k++) {
+        double re = 0.0, im = 0.0;
+        for (int64_t j = 0; j < n; j++) {
+            const int64_t src = (int64_t)o + (j << d);
+            const double ang = -2.0 * M_PI * (double)((j * k) % n) / (double)n;
+            re += p->fft_x[2 * src] * cos(ang) - p->fft_x[2 * src + 1] * sin(ang);
+            im += p->fft_x[2 * src] * sin(ang) + p->fft_x[2 * src + 1] * cos(ang);
+        }
+        p->fft_X[2 * (dst + k)] = re;
+        p->fft_X[2 * (dst + k) + 1] = im;
+    }
+}
+
+/* The combine of a block of n points at X[dst..dst+n): its first half holds
+ * E, the transform of the even points, its second half O, that of the odd
+ * points; with w = exp(-2*pi*i*k/n), X[k] = E[k] + w O[k] and
+ * X[k + n/2] = E[k] - w O[k] for k < n/2. */
+static void fft_combine(double *X, int64_t dst, int64_t n) {
+    for (int64_t k = 0; k < n / 2; k++) {
+        const double ang = -2.0 * M_PI * (double)k / (double)n, wr = cos(ang), wi = sin(ang);
+        double *e = X + 2 * (dst + k), *od = X + 2 * (dst + k + n / 2);
+        const double tr = wr * od[0] - wi * od[1], ti = wr * od[1] + wi * od[0];
+        const double er = e[0], ei = e[1];
+        e[0] = er + tr;
+        e[1] = ei + ti;
+        od[0] = er - tr;
+        od[1] = ei - ti;
+    }
+}
+
 static void run_map(tvm *m, const map_op *op) {
     uint32_t *k = m->p->keys;
     if (op->kind == MAP_LEAF_SORT) {
@@ -397,6 +474,8 @@ static void run_map(tvm *m, const map_op *op) {
         while (i < op->b) m->tmp[o++] = k[i++];
         while (j < op->c) m->tmp[o++] = k[j++];
         memcpy(k + op->a, m->tmp + op->a, sizeof(uint32_t) * (size_t)(op->c - op->a));
+    } else if (op->kind == MAP_FFT_COMBINE) {
+        fft_combine(m->p->fft_X, op->a, op->b);
     }
 }
 
@@ -504,6 +583,25 @@ static void run_task(tvm *m, uint32_t s, uint32_t type) {
         prim_emit(m, s, 0);
         break;
     }
+    case T_FFT: {
+        const int64_t n = p->fft_n >> a1;
+        if (n <= p->fft_leaf) {
+            fft_leaf(p, a0, a1, n);
+            prim_emit(m, s, 0);
+            break;
+        }
+        uint32_t first = prim_fork(m, T_FFT, a0, a1 + 1);   /* even-numbered points */
+        prim_fork(m, T_FFT, a0 + (1u << a1), a1 + 1);       /* odd-numbered points */
+        prim_join(m, s, T_FFT_COMBINE, a0, a1, first);
+        break;
+    }
+    case T_FFT_COMBINE: {
+        const int64_t n = p->fft_n >> a1, dst = fft_block(a0, a1, p->fft_n);
+        if (n <= p->fft_cutoff) fft_combine(p->fft_X, dst, n);
+        else prim_map(m, MAP_FFT_COMBINE, dst, n, 0);
+        prim_emit(m, s, 0);
+        break;
+    }
     default:
         m->err = 2;
     }
@@ -538,6 +636,11 @@ int oracle_tvm_run(const oracle_tvm_params *p, oracle_epoch_t *trace, uint64_t t
         for (int32_t v = 0; v < p->nnodes; v++) p->visit_epoch[v] = -1;
         root_type = p->program == ORACLE_POSTORDER ? T_PO : T_PRE;
         r0 = p->nnodes > 0 ? 0u : 0xFFFFFFFFu; break;
+    case ORACLE_FFT:
+        if (p->fft_n < 1 || (p->fft_n & (p->fft_n - 1)) || p->fft_n > (1LL << 30) || p->fft_leaf < 1 ||
+            !p->fft_x || !p->fft_X)
+            return 4;
+        root_type = T_FFT; r0 = 0; r1 = 0; break;
     default: return 4;
     }
     /* Initialisation (Sec. 4.3, 5.2.1): the root in entry 0 for epoch 0 */

@@ -60,6 +60,7 @@ def _load():
                                                    ctypes.c_void_p]
         lib.trees_gen_binary_tree.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p,
                                               ctypes.c_void_p]
+        lib.trees_gen_signal.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]
         _lib = lib
     return _lib
 
@@ -134,4 +135,12 @@ def weights(seed: int, row_ptr: np.ndarray, col: np.ndarray, wmax: int = 255) ->
     if col.size:
         _load().trees_gen_weights(seed, row_ptr.shape[0] - 1, row_ptr.ctypes.data, col.ctypes.data, wmax,
                                   out.ctypes.data)
+    return out
+
+
+def signal(seed: int, n: int) -> np.ndarray:
+    """``n`` complex64 points, real and imaginary parts uniform on [-1, 1)."""
+    out = np.empty(n, dtype=np.complex64)
+    if n:
+        _load().trees_gen_signal(seed, n, out.ctypes.data)
     return out

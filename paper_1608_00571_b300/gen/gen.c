@@ -224,3 +224,14 @@ void trees_gen_weights(uint64_t seed, int32_t nv, const int32_t *row_ptr, const 
         }
     }
 }
+
+/* n complex points as interleaved (re, im) floats: component c (0 = re,
+ * 1 = im) of point i is ((splitmix64(seed, 2i + c) >> 40) - 2^23) / 2^23,
+ * uniform on [-1, 1) with 24-bit resolution, so exactly a float. */
+void trees_gen_signal(uint64_t seed, uint64_t n, float *out) {
+    int64_t nn = (int64_t)(2 * n);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nn; i++)
+        out[i] = (float)((int64_t)(trees_gen_splitmix64(seed, (uint64_t)i) >> 40) - (1LL << 23)) *
+                 (1.0f / 8388608.0f);
+}

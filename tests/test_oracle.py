@@ -409,3 +409,87 @@ def test_sssp_source_out_of_range_and_isolated():
     assert reached == 0 and (dist == oracle.SSSP_INF).all()
     dist, reached = oracle.sssp_dijkstra(row_ptr, col, w, 2)
     assert reached == 1 and dist[2] == 0 and dist[0] == dist[1] == oracle.SSSP_INF
+
+
+# ------------------------------------------------------------ FFT (Sec. 6.2, Fig. 6)
+
+def fft_input(seed, n):
+    return gen.signal(seed, n).astype(np.complex128)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 12, 64])
+def test_dft_closed_forms(n):
+    j = np.arange(n)
+    # a constant sums to n at frequency 0 and cancels elsewhere
+    X = oracle.dft(np.full(n, 2.0 - 1.0j))
+    want = np.zeros(n, complex)
+    want[0] = n * (2.0 - 1.0j)
+    assert np.allclose(X, want, atol=1e-12 * n)
+    # the tone exp(+2 pi i f j / n) lands on bin f alone (a sign error would put it on n - f)
+    for f in range(n):
+        X = oracle.dft(np.exp(2j * np.pi * f * j / n))
+        want = np.zeros(n, complex)
+        want[f] = n
+        assert np.allclose(X, want, atol=1e-10 * n)
+    # a geometric sequence r^j has the closed form (1 - r^n) / (1 - r exp(-2 pi i k / n))
+    r = 0.9 * np.exp(0.3j)
+    X = oracle.dft(r ** j)
+    k = np.arange(n)
+    assert np.allclose(X, (1 - r ** n) / (1 - r * np.exp(-2j * np.pi * k / n)), atol=1e-11 * n)
+
+
+@pytest.mark.parametrize("n", [1, 7, 64, 1000])
+def test_dft_matches_numpy_and_theorems(n):
+    x = fft_input(11, n)
+    X = oracle.dft(x)
+    scale = np.linalg.norm(X) + 1.0
+    assert np.linalg.norm(X - np.fft.fft(x)) <= 1e-12 * n * scale
+    # Parseval: sum |x|^2 = sum |X|^2 / n
+    assert abs(np.sum(abs(x) ** 2) - np.sum(abs(X) ** 2) / n) <= 1e-10 * np.sum(abs(x) ** 2) + 1e-300
+    # shift theorem: x[j - m] <-> X[k] exp(-2 pi i k m / n)
+    m = n // 3
+    Xs = oracle.dft(np.roll(x, m))
+    assert np.linalg.norm(Xs - X * np.exp(-2j * np.pi * np.arange(n) * m / n)) <= 1e-11 * n * scale
+    # linearity
+    y = fft_input(12, n)
+    assert np.linalg.norm(oracle.dft(x + 2 * y) - (X + 2 * oracle.dft(y))) <= 1e-11 * n * scale
+    # single outputs equal the full transform's
+    ks = [0, n - 1, n // 2]
+    assert np.array_equal(oracle.dft_at(x, ks), X[ks])
+
+
+def fft_tvm_counts(n, leaf, cutoff):
+    """The FFT task tree in closed form: depth D = log2(n / leaf) levels of
+    forks (2^d tasks at depth d), 2^D leaves, one combine per internal task."""
+    D = max(0, n.bit_length() - 1 - (leaf.bit_length() - 1)) if n > leaf else 0
+    maps = sum(2 ** d for d in range(D) if (n >> d) > cutoff)
+    return {"epochs": 2 * D + 1, "tasks": 2 ** (D + 1) - 1 + 2 ** D - 1, "forks": 2 ** (D + 1) - 2,
+            "joins": 2 ** D - 1, "maps": maps, "peak_slots": 2 ** (D + 1) - 1, "final_slots": 0}, D
+
+
+@pytest.mark.parametrize("lg", [0, 1, 2, 3, 5, 8, 10])
+@pytest.mark.parametrize("leaf,cutoff", [(1, 0), (2, 4), (4, 1 << 20), (16, 32)])
+def test_fft_tvm_matches_dft_and_closed_forms(lg, leaf, cutoff):
+    n = 1 << lg
+    x = fft_input(lg * 7 + leaf, n)
+    r = oracle.tvm_run(oracle.FFT, x=x, fft_leaf=leaf, fft_cutoff=cutoff)
+    want = np.fft.fft(x)
+    assert np.linalg.norm(r["X"] - want) <= 1e-14 * (lg + 1) * np.linalg.norm(want)
+    counts, D = fft_tvm_counts(n, leaf, cutoff)
+    for key, v in counts.items():
+        assert r["stats"][key] == v, key
+    # the epochs: fork levels 0..D, then the join ranges revisited bottom-up
+    tr = r["trace"]
+    for i, t in enumerate(tr):
+        d = i if i <= D else 2 * D - i
+        assert (t["cen"], t["lo"], t["hi"], t["valid"]) == (d, 2 ** d - 1, 2 ** (d + 1) - 1, 2 ** d)
+        assert t["forks"] == (2 ** (d + 1) if i < D else 0)
+        assert t["joined"] == (1 if i < D else 0)
+        assert t["maps"] == (2 ** d if i > D and (n >> d) > cutoff else 0)
+
+
+def test_fft_tvm_single_leaf_is_the_definition():
+    x = fft_input(5, 16)
+    r = oracle.tvm_run(oracle.FFT, x=x, fft_leaf=16)
+    assert r["stats"]["tasks"] == 1 and r["stats"]["epochs"] == 1
+    assert np.allclose(r["X"], oracle.dft(x), rtol=0, atol=1e-13)

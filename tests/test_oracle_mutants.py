@@ -44,6 +44,21 @@ MUTANTS = {
                                  "if (queued[u] < 0) { queued[u] = r; out[nout++] = u; }"),
     # the plain recursion counts calls wrongly
     "fib_calls_skip": ("    (*calls)++;\n    if (n < 2) return n;", "    if (n < 2) return n;\n    (*calls)++;"),
+    # the definition's kernel has the wrong sign
+    "dft_kernel_sign": ("const double ang = -2.0 * M_PI * (double)((j * k) % n) / (double)n;\n    const double c",
+                        "const double ang = 2.0 * M_PI * (double)((j * k) % n) / (double)n;\n    const double c"),
+    # the definition pairs j with k by a sum instead of a product
+    "dft_index_sum": ("(double)((j * k) % n) / (double)n;\n    const double c",
+                      "(double)((j + k) % n) / (double)n;\n    const double c"),
+    # the combine's twiddle turns the wrong way
+    "fft_twiddle_sign": ("const double ang = -2.0 * M_PI * (double)k / (double)n, wr",
+                         "const double ang = 2.0 * M_PI * (double)k / (double)n, wr"),
+    # the second half of a combine adds instead of subtracting
+    "fft_combine_second_half": ("        od[0] = er - tr;\n", "        od[0] = er + tr;\n"),
+    # output blocks are placed with the bit weights reversed
+    "fft_block_bit_order": ("if ((o >> b) & 1u) pos += N >> (b + 1);", "if ((o >> b) & 1u) pos += N >> (d - b);"),
+    # a leaf drops the imaginary part of its input
+    "fft_leaf_drops_imag": (" - p->fft_x[2 * src + 1] * sin(ang);", ";"),
 }
 
 
@@ -64,6 +79,13 @@ def run_pins():
     pins.test_sssp_rmat_scipy_and_worklist()
     pins.test_fig3_postorder_trace("B")
     pins.test_traversal_orders_random_tree()
+    for n in (1, 8, 12):
+        pins.test_dft_closed_forms(n)
+    pins.test_dft_matches_numpy_and_theorems(64)
+    for lg in (1, 3, 8):
+        pins.test_fft_tvm_matches_dft_and_closed_forms(lg, 2, 4)
+        pins.test_fft_tvm_matches_dft_and_closed_forms(lg, 1, 0)
+        pins.test_fft_tvm_matches_dft_and_closed_forms(lg, 16, 32)
 
 
 @pytest.fixture(scope="module")
@@ -84,7 +106,7 @@ def test_mutant_is_caught(name, workdir):
     with open(path, "w") as f:
         f.write(src.replace(old, new))
     so = path[:-2] + ".so"
-    subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", path, "-o", so])
+    subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", path, "-o", so, "-lm"])
     saved = oracle._load()
     oracle._lib = oracle._bind(ctypes.CDLL(so))
     try:
