@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "tasks/sec & µs/epoch (fib, sort, BFS); batched jobs/sec, p99 latency vs plain"
 FIB_N = 34
 FLUSH_BYTES = 256 << 20  # > 126 MB L2
+FFT_LG, FFT_LEAF, FFT_CUTOFF = 24, 16, 64  # 2^24 points; 16-point leaves; combines of <= 64 points in-task
 SSSP_SLOTS_PER_VERTEX = 3  # task-vector slots per vertex for SSSP (measured 1.10-1.12 relax tasks per vertex)
 
 
@@ -47,7 +48,7 @@ def parse_args():
                     help="JSON file for the autotuner's choices (default: tune afresh every run)")
     ap.add_argument("--profile-case", default=None,
                     help="PROGRAM:SIZE[:BLOCK[:SLOTS_PER_THREAD[:SCHEDULER]]] -- run one small case twice and exit "
-                         "(for ncu): fib:N, sort:LOG2KEYS, bfs:RMAT_SCALE, sssp:RMAT_SCALE")
+                         "(for ncu): fib:N, sort:LOG2KEYS, bfs:RMAT_SCALE, sssp:RMAT_SCALE, fft:LOG2POINTS")
     return ap.parse_args()
 
 
@@ -99,6 +100,14 @@ def profile_case(spec):
         ctx = T.trees_create(3 * nv + 1024,
                              T.trees_default_config(block_size=bs, tasks_per_thread=tpt, scheduler=sched))
         job = T.make_job(T.TREES_PROG_SSSP, n=0, row_ptr=rp, col=cl, weight=wt, nv=nv, dist=dist, sched=sched_t)
+    elif prog == "fft":
+        n = 1 << size
+        xi = torch.from_numpy(gen.signal(1, n).view(np.float32)).cuda()
+        xo = torch.empty_like(xi)
+        keep += [xi, xo]
+        job = T.make_job(T.TREES_PROG_FFT, n=n, leaf=FFT_LEAF, cutoff=FFT_CUTOFF, fft_in=xi, fft_out=xo)
+        ctx = T.trees_create(T.trees_job_slots(job)[0],
+                             T.trees_default_config(block_size=bs, tasks_per_thread=tpt, scheduler=sched))
     else:
         raise SystemExit(f"unknown profile case {spec}")
     for _ in range(2):
@@ -246,6 +255,15 @@ def sssp_alg_bytes(row_ptr, reached, tasks):
     import numpy as np
     edges = int(np.diff(row_ptr)[reached].sum())
     return 16 * edges + 56 * tasks, edges
+
+
+def fft_alg_bytes(n, leaf):
+    """Bytes the FFT task tree must move: the leaves read x and write X once
+    (16 B per point), every combine level reads and writes X once more (16 B
+    per point per level, log2(n / leaf) levels).  Task-vector and map
+    descriptor traffic (under 1 % here) is left out."""
+    levels = max(0, n.bit_length() - leaf.bit_length())
+    return 16 * n * (1 + levels), levels
 
 
 def sssp_certificate(row_ptr, col, weight, src, dist, level):
@@ -681,6 +699,35 @@ def main():
                                                  "frac": ab5 / (m5 / 1000) / 1e9 / hbm_peak,
                                                  "algorithmic_bytes": ab5, "note": "lower bound (edges once per vertex)"}}
         del rp, cl, lv, wt, dist_t, sched_t
+        # FFT of 2^24 complex fp32 points (Sec. 6.2, Fig. 6): radix-2 tasks, combines above 64 points as maps
+        n6 = 1 << FFT_LG
+        x6 = gen.signal(1, n6)
+        xi6 = torch.from_numpy(x6.view(np.float32)).cuda()
+        xo6 = torch.empty_like(xi6)
+        j6 = T.make_job(T.TREES_PROG_FFT, n=n6, leaf=FFT_LEAF, cutoff=FFT_CUTOFF, fft_in=xi6, fft_out=xo6)
+        cap6 = T.trees_job_slots(j6)[0]
+        c6 = T.trees_create(cap6, tune(j6, cap6, f"fft:n=2^{FFT_LG}:leaf={FFT_LEAF}:cutoff={FFT_CUTOFF}"))
+        t6 = timed_runs(T, torch, c6, j6, 5, 1, stream, flush)
+        s6 = T.trees_stats(c6)
+        T.trees_destroy(c6)
+        X6 = xo6.cpu().numpy().view(np.complex64).astype(np.complex128)
+        import oracle
+        ks = np.array([0, 1, n6 // 3, n6 - 1])
+        norm_X = np.sqrt(n6) * np.linalg.norm(x6.astype(np.complex128))  # Parseval
+        rel = 24 * 8 * 2.0 ** -24 / (1 - 24 * 8 * 2.0 ** -24)           # radix-2 fp32 error bound
+        ok6 = bool(np.all(np.isfinite(X6)) and abs(np.linalg.norm(X6) - norm_X) <= rel * norm_X and
+                   np.all(np.abs(X6[ks] - oracle.dft_at(x6.astype(np.complex128), ks)) <= rel * norm_X))
+        m6 = statistics.mean(t6)
+        ab6, lv6 = fft_alg_bytes(n6, FFT_LEAF)
+        workloads[f"fft_2^{FFT_LG}"] = {
+            "ms": m6, "tasks": s6["tasks"], "epochs": s6["epochs"], "maps": s6["maps"],
+            "tasks_per_s": s6["tasks"] / (m6 / 1000), "us_per_epoch": 1000 * m6 / s6["epochs"],
+            "points_per_s": n6 / (m6 / 1000), "gflops_5nlogn": 5 * n6 * FFT_LG / (m6 / 1000) / 1e9,
+            "leaf": FFT_LEAF, "cutoff": FFT_CUTOFF, "dtype": "complex fp32", "combine_levels": lv6,
+            "sampled_outputs_within_bound": ok6,
+            "roofline": {"bound": "hbm", "achieved": ab6 / (m6 / 1000) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": ab6 / (m6 / 1000) / 1e9 / hbm_peak, "algorithmic_bytes": ab6}}
+        del xi6, xo6
         line["workloads"] = workloads
         # graph-relaunch and host-loop schedulers on the headline workload
         sch = {}

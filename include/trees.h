@@ -57,7 +57,12 @@ extern "C" {
 #define TREES_TASK_PRE 10        /* preorder(node) of Fig. 2 */
 #define TREES_TASK_SSSP_RELAX 11 /* SSSP vertex (Sec. 6.3's worklist relaxation as tasks): map over its
                                     out-edges; a neighbour whose distance it shortens is forked once per epoch */
-#define TREES_NUM_TASK_TYPES 11
+#define TREES_TASK_FFT 12        /* FFT (Sec. 6.2) of the points o, o + 2^d, o + 2*2^d, ... of the input:
+                                    a leaf transforms them in its task, else it forks its even and odd points
+                                    and joins FFT_COMBINE */
+#define TREES_TASK_FFT_COMBINE 13 /* join: radix-2 butterflies merging the two half transforms, in the task
+                                     or, above the cutoff, as a map over the butterflies */
+#define TREES_NUM_TASK_TYPES 13
 
 /* ------------------------------------------------------------ programs */
 #define TREES_PROG_FIB 1
@@ -67,6 +72,7 @@ extern "C" {
 #define TREES_PROG_POSTORDER 5
 #define TREES_PROG_PREORDER 6
 #define TREES_PROG_SSSP 7
+#define TREES_PROG_FFT 8
 
 /* ------------------------------------------------------------ schedulers */
 #define TREES_SCHED_PERSISTENT 0 /* one cooperative launch; one grid barrier per epoch */
@@ -124,9 +130,13 @@ int trees_geometry(const trees_ctx *ctx, int32_t *grid_blocks, int32_t *block_si
 typedef struct {
     int32_t program;          /* TREES_PROG_* */
     uint32_t n;               /* fib: n; N-Queens: board size (1..16); mergesort: number of keys;
-                                 BFS, SSSP: source vertex; traversal: number of nodes */
-    uint32_t cutoff;          /* fib: a call with n <= cutoff is a leaf computed in its task (0 = none) */
-    uint32_t leaf;            /* mergesort: leaf size, 1..1024 (0 = 1024) */
+                                 BFS, SSSP: source vertex; traversal: number of nodes;
+                                 FFT: number of points, a power of two in [1, 2^25] */
+    uint32_t cutoff;          /* fib: a call with n <= cutoff is a leaf computed in its task (0 = none);
+                                 FFT: a combine of <= cutoff points runs in its task, a larger one as a
+                                 map (0 = every combine is a map; >= n = none is, as in Sec. 6.2) */
+    uint32_t leaf;            /* mergesort: leaf size, 1..1024 (0 = 1024);
+                                 FFT: leaf transform size, 1, 2, 4, 8 or 16 (0 = 16) */
     uint32_t *keys;           /* mergesort: device keys, sorted in place */
     uint32_t *scratch;        /* mergesort: device buffer of n keys (NULL = the context's own) */
     const int32_t *row_ptr;   /* BFS, SSSP: device CSR row offsets [nv+1] */
@@ -140,6 +150,10 @@ typedef struct {
     uint64_t *dist;           /* SSSP: device output [nv], shortest distance from the source,
                                  UINT64_MAX = unreachable */
     uint32_t *sched;          /* SSSP: device scratch [nv]: the last epoch each vertex was forked for */
+    const float *fft_in;      /* FFT: device input, n complex points as interleaved (re, im) fp32,
+                                 8-byte aligned; read only */
+    float *fft_out;           /* FFT: device output [2n] floats, X[k] = sum_j x[j] exp(-2 pi i j k / n);
+                                 8-byte aligned, must not overlap fft_in */
 } trees_job_t;
 
 /* Sec. 5.2.1 initialisation + the epoch loop: writes the job's root task
@@ -211,6 +225,25 @@ int trees_bfs(trees_ctx *ctx, const int32_t *dev_row_ptr, const int32_t *dev_col
  * range), CAPACITY at run time. */
 int trees_sssp(trees_ctx *ctx, const int32_t *dev_row_ptr, const int32_t *dev_col, const uint32_t *dev_weight,
                int32_t nv, int32_t src, uint64_t *dev_dist, uint32_t *dev_sched, void *stream);
+/* Fast Fourier transform as tasks (Sec. 6.2, Fig. 6): the n-point DFT
+ * X[k] = sum_j x[j] exp(-2 pi i j k / n) by radix-2 decimation in time.
+ * FFT(o, d) transforms the n >> d points of index o modulo 2^d: at most
+ * `leaf` points are transformed inside the task (registers), more fork the
+ * even- and odd-numbered points and join a combine of n >> d points, run
+ * inside its task when it is at most `cutoff` points, else as a map whose
+ * butterflies the whole grid shares (the paper's FFT uses no maps; cutoff
+ * >= n reproduces that).  dev_in and dev_out hold n complex fp32 values as
+ * interleaved (re, im) pairs, 8-byte aligned, and must not overlap; dev_in
+ * is not written.  Arithmetic is fp32: every butterfly computes
+ * t = w * O[k] with fused multiply-adds in a fixed order and E[k] +- t,
+ * w = exp(-2 pi i k / m) from sincospif on the exact quotient 2k/m, so the
+ * output does not depend on leaf, cutoff, block size or scheduler.  Needs
+ * 2^(D+1) - 1 task slots and 2^(D-1) map descriptors, D = log2(n / leaf).
+ * Errors: INVALID_ARG (n not a power of two in [1, 2^25], leaf not a power
+ * of two <= 16, null or misaligned or overlapping buffers), CAPACITY at run
+ * time. */
+int trees_fft(trees_ctx *ctx, const float *dev_in, float *dev_out, uint32_t n, uint32_t leaf, uint32_t cutoff,
+              void *stream);
 
 /* ------------------------------------------------------------ measurement */
 

@@ -36,6 +36,7 @@ TREES_PROG_BFS = 4
 TREES_PROG_POSTORDER = 5
 TREES_PROG_PREORDER = 6
 TREES_PROG_SSSP = 7
+TREES_PROG_FFT = 8
 
 # schedulers
 TREES_SCHED_PERSISTENT = 0
@@ -63,7 +64,7 @@ class trees_job_t(ctypes.Structure):
                 ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("level", ctypes.c_void_p),
                 ("nv", ctypes.c_int32), ("left", ctypes.c_void_p), ("right", ctypes.c_void_p),
                 ("visit_epoch", ctypes.c_void_p), ("weight", ctypes.c_void_p), ("dist", ctypes.c_void_p),
-                ("sched", ctypes.c_void_p)]
+                ("sched", ctypes.c_void_p), ("fft_in", ctypes.c_void_p), ("fft_out", ctypes.c_void_p)]
 
 
 class trees_stats_t(ctypes.Structure):
@@ -123,6 +124,7 @@ _SIGNATURES = [
     ("trees_mergesort_u32", ctypes.c_int, [_ctxp, _vp, _vp, ctypes.c_uint32, _vp]),
     ("trees_bfs", ctypes.c_int, [_ctxp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
     ("trees_sssp", ctypes.c_int, [_ctxp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]),
+    ("trees_fft", ctypes.c_int, [_ctxp, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp]),
     ("trees_barrier_floor", ctypes.c_int, [_ctxp, ctypes.c_uint32, _vp, ctypes.POINTER(ctypes.c_double)]),
     ("trees_fib_noalloc", ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, _vp, _vp, _vp]),
     ("trees_autotune", ctypes.c_int, [ctypes.POINTER(trees_job_t), ctypes.c_size_t, ctypes.POINTER(trees_config_t),
@@ -231,7 +233,7 @@ def trees_geometry(ctx):
 
 def make_job(program: int, n: int = 0, cutoff: int = 0, leaf: int = 0, keys=None, scratch=None, row_ptr=None,
              col=None, level=None, nv: int = 0, left=None, right=None, visit_epoch=None, weight=None, dist=None,
-             sched=None) -> trees_job_t:
+             sched=None, fft_in=None, fft_out=None) -> trees_job_t:
     j = trees_job_t()
     j.program = program
     j.n = n
@@ -249,6 +251,8 @@ def make_job(program: int, n: int = 0, cutoff: int = 0, leaf: int = 0, keys=None
     j.weight = _ptr(weight)
     j.dist = _ptr(dist)
     j.sched = _ptr(sched)
+    j.fft_in = _ptr(fft_in)
+    j.fft_out = _ptr(fft_out)
     return j
 
 
@@ -301,6 +305,10 @@ def trees_bfs(ctx, row_ptr, col, nv: int, src: int, level, stream=None) -> int:
 def trees_sssp(ctx, row_ptr, col, weight, nv: int, src: int, dist, sched, stream=None) -> int:
     return _check("trees_sssp", lib().trees_sssp(ctx, _ptr(row_ptr), _ptr(col), _ptr(weight), nv, src, _ptr(dist),
                                                  _ptr(sched), _stream(stream)))
+
+
+def trees_fft(ctx, x, out, n: int, leaf: int = 0, cutoff: int = 0, stream=None) -> int:
+    return _check("trees_fft", lib().trees_fft(ctx, _ptr(x), _ptr(out), n, leaf, cutoff, _stream(stream)))
 
 
 def trees_barrier_floor(ctx, iters: int = 1000, stream=None) -> float:

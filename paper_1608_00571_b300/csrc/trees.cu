@@ -260,6 +260,7 @@ const void *persistent_kernel(int program, int bs, int tpt) {
     case TREES_PROG_NQUEENS: return persistent_kernel_nq(bs, tpt);
     case TREES_PROG_BFS: return persistent_kernel_bfs(bs, tpt);
     case TREES_PROG_SSSP: return persistent_kernel_sssp(bs, tpt);
+    case TREES_PROG_FFT: return persistent_kernel_fft(bs, tpt);
     default: return persistent_kernel_trav(bs, tpt);
     }
 }
@@ -803,6 +804,21 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
         type = TREES_TASK_SSSP_RELAX;
         a0 = job->n;
         break;
+    case TREES_PROG_FFT: {
+        const uint32_t n = job->n, leaf = job->leaf ? job->leaf : FFT_LEAF_MAX;
+        const uintptr_t in = (uintptr_t)job->fft_in, out = (uintptr_t)job->fft_out, bytes = (uintptr_t)n * 8u;
+        if (n < 1u || (n & (n - 1u)) || n > FFT_MAX_POINTS || leaf > FFT_LEAF_MAX || (leaf & (leaf - 1u)) || !in ||
+            !out || (in & 7u) || (out & 7u) || (in < out + bytes && out < in + bytes))
+            return TREES_ERR_INVALID_ARG;
+        rp.leaf = leaf;
+        rp.fx = reinterpret_cast<const float2 *>(job->fft_in);
+        rp.fX = reinterpret_cast<float2 *>(job->fft_out);
+        rp.lgn = (uint32_t)__builtin_ctz(n);
+        type = TREES_TASK_FFT;
+        a0 = 0;
+        a1 = 0;
+        break;
+    }
     case TREES_PROG_POSTORDER:
     case TREES_PROG_PREORDER:
         if (job->n && (!job->left || !job->right || !job->visit_epoch)) return TREES_ERR_INVALID_ARG;
@@ -981,6 +997,18 @@ int trees_sssp(trees_ctx *x, const int32_t *row_ptr, const int32_t *col, const u
     j.nv = nv;
     j.dist = dist;
     j.sched = sched;
+    return trees_run(x, &j, stream);
+}
+
+int trees_fft(trees_ctx *x, const float *in, float *out, uint32_t n, uint32_t leaf, uint32_t cutoff, void *stream) {
+    trees_job_t j;
+    std::memset(&j, 0, sizeof(j));
+    j.program = TREES_PROG_FFT;
+    j.n = n;
+    j.leaf = leaf;
+    j.cutoff = cutoff;
+    j.fft_in = in;
+    j.fft_out = out;
     return trees_run(x, &j, stream);
 }
 
@@ -1187,6 +1215,13 @@ uint64_t job_slots(const trees_job_t *j, int32_t *exact) {
         need = (uint64_t)std::max(j->nv, 1);
         ex = 0;
         break;
+    case TREES_PROG_FFT: {  // the whole task tree: 2^(D+1) - 1 FFT tasks, D = log2(n / leaf)
+        const uint64_t leaf = j->leaf ? j->leaf : FFT_LEAF_MAX;
+        uint64_t D = 0;
+        while (((uint64_t)j->n >> D) > leaf) ++D;
+        need = (2ull << D) - 1ull;
+        break;
+    }
     default:
         need = 0;
         ex = 0;

@@ -20,6 +20,9 @@ namespace trees {
 constexpr uint32_t NTT = TREES_NUM_TASK_TYPES;  // NumTaskTypes of footnote 2, Sec. 5.1.2
 constexpr int STK_CAP = 512;                    // epoch-range stack entries per job
 constexpr int LEAF_MAX = 1024;                  // largest leaf a block sorts in shared memory
+constexpr uint32_t FFT_LEAF_MAX = 16;           // largest FFT leaf a thread transforms in registers
+constexpr uint32_t FFT_MAX_POINTS = 1u << 25;   // twiddle quotients 2k/M stay exact in fp32 (k < 2^24)
+constexpr uint32_t FFT_CHUNK = 8;               // combine-map butterflies a thread keeps in flight
 // Outputs per thread of a merge tile (Sec. 5.2.4's map operations, tiled by
 // merge path) for a block of bs threads: odd counts keep the threads' probes
 // and run heads on distinct shared-memory banks.  A full tile is bs *
@@ -64,6 +67,9 @@ struct RunParams {
     const uint32_t *weight;    // SSSP edge weights (aligned with col)
     unsigned long long *dist;  // SSSP distances
     uint32_t *sched;           // SSSP: the last epoch each vertex was forked for
+    const float2 *fx;          // FFT input, N complex points
+    float2 *fX;                // FFT output
+    uint32_t lgn;              // FFT: log2 N
 };
 
 // Read-only during a run: where everything lives.
@@ -73,8 +79,9 @@ struct Conf {
     uint32_t cap;
     // tiled map list: one descriptor per map operation, `units` tiles each
     uint32_t *mt_kind, *mt_a, *mt_b, *mt_c, *mt_job, *mt_tilebase, *mt_split;
-    // element map list (BFS / SSSP expansion): one descriptor per vertex, one unit per edge;
-    // me_v = the vertex's first adjacency index, me_src = the vertex
+    // element map list (BFS / SSSP expansion, FFT combine): one descriptor per vertex, one unit
+    // per edge, me_v = the vertex's first adjacency index, me_src = the vertex; or one descriptor
+    // per combine, one unit per butterfly, me_v = the output block, me_src = log2 of its size
     uint32_t *me_v, *me_base, *me_job, *me_tfd, *me_src;
     uint32_t mcap;
     trees_epoch_t *trace;

@@ -49,9 +49,11 @@ __device__ __forceinline__ void trace_valid_add(const Conf &c, uint32_t e, uint3
 // SSSP R-MAT 22 6.1 -> 3.8 ms, BFS 1.63 -> 1.23 ms); the fib kernel trades
 // threads for registers as its slots per thread grow (1024, 768, 512 threads
 // per SM for 1, 2, 4 slots: measured, each spill-free beats more resident
-// warps that spill); the others take what they need.
+// warps that spill); the FFT kernel keeps 512 (128 registers: its leaf
+// transforms and combine butterflies spill at 64); the others take what
+// they need.
 __host__ __device__ constexpr int persistent_min_blocks(int bs, uint32_t pm, int tpt) {
-    const int tps = (pm == PM_MS || pm == PM_BFS || pm == PM_SSSP) ? 1024
+    const int tps = (pm == PM_MS || pm == PM_BFS || pm == PM_SSSP) ? 1024 : pm == PM_FFT ? 512
                   : pm == PM_FIB ? (tpt >= 4 ? 512 : tpt == 2 ? 768 : 1024) : 0;
     return tps / bs > 0 ? tps / bs : 1;
 }
@@ -346,5 +348,6 @@ const void *persistent_kernel_nq(int bs, int tpt);
 const void *persistent_kernel_bfs(int bs, int tpt);
 const void *persistent_kernel_trav(int bs, int tpt);
 const void *persistent_kernel_sssp(int bs, int tpt);
+const void *persistent_kernel_fft(int bs, int tpt);
 
 }  // namespace trees

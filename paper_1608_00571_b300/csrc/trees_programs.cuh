@@ -11,7 +11,8 @@
 //
 // Map operations (Sec. 4.2, 4.3.2, 5.2.4) are data-parallel work run by the
 // whole grid after the epoch's tasks and before the next epoch: the
-// mergesort leaf sort and merge-path merge, and the BFS adjacency expansion.
+// mergesort leaf sort and merge-path merge, the BFS and SSSP adjacency
+// expansions and the FFT's combine butterflies.
 #pragma once
 
 #include "trees_dev.cuh"
@@ -25,9 +26,9 @@ struct Acc {
 // Program masks: which task types (and maps) a kernel is compiled for.  A
 // kernel built for one program carries only that program's dispatch cases,
 // as the paper's compiler emits one kernel per program (Sec. 5).
-constexpr uint32_t PM_FIB = 1u, PM_MS = 2u, PM_NQ = 4u, PM_BFS = 8u, PM_TRAV = 16u, PM_SSSP = 32u;
-constexpr uint32_t PM_ALL = PM_FIB | PM_MS | PM_NQ | PM_BFS | PM_TRAV | PM_SSSP;
-constexpr uint32_t PM_MAPS = PM_MS | PM_BFS | PM_SSSP;  // programs that schedule map operations
+constexpr uint32_t PM_FIB = 1u, PM_MS = 2u, PM_NQ = 4u, PM_BFS = 8u, PM_TRAV = 16u, PM_SSSP = 32u, PM_FFT = 64u;
+constexpr uint32_t PM_ALL = PM_FIB | PM_MS | PM_NQ | PM_BFS | PM_TRAV | PM_SSSP | PM_FFT;
+constexpr uint32_t PM_MAPS = PM_MS | PM_BFS | PM_SSSP | PM_FFT;  // programs that schedule map operations
 
 __host__ __device__ constexpr uint32_t program_mask(int program) {
     return program == TREES_PROG_FIB         ? PM_FIB
@@ -35,6 +36,7 @@ __host__ __device__ constexpr uint32_t program_mask(int program) {
            : program == TREES_PROG_NQUEENS   ? PM_NQ
            : program == TREES_PROG_BFS       ? PM_BFS
            : program == TREES_PROG_SSSP      ? PM_SSSP
+           : program == TREES_PROG_FFT       ? PM_FFT
                                              : PM_TRAV;
 }
 
@@ -73,7 +75,105 @@ __device__ __forceinline__ uint32_t nq_free(uint32_t a0, uint32_t a1, uint32_t n
 // Which TV columns a task type reads besides its code.
 __device__ __forceinline__ bool needs_a0(uint32_t t) { return t != 0u && t != TREES_TASK_FIB_SUM; }
 __device__ __forceinline__ bool needs_a1(uint32_t t) {
-    return t == TREES_TASK_MS_SPLIT || t == TREES_TASK_MS_MERGE || t == TREES_TASK_NQ_ROW || t == TREES_TASK_NQ_SUM;
+    return t == TREES_TASK_MS_SPLIT || t == TREES_TASK_MS_MERGE || t == TREES_TASK_NQ_ROW || t == TREES_TASK_NQ_SUM ||
+           t == TREES_TASK_FFT || t == TREES_TASK_FFT_COMBINE;
+}
+
+// ------------------------------------------------------------------ FFT (Sec. 6.2)
+// Radix-2 Cooley-Tukey by decimation in time.  Task FFT(o, d) (a0 = o,
+// a1 = d) transforms the M = N >> d points x[o + j 2^d], j < M.  Its even-
+// numbered points are the points of FFT(o, d+1), its odd-numbered ones those
+// of FFT(o + 2^d, d+1); their transforms E and O land in the first and second
+// half of its own output block, which the combine turns into its transform:
+// X[k] = E[k] + w^k O[k], X[k + M/2] = E[k] - w^k O[k], w = exp(-2 pi i / M).
+// So the block of FFT(o, d) starts at the d low bits of o reversed, times M.
+__device__ __forceinline__ uint32_t fft_block(uint32_t o, uint32_t d, uint32_t lgn) {
+    return d ? (__brev(o) >> (32u - d)) << (lgn - d) : 0u;
+}
+
+// exp(-2 pi i k / 2^lgm), k < 2^(lgm-1): sincospif of 2k / 2^lgm, a quotient
+// that is exact in fp32 for k < 2^24.
+__device__ __forceinline__ float2 fft_twiddle(uint32_t k, uint32_t lgm) {
+    float sn, cs;
+    sincospif(ldexpf((float)k, 1 - (int)lgm), &sn, &cs);
+    return make_float2(cs, -sn);
+}
+
+// One butterfly, e <- e + w o, o <- e - w o, with the roundings spelled out
+// so that every caller (leaf, combine task, combine map) computes
+// bit-identical values.
+__device__ __forceinline__ void fft_bfly(float2 &e, float2 &o, float2 w) {
+    const float tr = __fmaf_rn(w.x, o.x, -__fmul_rn(w.y, o.y));
+    const float ti = __fmaf_rn(w.x, o.y, __fmul_rn(w.y, o.x));
+    const float2 a = e;
+    e = make_float2(__fadd_rn(a.x, tr), __fadd_rn(a.y, ti));
+    o = make_float2(__fsub_rn(a.x, tr), __fsub_rn(a.y, ti));
+}
+
+__host__ __device__ constexpr int fft_rev(int j, int bits) {
+    return bits == 0 ? 0 : ((j & 1) << (bits - 1)) | fft_rev(j >> 1, bits - 1);
+}
+
+// A leaf of K = 2^LK points in registers: its points are loaded in
+// bit-reversed order, so the LK butterfly stages (the combines of the
+// 2-, 4-, ..., K-point sub-transforms, in the same arithmetic as the combine
+// tasks) leave its transform in natural order.
+template <int LK>
+__device__ __forceinline__ void fft_leaf_k(const float2 *__restrict__ x, float2 *__restrict__ X, uint32_t o,
+                                           uint32_t d, uint32_t dst) {
+    constexpr int K = 1 << LK;
+    float2 a[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) a[fft_rev(j, LK)] = x[o + ((uint32_t)j << d)];
+#pragma unroll
+    for (int lm = 1; lm <= LK; ++lm) {
+        const int h = 1 << (lm - 1);
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const float2 w = fft_twiddle((uint32_t)k, (uint32_t)lm);
+#pragma unroll
+            for (int g = 0; g < K; g += 2 * h) fft_bfly(a[g + k], a[g + k + h], w);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) X[dst + k] = a[k];
+}
+
+static __device__ __noinline__ void fft_leaf(const float2 *x, float2 *X, uint32_t o, uint32_t d, uint32_t lgn) {
+    const uint32_t dst = fft_block(o, d, lgn);
+    switch (lgn - d) {
+    case 0: X[dst] = x[o]; break;
+    case 1: fft_leaf_k<1>(x, X, o, d, dst); break;
+    case 2: fft_leaf_k<2>(x, X, o, d, dst); break;
+    case 3: fft_leaf_k<3>(x, X, o, d, dst); break;
+    default: fft_leaf_k<4>(x, X, o, d, dst); break;
+    }
+}
+
+// A combine of 2^lgm points done by its own task (the paper's FFT).
+static __device__ __noinline__ void fft_combine_task(float2 *X, uint32_t dst, uint32_t lgm) {
+    const uint32_t h = 1u << (lgm - 1u);
+    uint32_t k = 0;
+    for (; k + 4u <= h; k += 4u) {
+        float2 e[4], o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            e[q] = X[dst + k + q];
+            o[q] = X[dst + h + k + q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            fft_bfly(e[q], o[q], fft_twiddle(k + q, lgm));
+            X[dst + k + q] = e[q];
+            X[dst + h + k + q] = o[q];
+        }
+    }
+    for (; k < h; ++k) {
+        float2 e = X[dst + k], o = X[dst + h + k];
+        fft_bfly(e, o, fft_twiddle(k, lgm));
+        X[dst + k] = e;
+        X[dst + h + k] = o;
+    }
 }
 __device__ __forceinline__ bool needs_link(uint32_t t) { return t == TREES_TASK_FIB_SUM || t == TREES_TASK_NQ_SUM; }
 
@@ -172,6 +272,26 @@ __device__ __forceinline__ void plan_task(const Conf &c, const RunParams &rp, Pl
             return;
         }
     }
+    if constexpr ((PM & PM_FFT) != 0u) {
+        // a leaf's transform and a combine done in its task run at the end of
+        // the tile (fft_task_body), out of this unrolled loop
+        if (p.t == TREES_TASK_FFT) {
+            if ((1u << (rp.lgn - a1)) <= rp.leaf) c.code[s] = 0u;
+            else p.n = 2u;
+            return;
+        }
+        if (p.t == TREES_TASK_FFT_COMBINE) {
+            const uint32_t lgm = rp.lgn - a1, dst = fft_block(a0, a1, rp.lgn);
+            if ((1u << lgm) > rp.cutoff) {  // a map over its 2^(lgm-1) butterflies
+                p.m = MAP_EXPAND;
+                p.a0 = dst;
+                p.a1 = lgm;
+                p.n = 1u << (lgm - 1u);
+            }
+            c.code[s] = 0u;
+            return;
+        }
+    }
     if constexpr ((PM & PM_TRAV) != 0u) {
         if (p.t == TREES_TASK_PO) {
             if ((int32_t)a0 < 0) c.code[s] = 0u;
@@ -195,6 +315,14 @@ __device__ __forceinline__ void plan_task(const Conf &c, const RunParams &rp, Pl
 }
 
 __device__ __forceinline__ uint32_t forks_of(const Plan &p) { return p.m ? 0u : p.n; }
+
+// The work of an FFT leaf or of a combine below the cutoff (both emit and
+// fork nothing, so it can follow the tile's forks).
+__device__ __forceinline__ void fft_task_body(const RunParams &rp, const Plan &p) {
+    if (p.t == TREES_TASK_FFT && p.n == 0u) fft_leaf(rp.fx, rp.fX, p.a0, p.a1, rp.lgn);
+    else if (p.t == TREES_TASK_FFT_COMBINE && p.m == 0u)
+        fft_combine_task(rp.fX, fft_block(p.a0, p.a1, rp.lgn), rp.lgn - p.a1);
+}
 
 // Step 2: write the children into [child, child + n) for epoch CEN+1 and turn
 // the task into its join continuation.  Returns 1 if it joined.
@@ -244,6 +372,18 @@ __device__ __forceinline__ uint32_t commit_task(const Conf &c, const RunParams &
             }
             c.link[s] = child;
             c.code[s] = enc(cen, TREES_TASK_NQ_SUM);
+            return 1u;
+        }
+    }
+    if constexpr ((PM & PM_FFT) != 0u) {
+        if (p.t == TREES_TASK_FFT) {  // even-numbered points, then odd-numbered; join the combine (o, d)
+            c.code[child] = fe + TREES_TASK_FFT;
+            c.a0[child] = p.a0;
+            c.a1[child] = p.a1 + 1u;
+            c.code[child + 1] = fe + TREES_TASK_FFT;
+            c.a0[child + 1] = p.a0 + (1u << p.a1);
+            c.a1[child + 1] = p.a1 + 1u;
+            c.code[s] = enc(cen, TREES_TASK_FFT_COMBINE);
             return 1u;
         }
     }
@@ -330,7 +470,7 @@ __device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan (&p)
                 c.me_v[di] = p[k].a0;
                 c.me_base[di] = b;
                 c.me_job[di] = job;
-                c.me_src[di] = p[k].a1;  // the vertex (SSSP reads its distance)
+                c.me_src[di] = p[k].a1;  // the vertex (SSSP reads its distance); FFT: log2 block size
                 for (uint32_t t = (b + EXPAND_TILE - 1u) / EXPAND_TILE; t * EXPAND_TILE < b + p[k].n; ++t)
                     c.me_tfd[t] = di;
                 acc.maps++;
@@ -362,8 +502,8 @@ struct TileLoad {
 template <int BS, int TPT, uint32_t PM>
 __device__ __forceinline__ void tile_load(const Conf &c, unsigned long long t0, uint32_t hi, int mode,
                                           TileLoad<TPT> &L) {
-    constexpr bool fresh_a1 = (PM & (PM_MS | PM_NQ)) != 0u;
-    constexpr bool join_a0 = (PM & (PM_MS | PM_NQ | PM_TRAV)) != 0u;
+    constexpr bool fresh_a1 = (PM & (PM_MS | PM_NQ | PM_FFT)) != 0u;
+    constexpr bool join_a0 = (PM & (PM_MS | PM_NQ | PM_TRAV | PM_FFT)) != 0u;
     constexpr bool join_link = (PM & (PM_FIB | PM_NQ)) != 0u;
     const bool sa0 = mode == LOAD_FRESH || (mode == LOAD_JOIN && join_a0);
     const bool sa1 = (mode == LOAD_FRESH || mode == LOAD_JOIN) && fresh_a1;
@@ -404,8 +544,8 @@ __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> 
                                            uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, Acc &acc, int par,
                                            int mode, const TileLoad<TPT> &L, bool known, uint32_t known_off,
                                            bool jr_use = false, const TileLoad<TPT> *pf = nullptr) {
-    constexpr bool fresh_a1 = (PM & (PM_MS | PM_NQ)) != 0u;
-    constexpr bool join_a0 = (PM & (PM_MS | PM_NQ | PM_TRAV)) != 0u;
+    constexpr bool fresh_a1 = (PM & (PM_MS | PM_NQ | PM_FFT)) != 0u;
+    constexpr bool join_a0 = (PM & (PM_MS | PM_NQ | PM_TRAV | PM_FFT)) != 0u;
     constexpr bool join_link = (PM & (PM_FIB | PM_NQ)) != 0u;
     const bool sa0 = mode == LOAD_FRESH || (mode == LOAD_JOIN && join_a0);
     const bool sa1 = (mode == LOAD_FRESH || mode == LOAD_JOIN) && fresh_a1;
@@ -506,6 +646,12 @@ __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> 
     }
     if constexpr ((PM & PM_MAPS) != 0u) {
         if (anymap) map_alloc<BS, TPT>(c, ctl, sm, p, cen, ep, e, 0u, acc);
+    }
+    if constexpr ((PM & PM_FFT) != 0u) {
+        if (PM == PM_FFT || c.rp.program == TREES_PROG_FFT) {
+#pragma unroll 1
+            for (int k = 0; k < TPT; ++k) fft_task_body(c.rp, p[k]);
+        }
     }
     return out;
 }
@@ -1213,6 +1359,66 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
     __syncthreads();
 }
 
+// One tile of FFT combine butterflies (the combine maps of an epoch laid out
+// back to back, EXPAND_TILE butterflies a tile): butterfly k of the combine
+// of block [dst, dst + 2h) pairs X[dst + k] with X[dst + h + k], so
+// consecutive threads touch consecutive points.
+template <int BS>
+__device__ void fft_combine_tile(const Conf &c, Smem<BS> &sm, uint32_t t, uint32_t nd, uint32_t ne, uint32_t nt) {
+    constexpr uint32_t EPT = EXPAND_TILE / BS;
+    const uint32_t g0 = t * EXPAND_TILE, g1 = min(g0 + EXPAND_TILE, ne);
+    const uint32_t dfirst = c.me_tfd[t];
+    const uint32_t dlast = (t + 1u < nt) ? c.me_tfd[t + 1u] : nd - 1u;
+    const uint32_t nloc = dlast - dfirst + 1u;
+    for (uint32_t k = threadIdx.x; k < nloc; k += BS) {
+        sm.u.ex.base[k] = c.me_base[dfirst + k];
+        sm.u.ex.v[k] = c.me_v[dfirst + k];
+        sm.u.ex.src[k] = c.me_src[dfirst + k];
+    }
+    __syncthreads();
+    // FFT_CHUNK butterflies per thread in flight at a time: their loads first, then the arithmetic
+    constexpr uint32_t CH = EPT < FFT_CHUNK ? EPT : FFT_CHUNK;
+    float2 *X = c.rp.fX;
+    for (uint32_t j0 = 0; j0 < EPT; j0 += CH) {
+        uint32_t pe[CH], kk[CH], lg[CH];
+#pragma unroll
+        for (uint32_t j = 0; j < CH; ++j) {
+            const uint32_t g = g0 + (j0 + j) * BS + threadIdx.x;
+            pe[j] = 0xFFFFFFFFu;
+            kk[j] = 0u;
+            lg[j] = 1u;
+            if (g < g1) {
+                uint32_t lo = 0, hi = nloc;
+                while (hi - lo > 1u) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (sm.u.ex.base[mid] <= g) lo = mid;
+                    else hi = mid;
+                }
+                kk[j] = g - sm.u.ex.base[lo];
+                lg[j] = sm.u.ex.src[lo];
+                pe[j] = sm.u.ex.v[lo] + kk[j];
+            }
+        }
+        float2 e[CH], o[CH];
+#pragma unroll
+        for (uint32_t j = 0; j < CH; ++j) {
+            if (pe[j] != 0xFFFFFFFFu) {
+                e[j] = X[pe[j]];
+                o[j] = X[pe[j] + (1u << (lg[j] - 1u))];
+            }
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < CH; ++j) {
+            if (pe[j] != 0xFFFFFFFFu) {
+                fft_bfly(e[j], o[j], fft_twiddle(kk[j], lg[j]));
+                X[pe[j]] = e[j];
+                X[pe[j] + (1u << (lg[j] - 1u))] = o[j];
+            }
+        }
+    }
+    __syncthreads();  // the descriptor copy is reused by the next tile
+}
+
 // The map phase of epoch e, after the partition sub-phase: leaf sorts one
 // warp per leaf, merge tiles one block per tile, then the expansion tiles.
 template <int BS, uint32_t PM>
@@ -1238,11 +1444,20 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
         merge_phase<BS>(c, ctl, sm, nt1, nd1, job_params, job_stride);
       }
     }
-    if constexpr ((PM & (PM_BFS | PM_SSSP)) != 0u) {
+    if constexpr ((PM & (PM_BFS | PM_SSSP | PM_FFT)) != 0u) {
+        const bool fft = (PM & PM_FFT) != 0u && ((PM & (PM_BFS | PM_SSSP)) == 0u || c.rp.program == TREES_PROG_FFT);
         const bool sssp = (PM & PM_BFS) == 0u || ((PM & PM_SSSP) != 0u && c.rp.program == TREES_PROG_SSSP);
         for (uint32_t t = blockIdx.x; t < nt2; t += gridDim.x) {
-            if (sssp) relax_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e);
-            else expand_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e);
+            if constexpr ((PM & PM_FFT) != 0u) {
+                if (fft) {
+                    fft_combine_tile<BS>(c, sm, t, nd2, ne2, nt2);
+                    continue;
+                }
+            }
+            if constexpr ((PM & (PM_BFS | PM_SSSP)) != 0u) {
+                if (sssp) relax_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e);
+                else expand_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e);
+            }
         }
     }
 }
