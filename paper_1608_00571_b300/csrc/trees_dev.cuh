@@ -44,7 +44,8 @@ constexpr uint32_t SMP_SHIFT = 6;               // mergesort splitter samples: e
 constexpr int MCHUNK = 64;                      // merge tiles a block resolves at once
 constexpr unsigned long long CTR_LOW_MASK = (1ull << 40) - 1;  // map counters: (descs << 40) | units
 
-enum MapKind : uint32_t { MAP_LEAF_SORT = 1, MAP_MERGE = 2, MAP_EXPAND = 3 };
+// MAP_FFT: the combines of an FFT epoch; they need no descriptors (fft_combine_map)
+enum MapKind : uint32_t { MAP_LEAF_SORT = 1, MAP_MERGE = 2, MAP_EXPAND = 3, MAP_FFT = 4 };
 constexpr int TPT_MAX = 4;                      // largest number of slots a thread takes per tile
 constexpr int NBLK_STATS = 8192;                // per-block statistics slots
 
@@ -79,9 +80,8 @@ struct Conf {
     uint32_t cap;
     // tiled map list: one descriptor per map operation, `units` tiles each
     uint32_t *mt_kind, *mt_a, *mt_b, *mt_c, *mt_job, *mt_tilebase, *mt_split;
-    // element map list (BFS / SSSP expansion, FFT combine): one descriptor per vertex, one unit
-    // per edge, me_v = the vertex's first adjacency index, me_src = the vertex; or one descriptor
-    // per combine, one unit per butterfly, me_v = the output block, me_src = log2 of its size
+    // element map list (BFS / SSSP expansion): one descriptor per vertex, one unit per edge;
+    // me_v = the vertex's first adjacency index, me_src = the vertex
     uint32_t *me_v, *me_base, *me_job, *me_tfd, *me_src;
     uint32_t mcap;
     trees_epoch_t *trace;

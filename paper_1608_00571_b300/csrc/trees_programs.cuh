@@ -281,11 +281,9 @@ __device__ __forceinline__ void plan_task(const Conf &c, const RunParams &rp, Pl
             return;
         }
         if (p.t == TREES_TASK_FFT_COMBINE) {
-            const uint32_t lgm = rp.lgn - a1, dst = fft_block(a0, a1, rp.lgn);
+            const uint32_t lgm = rp.lgn - a1;
             if ((1u << lgm) > rp.cutoff) {  // a map over its 2^(lgm-1) butterflies
-                p.m = MAP_EXPAND;
-                p.a0 = dst;
-                p.a1 = lgm;
+                p.m = MAP_FFT;
                 p.n = 1u << (lgm - 1u);
             }
             c.code[s] = 0u;
@@ -326,9 +324,11 @@ __device__ __forceinline__ void fft_task_body(const RunParams &rp, const Plan &p
 
 // Step 2: write the children into [child, child + n) for epoch CEN+1 and turn
 // the task into its join continuation.  Returns 1 if it joined.
+// fbase: the first slot of the epoch's fork range (the FFT places its
+// children by their point offset, see below).
 template <uint32_t PM>
 __device__ __forceinline__ uint32_t commit_task(const Conf &c, const RunParams &rp, const Plan &p, uint32_t cen,
-                                                 uint32_t child) {
+                                                 uint32_t child, uint32_t fbase = 0u) {
     const uint32_t s = p.s;
     const uint32_t fe = enc(cen + 1u, 0u);
     if constexpr ((PM & PM_FIB) != 0u) {
@@ -376,13 +376,20 @@ __device__ __forceinline__ uint32_t commit_task(const Conf &c, const RunParams &
         }
     }
     if constexpr ((PM & PM_FFT) != 0u) {
+        // Every task of an FFT epoch has the same depth d and forks two, so the
+        // epoch forks exactly the 2^(d+1) tasks of depth d+1 into
+        // [fbase, fbase + 2^(d+1)); child o' goes to slot fbase + o'.  Slot order
+        // is then point order, and the leaves' strided loads are coalesced
+        // (x[o + j 2^d] for consecutive o).  `child` (this task's share of the
+        // reservation) is not needed: the reservation covers the same range.
         if (p.t == TREES_TASK_FFT) {  // even-numbered points, then odd-numbered; join the combine (o, d)
-            c.code[child] = fe + TREES_TASK_FFT;
-            c.a0[child] = p.a0;
-            c.a1[child] = p.a1 + 1u;
-            c.code[child + 1] = fe + TREES_TASK_FFT;
-            c.a0[child + 1] = p.a0 + (1u << p.a1);
-            c.a1[child + 1] = p.a1 + 1u;
+            const uint32_t c0 = fbase + p.a0, c1 = c0 + (1u << p.a1);
+            c.code[c0] = fe + TREES_TASK_FFT;
+            c.a0[c0] = p.a0;
+            c.a1[c0] = p.a1 + 1u;
+            c.code[c1] = fe + TREES_TASK_FFT;
+            c.a0[c1] = p.a0 + (1u << p.a1);
+            c.a1[c1] = p.a1 + 1u;
             c.code[s] = enc(cen, TREES_TASK_FFT_COMBINE);
             return 1u;
         }
@@ -415,7 +422,7 @@ __device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan (&p)
 #pragma unroll
     for (int k = 0; k < TPT; ++k) {
         if (p[k].m == MAP_LEAF_SORT || p[k].m == MAP_MERGE) qa += (1ull << 40) | p[k].n;
-        else if (p[k].m == MAP_EXPAND) qb += (1ull << 40) | p[k].n;
+        else if (p[k].m == MAP_EXPAND || p[k].m == MAP_FFT) qb += (1ull << 40) | p[k].n;
     }
     unsigned long long ea, eb, ta, tb;
     block_scan_u64x2<BS>(qa, qb, &ea, &eb, &ta, &tb, sm);
@@ -466,11 +473,12 @@ __device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan (&p)
             uint32_t b = (uint32_t)(ebase + (eb & CTR_LOW_MASK));
 #pragma unroll
             for (int k = 0; k < TPT; ++k) {
+                if (p[k].m == MAP_FFT) acc.maps++;  // counted; fft_combine_map needs no descriptor
                 if (p[k].m != MAP_EXPAND) continue;
                 c.me_v[di] = p[k].a0;
                 c.me_base[di] = b;
                 c.me_job[di] = job;
-                c.me_src[di] = p[k].a1;  // the vertex (SSSP reads its distance); FFT: log2 block size
+                c.me_src[di] = p[k].a1;  // the vertex (SSSP reads its distance)
                 for (uint32_t t = (b + EXPAND_TILE - 1u) / EXPAND_TILE; t * EXPAND_TILE < b + p[k].n; ++t)
                     c.me_tfd[t] = di;
                 acc.maps++;
@@ -635,7 +643,7 @@ __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> 
             uint32_t kbase = base + b0;
 #pragma unroll
             for (int k = 0; k < TPT; ++k) {
-                if (nf[k]) joined += commit_task<PM>(c, c.rp, p[k], cen, kbase + ex[k]);
+                if (nf[k]) joined += commit_task<PM>(c, c.rp, p[k], cen, kbase + ex[k], base);
                 kbase += tot[k];
             }
         }
@@ -1359,64 +1367,43 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
     __syncthreads();
 }
 
-// One tile of FFT combine butterflies (the combine maps of an epoch laid out
-// back to back, EXPAND_TILE butterflies a tile): butterfly k of the combine
-// of block [dst, dst + 2h) pairs X[dst + k] with X[dst + h + k], so
-// consecutive threads touch consecutive points.
+// The combine maps of one FFT epoch as one flat array of butterflies.  The
+// epoch's range holds all 2^d tasks of depth d, each a combine of 2^lgm
+// points (lgm = log2 N - d), so nd = 2^d and there are N/2 butterflies:
+// butterfly g is butterfly k = g mod h of the combine of task o = g / h,
+// h = 2^(lgm-1), which pairs X[blk + k] with X[blk + h + k], blk the block of
+// (o, d).  Consecutive threads take consecutive butterflies (coalesced, a
+// warp spans at most 32 / h blocks); each thread keeps FFT_CHUNK of them in
+// flight, their loads first.
 template <int BS>
-__device__ void fft_combine_tile(const Conf &c, Smem<BS> &sm, uint32_t t, uint32_t nd, uint32_t ne, uint32_t nt) {
-    constexpr uint32_t EPT = EXPAND_TILE / BS;
-    const uint32_t g0 = t * EXPAND_TILE, g1 = min(g0 + EXPAND_TILE, ne);
-    const uint32_t dfirst = c.me_tfd[t];
-    const uint32_t dlast = (t + 1u < nt) ? c.me_tfd[t + 1u] : nd - 1u;
-    const uint32_t nloc = dlast - dfirst + 1u;
-    for (uint32_t k = threadIdx.x; k < nloc; k += BS) {
-        sm.u.ex.base[k] = c.me_base[dfirst + k];
-        sm.u.ex.v[k] = c.me_v[dfirst + k];
-        sm.u.ex.src[k] = c.me_src[dfirst + k];
-    }
-    __syncthreads();
-    // FFT_CHUNK butterflies per thread in flight at a time: their loads first, then the arithmetic
-    constexpr uint32_t CH = EPT < FFT_CHUNK ? EPT : FFT_CHUNK;
+__device__ void fft_combine_map(const Conf &c, uint32_t nd, uint32_t ne) {
+    const uint32_t d = 31u - (uint32_t)__clz(nd), lgn = c.rp.lgn, lh = lgn - d - 1u;
+    const uint32_t hmask = (1u << lh) - 1u, stride = gridDim.x * BS;
     float2 *X = c.rp.fX;
-    for (uint32_t j0 = 0; j0 < EPT; j0 += CH) {
-        uint32_t pe[CH], kk[CH], lg[CH];
+    for (uint32_t g0 = blockIdx.x * BS + threadIdx.x; g0 < ne; g0 += stride * FFT_CHUNK) {
+        uint32_t pe[FFT_CHUNK];
+        float2 e[FFT_CHUNK], o[FFT_CHUNK];
 #pragma unroll
-        for (uint32_t j = 0; j < CH; ++j) {
-            const uint32_t g = g0 + (j0 + j) * BS + threadIdx.x;
-            pe[j] = 0xFFFFFFFFu;
-            kk[j] = 0u;
-            lg[j] = 1u;
-            if (g < g1) {
-                uint32_t lo = 0, hi = nloc;
-                while (hi - lo > 1u) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (sm.u.ex.base[mid] <= g) lo = mid;
-                    else hi = mid;
-                }
-                kk[j] = g - sm.u.ex.base[lo];
-                lg[j] = sm.u.ex.src[lo];
-                pe[j] = sm.u.ex.v[lo] + kk[j];
-            }
+        for (uint32_t j = 0; j < FFT_CHUNK; ++j) {
+            const uint32_t g = g0 + j * stride;
+            pe[j] = g < ne ? fft_block(g >> lh, d, lgn) + (g & hmask) : 0xFFFFFFFFu;
         }
-        float2 e[CH], o[CH];
 #pragma unroll
-        for (uint32_t j = 0; j < CH; ++j) {
+        for (uint32_t j = 0; j < FFT_CHUNK; ++j) {
             if (pe[j] != 0xFFFFFFFFu) {
                 e[j] = X[pe[j]];
-                o[j] = X[pe[j] + (1u << (lg[j] - 1u))];
+                o[j] = X[pe[j] + (1u << lh)];
             }
         }
 #pragma unroll
-        for (uint32_t j = 0; j < CH; ++j) {
+        for (uint32_t j = 0; j < FFT_CHUNK; ++j) {
             if (pe[j] != 0xFFFFFFFFu) {
-                fft_bfly(e[j], o[j], fft_twiddle(kk[j], lg[j]));
+                fft_bfly(e[j], o[j], fft_twiddle((g0 + j * stride) & hmask, lh + 1u));
                 X[pe[j]] = e[j];
-                X[pe[j] + (1u << (lg[j] - 1u))] = o[j];
+                X[pe[j] + (1u << lh)] = o[j];
             }
         }
     }
-    __syncthreads();  // the descriptor copy is reused by the next tile
 }
 
 // The map phase of epoch e, after the partition sub-phase: leaf sorts one
@@ -1446,15 +1433,15 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
     }
     if constexpr ((PM & (PM_BFS | PM_SSSP | PM_FFT)) != 0u) {
         const bool fft = (PM & PM_FFT) != 0u && ((PM & (PM_BFS | PM_SSSP)) == 0u || c.rp.program == TREES_PROG_FFT);
-        const bool sssp = (PM & PM_BFS) == 0u || ((PM & PM_SSSP) != 0u && c.rp.program == TREES_PROG_SSSP);
-        for (uint32_t t = blockIdx.x; t < nt2; t += gridDim.x) {
-            if constexpr ((PM & PM_FFT) != 0u) {
-                if (fft) {
-                    fft_combine_tile<BS>(c, sm, t, nd2, ne2, nt2);
-                    continue;
-                }
+        if constexpr ((PM & PM_FFT) != 0u) {
+            if (fft) {
+                if (nd2) fft_combine_map<BS>(c, nd2, ne2);
+                return;
             }
-            if constexpr ((PM & (PM_BFS | PM_SSSP)) != 0u) {
+        }
+        if constexpr ((PM & (PM_BFS | PM_SSSP)) != 0u) {
+            const bool sssp = (PM & PM_BFS) == 0u || ((PM & PM_SSSP) != 0u && c.rp.program == TREES_PROG_SSSP);
+            for (uint32_t t = blockIdx.x; t < nt2; t += gridDim.x) {
                 if (sssp) relax_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e);
                 else expand_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e);
             }
