@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "tasks/sec & µs/epoch (fib, sort, BFS); batched jobs/sec, p99 latency vs plain"
 FIB_N = 34
 FLUSH_BYTES = 256 << 20  # > 126 MB L2
-FFT_LG, FFT_LEAF, FFT_CUTOFF = 24, 16, 64  # 2^24 points; 16-point leaves; combines of <= 64 points in-task
+FFT_LG, FFT_LEAF, FFT_CUTOFF = 24, 16, 0  # 2^24 points; 16-point leaves; every combine a map
 SSSP_SLOTS_PER_VERTEX = 3  # task-vector slots per vertex for SSSP (measured 1.10-1.12 relax tasks per vertex)
 
 
@@ -699,14 +699,15 @@ def main():
                                                  "frac": ab5 / (m5 / 1000) / 1e9 / hbm_peak,
                                                  "algorithmic_bytes": ab5, "note": "lower bound (edges once per vertex)"}}
         del rp, cl, lv, wt, dist_t, sched_t
-        # FFT of 2^24 complex fp32 points (Sec. 6.2, Fig. 6): radix-2 tasks, combines above 64 points as maps
+        # FFT of 2^24 complex fp32 points (Sec. 6.2, Fig. 6): radix-2 tasks, every combine a map
         n6 = 1 << FFT_LG
         x6 = gen.signal(1, n6)
         xi6 = torch.from_numpy(x6.view(np.float32)).cuda()
         xo6 = torch.empty_like(xi6)
         j6 = T.make_job(T.TREES_PROG_FFT, n=n6, leaf=FFT_LEAF, cutoff=FFT_CUTOFF, fft_in=xi6, fft_out=xo6)
         cap6 = T.trees_job_slots(j6)[0]
-        c6 = T.trees_create(cap6, tune(j6, cap6, f"fft:n=2^{FFT_LG}:leaf={FFT_LEAF}:cutoff={FFT_CUTOFF}"))
+        cfg6 = tune(j6, cap6, f"fft:n=2^{FFT_LG}:leaf={FFT_LEAF}:cutoff={FFT_CUTOFF}")
+        c6 = T.trees_create(cap6, cfg6)
         t6 = timed_runs(T, torch, c6, j6, 5, 1, stream, flush)
         s6 = T.trees_stats(c6)
         T.trees_destroy(c6)
@@ -726,7 +727,10 @@ def main():
             "leaf": FFT_LEAF, "cutoff": FFT_CUTOFF, "dtype": "complex fp32", "combine_levels": lv6,
             "sampled_outputs_within_bound": ok6,
             "roofline": {"bound": "hbm", "achieved": ab6 / (m6 / 1000) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": ab6 / (m6 / 1000) / 1e9 / hbm_peak, "algorithmic_bytes": ab6}}
+                         "frac": ab6 / (m6 / 1000) / 1e9 / hbm_peak, "algorithmic_bytes": ab6,
+                         "traffic": ncu_traffic(f"fft{FFT_LG}_persistent_{cfg6.block_size}x{cfg6.tasks_per_thread}"
+                                                if cfg6.scheduler == T.TREES_SCHED_PERSISTENT else "none"),
+                         "kernel": f"k_persistent<{cfg6.block_size},{cfg6.tasks_per_thread},PM_FFT>"}}
         del xi6, xo6
         line["workloads"] = workloads
         # graph-relaunch and host-loop schedulers on the headline workload
