@@ -114,40 +114,78 @@ __host__ __device__ constexpr int fft_rev(int j, int bits) {
     return bits == 0 ? 0 : ((j & 1) << (bits - 1)) | fft_rev(j >> 1, bits - 1);
 }
 
-// A leaf of K = 2^LK points in registers: its points are loaded in
-// bit-reversed order, so the LK butterfly stages (the combines of the
-// 2-, 4-, ..., K-point sub-transforms, in the same arithmetic as the combine
-// tasks) leave its transform in natural order.
-template <int LK>
-__device__ __forceinline__ void fft_leaf_k(const float2 *__restrict__ x, float2 *__restrict__ X, uint32_t o,
-                                           uint32_t d, uint32_t dst) {
-    constexpr int K = 1 << LK;
-    float2 a[K];
+// The leaves among one thread's TPT slots of a tile, K = 2^LK points each,
+// in registers: the points of G leaves are loaded together (their loads in
+// flight at once), then each leaf is transformed and stored.  Register r of
+// a leaf holds its point of index rev(r) (LK-bit reversal), so the LK
+// butterfly stages (the combines of its 2-, 4-, ..., K-point
+// sub-transforms, in the same arithmetic as the combine tasks) leave the
+// transform in natural order.
+template <int LK, int TPT>
+__device__ __forceinline__ void fft_leaves_k(const float2 *__restrict__ x, float2 *__restrict__ X, uint32_t lgn,
+                                             const Plan (&p)[TPT], uint32_t d) {
+    constexpr int K = 1 << LK, G = LK >= 4 ? 1 : (TPT < 2 ? TPT : 2);  // at most 16 points in flight per thread
 #pragma unroll
-    for (int j = 0; j < K; ++j) a[fft_rev(j, LK)] = x[o + ((uint32_t)j << d)];
+    for (int k0 = 0; k0 < TPT; k0 += G) {
+        float2 a[G][K];
+        bool lf[G];
 #pragma unroll
-    for (int lm = 1; lm <= LK; ++lm) {
-        const int h = 1 << (lm - 1);
+        for (int g = 0; g < G; ++g) {
+            lf[g] = p[k0 + g].t == TREES_TASK_FFT && p[k0 + g].n == 0u;
+            if (lf[g]) {
 #pragma unroll
-        for (int k = 0; k < h; ++k) {
-            const float2 w = fft_twiddle((uint32_t)k, (uint32_t)lm);
+                for (int r = 0; r < K; ++r) a[g][r] = x[p[k0 + g].a0 + ((uint32_t)fft_rev(r, LK) << d)];
+            }
+        }
 #pragma unroll
-            for (int g = 0; g < K; g += 2 * h) fft_bfly(a[g + k], a[g + k + h], w);
+        for (int g = 0; g < G; ++g) {
+            if (!lf[g]) continue;
+#pragma unroll
+            for (int lm = 1; lm <= LK; ++lm) {
+                const int h = 1 << (lm - 1);
+#pragma unroll
+                for (int k = 0; k < h; ++k) {
+                    const float2 w = fft_twiddle((uint32_t)k, (uint32_t)lm);
+#pragma unroll
+                    for (int q = 0; q < K; q += 2 * h) fft_bfly(a[g][q + k], a[g][q + k + h], w);
+                }
+            }
+            const uint32_t dst = fft_block(p[k0 + g].a0, d, lgn);
+#pragma unroll
+            for (int k = 0; k < K; ++k) X[dst + k] = a[g][k];
         }
     }
-#pragma unroll
-    for (int k = 0; k < K; ++k) X[dst + k] = a[k];
 }
 
-static __device__ __noinline__ void fft_leaf(const float2 *x, float2 *X, uint32_t o, uint32_t d, uint32_t lgn) {
-    const uint32_t dst = fft_block(o, d, lgn);
+// All leaves of an epoch have the same depth d, so one leaf size serves the thread.
+template <int TPT>
+__device__ __forceinline__ void fft_leaves(const float2 *x, float2 *X, uint32_t lgn, const Plan (&p)[TPT]) {
+    uint32_t d = 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < TPT; ++k)
+        if (p[k].t == TREES_TASK_FFT && p[k].n == 0u) d = p[k].a1;
+    if (d == 0xFFFFFFFFu) return;
     switch (lgn - d) {
-    case 0: X[dst] = x[o]; break;
-    case 1: fft_leaf_k<1>(x, X, o, d, dst); break;
-    case 2: fft_leaf_k<2>(x, X, o, d, dst); break;
-    case 3: fft_leaf_k<3>(x, X, o, d, dst); break;
-    default: fft_leaf_k<4>(x, X, o, d, dst); break;
+    case 0:  // one point: the transform is the point
+#pragma unroll
+        for (int k = 0; k < TPT; ++k)
+            if (p[k].t == TREES_TASK_FFT && p[k].n == 0u) X[fft_block(p[k].a0, d, lgn)] = x[p[k].a0];
+        break;
+    case 1: fft_leaves_k<1, TPT>(x, X, lgn, p, d); break;
+    case 2: fft_leaves_k<2, TPT>(x, X, lgn, p, d); break;
+    case 3: fft_leaves_k<3, TPT>(x, X, lgn, p, d); break;
+    default: fft_leaves_k<4, TPT>(x, X, lgn, p, d); break;
     }
+}
+
+// One leaf, out of line (see fft_task_bodies).
+static __device__ __noinline__ void fft_leaf_slot(const float2 *x, float2 *X, uint32_t o, uint32_t d, uint32_t lgn) {
+    Plan q[1];
+    q[0].t = TREES_TASK_FFT;
+    q[0].n = 0u;
+    q[0].a0 = o;
+    q[0].a1 = d;
+    fft_leaves<1>(x, X, lgn, q);
 }
 
 // A combine of 2^lgm points done by its own task (the paper's FFT).
@@ -314,12 +352,24 @@ __device__ __forceinline__ void plan_task(const Conf &c, const RunParams &rp, Pl
 
 __device__ __forceinline__ uint32_t forks_of(const Plan &p) { return p.m ? 0u : p.n; }
 
-// The work of an FFT leaf or of a combine below the cutoff (both emit and
-// fork nothing, so it can follow the tile's forks).
-__device__ __forceinline__ void fft_task_body(const RunParams &rp, const Plan &p) {
-    if (p.t == TREES_TASK_FFT && p.n == 0u) fft_leaf(rp.fx, rp.fX, p.a0, p.a1, rp.lgn);
-    else if (p.t == TREES_TASK_FFT_COMBINE && p.m == 0u)
-        fft_combine_task(rp.fX, fft_block(p.a0, p.a1, rp.lgn), rp.lgn - p.a1);
+// The work of FFT leaves and of combines below the cutoff (both emit and
+// fork nothing, so it can follow the tile's forks).  The FFT's own kernel
+// with one slot per thread runs its leaf inline (spill-free at 128
+// registers); the others call the leaves out of line, so that the leaf's
+// registers do not weigh on the rest of the kernel.
+template <uint32_t PM, int TPT>
+__device__ __forceinline__ void fft_task_bodies(const RunParams &rp, const Plan (&p)[TPT]) {
+    if constexpr (PM == PM_FFT && TPT == 1) {
+        fft_leaves<TPT>(rp.fx, rp.fX, rp.lgn, p);
+    } else {
+#pragma unroll 1
+        for (int k = 0; k < TPT; ++k)
+            if (p[k].t == TREES_TASK_FFT && p[k].n == 0u) fft_leaf_slot(rp.fx, rp.fX, p[k].a0, p[k].a1, rp.lgn);
+    }
+#pragma unroll
+    for (int k = 0; k < TPT; ++k)
+        if (p[k].t == TREES_TASK_FFT_COMBINE && p[k].m == 0u)
+            fft_combine_task(rp.fX, fft_block(p[k].a0, p[k].a1, rp.lgn), rp.lgn - p[k].a1);
 }
 
 // Step 2: write the children into [child, child + n) for epoch CEN+1 and turn
@@ -656,10 +706,7 @@ __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> 
         if (anymap) map_alloc<BS, TPT>(c, ctl, sm, p, cen, ep, e, 0u, acc);
     }
     if constexpr ((PM & PM_FFT) != 0u) {
-        if (PM == PM_FFT || c.rp.program == TREES_PROG_FFT) {
-#pragma unroll 1
-            for (int k = 0; k < TPT; ++k) fft_task_body(c.rp, p[k]);
-        }
+        if (PM == PM_FFT || c.rp.program == TREES_PROG_FFT) fft_task_bodies<PM, TPT>(c.rp, p);
     }
     return out;
 }
