@@ -27,6 +27,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "trees_user.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -73,6 +75,7 @@ extern "C" {
 #define TREES_PROG_PREORDER 6
 #define TREES_PROG_SSSP 7
 #define TREES_PROG_FFT 8
+#define TREES_PROG_USER 9        /* a user task program (trees_program.cuh), run by its own kernel */
 
 /* ------------------------------------------------------------ schedulers */
 #define TREES_SCHED_PERSISTENT 0 /* one cooperative launch; one grid barrier per epoch */
@@ -127,6 +130,18 @@ size_t trees_capacity(const trees_ctx *ctx);
 int trees_geometry(const trees_ctx *ctx, int32_t *grid_blocks, int32_t *block_size, int32_t *sms);
 
 /* ------------------------------------------------------------ one job */
+/* A user task program compiled against trees_program.cuh by
+ * TREES_DEFINE_PROGRAM: op TREES_USER_OP_OCCUPANCY writes to *out how many
+ * blocks of block_size threads of its persistent kernel fit on one SM; op
+ * TREES_USER_OP_LAUNCH launches that kernel cooperatively on `grid` blocks
+ * with the kernel arguments `args` on `stream`.  Returns a cudaError_t value
+ * (0 = success).  The program's kernels live in the caller's module; the
+ * library calls this function instead of launching them itself. */
+typedef int (*trees_program_fn)(int32_t op, int32_t block_size, int32_t tasks_per_thread, void **args, int32_t grid,
+                                void *stream, int32_t *out);
+#define TREES_USER_OP_OCCUPANCY 0
+#define TREES_USER_OP_LAUNCH 1
+
 typedef struct {
     int32_t program;          /* TREES_PROG_* */
     uint32_t n;               /* fib: n; N-Queens: board size (1..16); mergesort: number of keys;
@@ -154,13 +169,20 @@ typedef struct {
                                  8-byte aligned; read only */
     float *fft_out;           /* FFT: device output [2n] floats, X[k] = sum_j x[j] exp(-2 pi i j k / n);
                                  8-byte aligned, must not overlap fft_in */
+    trees_program_fn user_program;  /* user program: its launcher (persistent scheduler only) */
+    uint32_t user_type, user_a0, user_a1;  /* user program: the root task, type 1..TREES_NUM_TASK_TYPES */
+    uint32_t user_pad;
+    void *user_ptr[TREES_USER_PARAMS];     /* user program: parameters passed to its device functions */
+    uint64_t user_val[TREES_USER_PARAMS];
 } trees_job_t;
 
 /* Sec. 5.2.1 initialisation + the epoch loop: writes the job's root task
  * into TV entry 0 for epoch 0 and runs epochs until the range stack is empty.
  * Asynchronous on `stream` for the persistent and graph schedulers; the host
- * loop scheduler returns when the run is over.  Errors before launch:
- * INVALID_ARG (bad job), BUSY, CUDA. */
+ * loop scheduler returns when the run is over.  A TREES_PROG_USER job runs
+ * its program's own persistent kernel (user_program; the graph and host-loop
+ * schedulers, whose kernels are compiled for the built-in programs, reject
+ * it).  Errors before launch: INVALID_ARG (bad job), BUSY, CUDA. */
 int trees_run(trees_ctx *ctx, const trees_job_t *job, void *stream);
 
 /* Waits for the context's last run and returns its status (TREES_OK or the

@@ -274,3 +274,47 @@ def tvm_run(program: int, *, fib_n: int = 0, fib_cutoff: int = 0, keys: np.ndarr
     out["stats"] = {f: int(getattr(st, f)) for f, _ in _Stats._fields_ if f != "err"}
     out["trace"] = arr
     return out
+
+
+# ------------------------------------------------------------ the user-program example
+
+def chunk_sum_tree(n: int, chunk: int, arity: int):
+    """The task tree of the chunked-sum example program, by its definition:
+    SUM(lo, hi) over a range of at most ``chunk`` keys is a leaf (one map
+    unit, or an emit of 0 when empty); a longer range has
+    k = min(arity, ceil(len / chunk)) children over the parts
+    [lo + len*i//k, lo + len*(i+1)//k) and a join.  Returns the counts and
+    the per-epoch trace the task vector machine gives it: the fork levels
+    0..D (every task of depth d in one range), then the join ranges revisited
+    from depth D-1 back to 0 (Sec. 4.3)."""
+    levels = []  # per depth: list of (lo, hi)
+
+    def walk(lo, hi, d):
+        while len(levels) <= d:
+            levels.append([])
+        levels[d].append((lo, hi))
+        ln = hi - lo
+        if ln > chunk:
+            k = min(arity, -(-ln // chunk))
+            for i in range(k):
+                walk(lo + ln * i // k, lo + ln * (i + 1) // k, d + 1)
+
+    walk(0, n, 0)
+    D = len(levels) - 1
+    internal = [sum(1 for lo, hi in lv if hi - lo > chunk) for lv in levels]
+    maps = [sum(1 for lo, hi in lv if 0 < hi - lo <= chunk) for lv in levels]
+    starts = [0]
+    for lv in levels:
+        starts.append(starts[-1] + len(lv))
+    trace = []
+    for d in range(D + 1):  # fork levels
+        forks = len(levels[d + 1]) if d < D else 0
+        trace.append({"cen": d, "lo": starts[d], "hi": starts[d + 1], "valid": len(levels[d]), "forks": forks,
+                      "joined": int(internal[d] > 0), "maps": maps[d]})
+    for d in range(D - 1, -1, -1):  # join ranges, deepest first
+        trace.append({"cen": d, "lo": starts[d], "hi": starts[d + 1], "valid": internal[d], "forks": 0,
+                      "joined": 0, "maps": 0})
+    stats = {"epochs": len(trace), "tasks": sum(t["valid"] for t in trace), "joins": sum(internal),
+             "maps": sum(maps), "forks": sum(len(lv) for lv in levels[1:]), "peak_slots": starts[-1],
+             "final_slots": 0}
+    return stats, trace

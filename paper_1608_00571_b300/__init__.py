@@ -37,6 +37,9 @@ TREES_PROG_POSTORDER = 5
 TREES_PROG_PREORDER = 6
 TREES_PROG_SSSP = 7
 TREES_PROG_FFT = 8
+TREES_PROG_USER = 9
+TREES_USER_PARAMS = 4
+TREES_NUM_TASK_TYPES = 13  # task types 1..13; a user program's types share this range
 
 # schedulers
 TREES_SCHED_PERSISTENT = 0
@@ -64,7 +67,10 @@ class trees_job_t(ctypes.Structure):
                 ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("level", ctypes.c_void_p),
                 ("nv", ctypes.c_int32), ("left", ctypes.c_void_p), ("right", ctypes.c_void_p),
                 ("visit_epoch", ctypes.c_void_p), ("weight", ctypes.c_void_p), ("dist", ctypes.c_void_p),
-                ("sched", ctypes.c_void_p), ("fft_in", ctypes.c_void_p), ("fft_out", ctypes.c_void_p)]
+                ("sched", ctypes.c_void_p), ("fft_in", ctypes.c_void_p), ("fft_out", ctypes.c_void_p),
+                ("user_program", ctypes.c_void_p), ("user_type", ctypes.c_uint32), ("user_a0", ctypes.c_uint32),
+                ("user_a1", ctypes.c_uint32), ("user_pad", ctypes.c_uint32),
+                ("user_ptr", ctypes.c_void_p * 4), ("user_val", ctypes.c_uint64 * 4)]
 
 
 class trees_stats_t(ctypes.Structure):
@@ -233,7 +239,8 @@ def trees_geometry(ctx):
 
 def make_job(program: int, n: int = 0, cutoff: int = 0, leaf: int = 0, keys=None, scratch=None, row_ptr=None,
              col=None, level=None, nv: int = 0, left=None, right=None, visit_epoch=None, weight=None, dist=None,
-             sched=None, fft_in=None, fft_out=None) -> trees_job_t:
+             sched=None, fft_in=None, fft_out=None, user_program=None, user_type: int = 0, user_a0: int = 0,
+             user_a1: int = 0, user_ptr=(), user_val=()) -> trees_job_t:
     j = trees_job_t()
     j.program = program
     j.n = n
@@ -253,6 +260,16 @@ def make_job(program: int, n: int = 0, cutoff: int = 0, leaf: int = 0, keys=None
     j.sched = _ptr(sched)
     j.fft_in = _ptr(fft_in)
     j.fft_out = _ptr(fft_out)
+    if user_program is not None:  # a function of a user program library, or its address
+        j.user_program = user_program if isinstance(user_program, int) else ctypes.cast(user_program,
+                                                                                          ctypes.c_void_p).value
+    j.user_type = user_type
+    j.user_a0 = user_a0
+    j.user_a1 = user_a1
+    for i, v in enumerate(user_ptr):
+        j.user_ptr[i] = _ptr(v)
+    for i, v in enumerate(user_val):
+        j.user_val[i] = v
     return j
 
 

@@ -28,7 +28,7 @@ def sources():
 
 def _deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
-        [os.path.join(INCLUDE, "trees.h")]
+        glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
 def stale() -> bool:
@@ -70,3 +70,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 if __name__ == "__main__":
     build(force=True, verbose=True)
+
+
+def build_program(source: str, output: str, force: bool = False) -> str:
+    """Compiles a user task program (a .cu file written against
+    include/trees_program.cuh, ending in TREES_DEFINE_PROGRAM) into the
+    shared library ``output`` with the library's own flags, unless it is
+    newer than its source and the runtime headers.  Returns ``output``."""
+    deps = [source] + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*"))
+    if not force and os.path.exists(output) and all(os.path.getmtime(output) >= os.path.getmtime(d) for d in deps):
+        return output
+    tmp = output + ".tmp"
+    subprocess.check_call(["nvcc", *NVCC_FLAGS, "-I", INCLUDE, "-I", CSRC, source, "-o", tmp])
+    os.replace(tmp, output)
+    return output

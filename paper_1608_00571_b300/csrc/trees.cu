@@ -819,6 +819,18 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
         a1 = 0;
         break;
     }
+    case TREES_PROG_USER:  // its own kernel, launched through its function: persistent scheduler only
+        if (!job->user_program || job->user_type < 1u || job->user_type > (uint32_t)TREES_NUM_TASK_TYPES ||
+            x->cfg.scheduler != TREES_SCHED_PERSISTENT)
+            return TREES_ERR_INVALID_ARG;
+        for (int i = 0; i < TREES_USER_PARAMS; ++i) {
+            rp.up[i] = job->user_ptr[i];
+            rp.uv[i] = job->user_val[i];
+        }
+        type = job->user_type;
+        a0 = job->user_a0;
+        a1 = job->user_a1;
+        break;
     case TREES_PROG_POSTORDER:
     case TREES_PROG_PREORDER:
         if (job->n && (!job->left || !job->right || !job->visit_epoch)) return TREES_ERR_INVALID_ARG;
@@ -853,6 +865,20 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
     switch (x->cfg.scheduler) {
     case TREES_SCHED_PERSISTENT: {
         void *args[] = {&x->ctl, &x->conf, &x->blk};
+        if (job->program == TREES_PROG_USER) {
+            const trees_program_fn f = job->user_program;
+            int32_t occ = 0;
+            if (f(TREES_USER_OP_OCCUPANCY, x->bs, x->cfg.tasks_per_thread, nullptr, 0, stream, &occ) != 0 || occ < 1)
+                return TREES_ERR_CUDA;
+            const int per_sm = x->cfg.blocks_per_sm > 0 ? std::min(x->cfg.blocks_per_sm, (int)occ) : (int)occ;
+            const int grid = x->cfg.grid_blocks > 0 ? std::min(x->cfg.grid_blocks, x->sms * (int)occ) : x->sms * per_sm;
+            x->last_grid = grid;
+            if (f(TREES_USER_OP_LAUNCH, x->bs, x->cfg.tasks_per_thread, args, grid, stream, nullptr) != 0) {
+                cudaGetLastError();
+                return TREES_ERR_CUDA;
+            }
+            return TREES_OK;
+        }
         const void *kern = persistent_kernel(job->program, x->bs, x->cfg.tasks_per_thread);
         const int grid = kernel_grid(x, kern);
         if (!kern || grid < 1) return TREES_ERR_CUDA;

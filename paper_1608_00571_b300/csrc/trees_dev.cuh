@@ -44,8 +44,9 @@ constexpr uint32_t SMP_SHIFT = 6;               // mergesort splitter samples: e
 constexpr int MCHUNK = 64;                      // merge tiles a block resolves at once
 constexpr unsigned long long CTR_LOW_MASK = (1ull << 40) - 1;  // map counters: (descs << 40) | units
 
-// MAP_FFT: the combines of an FFT epoch; they need no descriptors (fft_combine_map)
-enum MapKind : uint32_t { MAP_LEAF_SORT = 1, MAP_MERGE = 2, MAP_EXPAND = 3, MAP_FFT = 4 };
+// MAP_FFT: the combines of an FFT epoch; they need no descriptors (fft_combine_map).
+// MAP_USER: a user program's map, one tile per unit (mt_c holds the scheduling slot).
+enum MapKind : uint32_t { MAP_LEAF_SORT = 1, MAP_MERGE = 2, MAP_EXPAND = 3, MAP_FFT = 4, MAP_USER = 5 };
 constexpr int TPT_MAX = 4;                      // largest number of slots a thread takes per tile
 constexpr int NBLK_STATS = 8192;                // per-block statistics slots
 
@@ -71,6 +72,8 @@ struct RunParams {
     const float2 *fx;          // FFT input, N complex points
     float2 *fX;                // FFT output
     uint32_t lgn;              // FFT: log2 N
+    void *up[TREES_USER_PARAMS];               // user program parameters
+    unsigned long long uv[TREES_USER_PARAMS];
 };
 
 // Read-only during a run: where everything lives.
@@ -199,6 +202,8 @@ struct Smem {
     } u;
 };
 
+static_assert(sizeof(Smem<128>::u) >= TREES_USER_SMEM_BYTES && sizeof(Smem<1024>::u) >= TREES_USER_SMEM_BYTES,
+              "a user map unit gets the shared union");
 static_assert(sizeof(Smem<256>) <= 48 * 1024 && sizeof(Smem<512>) <= 48 * 1024 && sizeof(Smem<1024>) <= 48 * 1024,
               "a block's static shared memory is limited to 48 KB");
 

@@ -50,10 +50,11 @@ __device__ __forceinline__ void trace_valid_add(const Conf &c, uint32_t e, uint3
 // threads for registers as its slots per thread grow (1024, 768, 512 threads
 // per SM for 1, 2, 4 slots: measured, each spill-free beats more resident
 // warps that spill); the FFT kernel keeps 512 (128 registers: its leaf
-// transforms and combine butterflies spill at 64); the others take what
+// transforms and combine butterflies spill at 64), and so does a user
+// program's (its device functions are unknown here); the others take what
 // they need.
 __host__ __device__ constexpr int persistent_min_blocks(int bs, uint32_t pm, int tpt) {
-    const int tps = (pm == PM_MS || pm == PM_BFS || pm == PM_SSSP) ? 1024 : pm == PM_FFT ? 512
+    const int tps = (pm == PM_MS || pm == PM_BFS || pm == PM_SSSP) ? 1024 : (pm == PM_FFT || pm == PM_USER) ? 512
                   : pm == PM_FIB ? (tpt >= 4 ? 512 : tpt == 2 ? 768 : 1024) : 0;
     return tps / bs > 0 ? tps / bs : 1;
 }
@@ -232,7 +233,7 @@ __device__ __forceinline__ uint32_t adopt_solo_state(const Conf &c, Ctl *ctl, Sm
     return sm.bc32[0];
 }
 
-template <int BS, int TPT, uint32_t PM>
+template <int BS, int TPT, uint32_t PM, typename UP = NoUserProgram>
 __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_persistent(Ctl *ctl, Conf c, unsigned long long *blk) {
     __shared__ Smem<BS> sm;
     __shared__ uint32_t sm_e;
@@ -254,20 +255,22 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
         popped = false;
         __syncthreads();
         if (sm.stop) break;
-        if (solo_range<BS, TPT, PM>(c, sm.lo, sm.hi)) {
-            if (blockIdx.x == 0) {
-                const uint32_t ne = solo_epochs<BS, TPT, PM>(c, ctl, sm, e, acc, st);
-                if (threadIdx.x == 0) sm_e = ne;
+        if constexpr ((PM & PM_MAPS) == 0u) {
+            if (solo_range<BS, TPT, PM>(c, sm.lo, sm.hi)) {
+                if (blockIdx.x == 0) {
+                    const uint32_t ne = solo_epochs<BS, TPT, PM>(c, ctl, sm, e, acc, st);
+                    if (threadIdx.x == 0) sm_e = ne;
+                }
+                if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, e % 3u)) break;
+                if (blockIdx.x != 0) {
+                    const uint32_t ne = adopt_solo_state<BS>(c, ctl, sm);
+                    if (threadIdx.x == 0) sm_e = ne;
+                }
+                __syncthreads();
+                e = sm_e - 1u;  // the loop's ++e lands on the popped epoch
+                popped = true;
+                continue;
             }
-            if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, e % 3u)) break;
-            if (blockIdx.x != 0) {
-                const uint32_t ne = adopt_solo_state<BS>(c, ctl, sm);
-                if (threadIdx.x == 0) sm_e = ne;
-            }
-            __syncthreads();
-            e = sm_e - 1u;  // the loop's ++e lands on the popped epoch
-            popped = true;
-            continue;
         }
         const uint32_t cen = sm.cen, lo = sm.lo, hi = sm.hi, base = sm.base, ep = e % 3u;
         const int mode = sm.rjoin ? LOAD_JOIN : LOAD_FRESH;
@@ -285,8 +288,8 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
         for (; t0 < hi; t0 += step) {
             const bool more = t0 + step < hi;
             if (more) tile_load<BS, TPT, PM>(c, t0 + step, hi, mode, nxt);
-            epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode, cur, solo, 0u, jr_use,
-                                    jr && more ? &nxt : nullptr);
+            epoch_tile<BS, TPT, PM, UP>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode, cur, solo, 0u, jr_use,
+                                        jr && more ? &nxt : nullptr);
             jr_use = jr && more;
             if (more) cur = nxt;
             par ^= 1;
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
                     if (stamp) st.t_pt = st.t_mp = globaltimer();
                 }
             }
-            map_phase<BS, PM>(c, ctl, sm, ep, e, cen, base, mt, me);
+            map_phase<BS, PM, UP>(c, ctl, sm, ep, e, cen, base, mt, me);
             if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, ep)) break;
             if (stamp) st.t_mp = globaltimer();
         }
@@ -321,22 +324,22 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
     }
 }
 
-// Returns k_persistent<BS, TPT, PM> for a runtime (bs, tpt), or nullptr.
-template <uint32_t PM>
+// Returns k_persistent<BS, TPT, PM, UP> for a runtime (bs, tpt), or nullptr.
+template <uint32_t PM, typename UP = NoUserProgram>
 const void *persistent_kernel_for(int bs, int tpt) {
     switch (bs * 10 + tpt) {
-    case 1281: return (const void *)k_persistent<128, 1, PM>;
-    case 1282: return (const void *)k_persistent<128, 2, PM>;
-    case 1284: return (const void *)k_persistent<128, 4, PM>;
-    case 2561: return (const void *)k_persistent<256, 1, PM>;
-    case 2562: return (const void *)k_persistent<256, 2, PM>;
-    case 2564: return (const void *)k_persistent<256, 4, PM>;
-    case 5121: return (const void *)k_persistent<512, 1, PM>;
-    case 5122: return (const void *)k_persistent<512, 2, PM>;
-    case 5124: return (const void *)k_persistent<512, 4, PM>;
-    case 10241: return (const void *)k_persistent<1024, 1, PM>;
-    case 10242: return (const void *)k_persistent<1024, 2, PM>;
-    case 10244: return (const void *)k_persistent<1024, 4, PM>;
+    case 1281: return (const void *)k_persistent<128, 1, PM, UP>;
+    case 1282: return (const void *)k_persistent<128, 2, PM, UP>;
+    case 1284: return (const void *)k_persistent<128, 4, PM, UP>;
+    case 2561: return (const void *)k_persistent<256, 1, PM, UP>;
+    case 2562: return (const void *)k_persistent<256, 2, PM, UP>;
+    case 2564: return (const void *)k_persistent<256, 4, PM, UP>;
+    case 5121: return (const void *)k_persistent<512, 1, PM, UP>;
+    case 5122: return (const void *)k_persistent<512, 2, PM, UP>;
+    case 5124: return (const void *)k_persistent<512, 4, PM, UP>;
+    case 10241: return (const void *)k_persistent<1024, 1, PM, UP>;
+    case 10242: return (const void *)k_persistent<1024, 2, PM, UP>;
+    case 10244: return (const void *)k_persistent<1024, 4, PM, UP>;
     default: return nullptr;
     }
 }

@@ -27,8 +27,23 @@ struct Acc {
 // kernel built for one program carries only that program's dispatch cases,
 // as the paper's compiler emits one kernel per program (Sec. 5).
 constexpr uint32_t PM_FIB = 1u, PM_MS = 2u, PM_NQ = 4u, PM_BFS = 8u, PM_TRAV = 16u, PM_SSSP = 32u, PM_FFT = 64u;
-constexpr uint32_t PM_ALL = PM_FIB | PM_MS | PM_NQ | PM_BFS | PM_TRAV | PM_SSSP | PM_FFT;
-constexpr uint32_t PM_MAPS = PM_MS | PM_BFS | PM_SSSP | PM_FFT;  // programs that schedule map operations
+constexpr uint32_t PM_USER = 128u;  // a user program (trees_program.cuh), compiled into its own kernel
+constexpr uint32_t PM_ALL = PM_FIB | PM_MS | PM_NQ | PM_BFS | PM_TRAV | PM_SSSP | PM_FFT;  // the built-in programs
+constexpr uint32_t PM_MAPS = PM_MS | PM_BFS | PM_SSSP | PM_FFT | PM_USER;  // programs that may schedule maps
+
+// The program type a kernel built for built-in programs carries (none).
+struct NoUserProgram {};
+
+__device__ __forceinline__ trees_user_env user_env(const Conf &c) {
+    trees_user_env env;
+#pragma unroll
+    for (int i = 0; i < TREES_USER_PARAMS; ++i) {
+        env.ptr[i] = c.rp.up[i];
+        env.val[i] = c.rp.uv[i];
+    }
+    env.result = reinterpret_cast<uint64_t *>(c.result);
+    return env;
+}
 
 __host__ __device__ constexpr uint32_t program_mask(int program) {
     return program == TREES_PROG_FIB         ? PM_FIB
@@ -218,12 +233,27 @@ __device__ __forceinline__ bool needs_link(uint32_t t) { return t == TREES_TASK_
 // Step 1 of a task: given its arguments, emit if it is a leaf (own-slot
 // writes, Sec. 4.3.2), count its forks, or request a map.  Only the task
 // types of the programs in PM are compiled in.
-template <uint32_t PM, uint32_t MT>
+template <uint32_t PM, uint32_t MT, typename UP = NoUserProgram>
 __device__ __forceinline__ void plan_task(const Conf &c, const RunParams &rp, Plan &p, uint32_t cen, uint32_t e,
                                           uint32_t a0, uint32_t a1, uint32_t lk) {
     const uint32_t s = p.s;
     p.a0 = a0;
     p.a1 = a1;
+    if constexpr ((PM & PM_USER) != 0u) {  // the user program decides (trees_user.h)
+        const trees_user_task t = {s, p.t, a0, a1, lk, cen};
+        const trees_user_plan q = UP::plan(t, user_env(c));
+        if (q.map_units) {
+            p.m = MAP_USER;
+            p.n = q.map_units;
+            p.a0 = q.map_a;
+            p.a1 = q.map_b;
+        } else {
+            p.n = q.forks;
+        }
+        if (q.emit) c.result[s] = q.value;
+        if (!q.forks || q.map_units) c.code[s] = 0u;
+        return;
+    }
     if constexpr ((PM & PM_FIB) != 0u) {
         if (p.t == TREES_TASK_FIB) {
             if (a0 < 2u || a0 <= rp.cutoff) {
@@ -376,11 +406,32 @@ __device__ __forceinline__ void fft_task_bodies(const RunParams &rp, const Plan 
 // the task into its join continuation.  Returns 1 if it joined.
 // fbase: the first slot of the epoch's fork range (the FFT places its
 // children by their point offset, see below).
-template <uint32_t PM>
+template <uint32_t PM, typename UP = NoUserProgram>
 __device__ __forceinline__ uint32_t commit_task(const Conf &c, const RunParams &rp, const Plan &p, uint32_t cen,
                                                  uint32_t child, uint32_t fbase = 0u) {
     const uint32_t s = p.s;
     const uint32_t fe = enc(cen + 1u, 0u);
+    if constexpr ((PM & PM_USER) != 0u) {  // children in the program's order, then the continuation
+        const trees_user_env env = user_env(c);
+        const trees_user_task t = {s, p.t, p.a0, p.a1, child, cen};
+        for (uint32_t i = 0; i < p.n; ++i) {
+            const trees_user_child ch = UP::child(t, i, env);
+            const bool ok = ch.type >= 1u && ch.type <= (uint32_t)TREES_NUM_TASK_TYPES;
+            c.code[child + i] = ok ? fe + ch.type : 0u;
+            c.a0[child + i] = ch.a0;
+            c.a1[child + i] = ch.a1;
+        }
+        const trees_user_child j = UP::join(t, env);
+        if (j.type >= 1u && j.type <= (uint32_t)TREES_NUM_TASK_TYPES) {
+            c.link[s] = child;
+            c.a0[s] = j.a0;
+            c.a1[s] = j.a1;
+            c.code[s] = enc(cen, j.type);
+            return 1u;
+        }
+        c.code[s] = 0u;
+        return 0u;
+    }
     if constexpr ((PM & PM_FIB) != 0u) {
         if (p.t == TREES_TASK_FIB) {
             c.code[child] = fe + TREES_TASK_FIB;
@@ -471,7 +522,7 @@ __device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan (&p)
     unsigned long long qa = 0ull, qb = 0ull;
 #pragma unroll
     for (int k = 0; k < TPT; ++k) {
-        if (p[k].m == MAP_LEAF_SORT || p[k].m == MAP_MERGE) qa += (1ull << 40) | p[k].n;
+        if (p[k].m == MAP_LEAF_SORT || p[k].m == MAP_MERGE || p[k].m == MAP_USER) qa += (1ull << 40) | p[k].n;
         else if (p[k].m == MAP_EXPAND || p[k].m == MAP_FFT) qb += (1ull << 40) | p[k].n;
     }
     unsigned long long ea, eb, ta, tb;
@@ -493,12 +544,12 @@ __device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan (&p)
             uint32_t rank = (uint32_t)(ea >> 40), toff = (uint32_t)(ea & CTR_LOW_MASK);
 #pragma unroll
             for (int k = 0; k < TPT; ++k) {
-                if (p[k].m != MAP_LEAF_SORT && p[k].m != MAP_MERGE) continue;
+                if (p[k].m != MAP_LEAF_SORT && p[k].m != MAP_MERGE && p[k].m != MAP_USER) continue;
                 const uint32_t di = dbase + rank;
                 c.mt_kind[di] = p[k].m;
                 c.mt_a[di] = p[k].a0;
                 c.mt_b[di] = p[k].a1;
-                c.mt_c[di] = cen;
+                c.mt_c[di] = p[k].m == MAP_USER ? p[k].s : cen;
                 c.mt_job[di] = job;
                 c.mt_tilebase[di] = tbase + toff;
                 acc.maps++;
@@ -560,9 +611,9 @@ struct TileLoad {
 template <int BS, int TPT, uint32_t PM>
 __device__ __forceinline__ void tile_load(const Conf &c, unsigned long long t0, uint32_t hi, int mode,
                                           TileLoad<TPT> &L) {
-    constexpr bool fresh_a1 = (PM & (PM_MS | PM_NQ | PM_FFT)) != 0u;
-    constexpr bool join_a0 = (PM & (PM_MS | PM_NQ | PM_TRAV | PM_FFT)) != 0u;
-    constexpr bool join_link = (PM & (PM_FIB | PM_NQ)) != 0u;
+    constexpr bool fresh_a1 = (PM & (PM_MS | PM_NQ | PM_FFT | PM_USER)) != 0u;
+    constexpr bool join_a0 = (PM & (PM_MS | PM_NQ | PM_TRAV | PM_FFT | PM_USER)) != 0u;
+    constexpr bool join_link = (PM & (PM_FIB | PM_NQ | PM_USER)) != 0u;
     const bool sa0 = mode == LOAD_FRESH || (mode == LOAD_JOIN && join_a0);
     const bool sa1 = (mode == LOAD_FRESH || mode == LOAD_JOIN) && fresh_a1;
     const bool slk = mode == LOAD_JOIN && join_link;
@@ -597,14 +648,14 @@ __device__ __forceinline__ constexpr bool join_prefetch() {
     return (PM & PM_FIB) != 0u && BS * TPT <= (int)JR_SLOTS;
 }
 
-template <int BS, int TPT, uint32_t PM>
+template <int BS, int TPT, uint32_t PM, typename UP = NoUserProgram>
 __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, unsigned long long t0, uint32_t hi,
                                            uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, Acc &acc, int par,
                                            int mode, const TileLoad<TPT> &L, bool known, uint32_t known_off,
                                            bool jr_use = false, const TileLoad<TPT> *pf = nullptr) {
-    constexpr bool fresh_a1 = (PM & (PM_MS | PM_NQ | PM_FFT)) != 0u;
-    constexpr bool join_a0 = (PM & (PM_MS | PM_NQ | PM_TRAV | PM_FFT)) != 0u;
-    constexpr bool join_link = (PM & (PM_FIB | PM_NQ)) != 0u;
+    constexpr bool fresh_a1 = (PM & (PM_MS | PM_NQ | PM_FFT | PM_USER)) != 0u;
+    constexpr bool join_a0 = (PM & (PM_MS | PM_NQ | PM_TRAV | PM_FFT | PM_USER)) != 0u;
+    constexpr bool join_link = (PM & (PM_FIB | PM_NQ | PM_USER)) != 0u;
     const bool sa0 = mode == LOAD_FRESH || (mode == LOAD_JOIN && join_a0);
     const bool sa1 = (mode == LOAD_FRESH || mode == LOAD_JOIN) && fresh_a1;
     const bool slk = mode == LOAD_JOIN && join_link;
@@ -640,7 +691,7 @@ __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> 
                     done = true;
                 }
             }
-            if (!done) plan_task<PM, merge_tile(BS)>(c, c.rp, p[k], cen, e, a0v[k], a1v[k], lkv[k]);
+            if (!done) plan_task<PM, merge_tile(BS), UP>(c, c.rp, p[k], cen, e, a0v[k], a1v[k], lkv[k]);
         }
         nf[k] = forks_of(p[k]);
         hasmap |= p[k].m != 0u;
@@ -693,7 +744,7 @@ __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> 
             uint32_t kbase = base + b0;
 #pragma unroll
             for (int k = 0; k < TPT; ++k) {
-                if (nf[k]) joined += commit_task<PM>(c, c.rp, p[k], cen, kbase + ex[k], base);
+                if (nf[k]) joined += commit_task<PM, UP>(c, c.rp, p[k], cen, kbase + ex[k], base);
                 kbase += tot[k];
             }
         }
@@ -1455,7 +1506,7 @@ __device__ void fft_combine_map(const Conf &c, uint32_t nd, uint32_t ne) {
 
 // The map phase of epoch e, after the partition sub-phase: leaf sorts one
 // warp per leaf, merge tiles one block per tile, then the expansion tiles.
-template <int BS, uint32_t PM>
+template <int BS, uint32_t PM, typename UP = NoUserProgram>
 __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, uint32_t e, uint32_t cen, uint32_t base,
                           unsigned long long mt, unsigned long long me, const RunParams *job_params = nullptr,
                           uint32_t job_stride = 0) {
@@ -1463,6 +1514,17 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
     const uint32_t nd2 = (uint32_t)(me >> 40), ne2 = (uint32_t)(me & CTR_LOW_MASK);
     const uint32_t nt2 = (ne2 + EXPAND_TILE - 1u) / EXPAND_TILE;
     uint32_t *keys, *scratch;
+    if constexpr ((PM & PM_USER) != 0u) {  // one block per unit, grid-stride over the epoch's units
+        const trees_user_env env = user_env(c);
+        for (uint32_t t = blockIdx.x; t < nt1; t += gridDim.x) {
+            const uint32_t di = tile_owner(c, t, nd1, nt1);
+            const uint32_t t0 = c.mt_tilebase[di];
+            const uint32_t t1 = di + 1u < nd1 ? c.mt_tilebase[di + 1u] : nt1;
+            const trees_user_map m = {c.mt_a[di], c.mt_b[di], c.mt_c[di], t1 - t0};
+            UP::template map<BS>(m, t - t0, env, static_cast<void *>(&sm.u));
+            __syncthreads();  // the shared memory is the next unit's
+        }
+    }
     if constexpr ((PM & PM_MS) != 0u) {
       if (nt1) {
         // leaves: one warp each

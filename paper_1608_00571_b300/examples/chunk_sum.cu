@@ -1,0 +1,73 @@
+// A user task program for the TREES runtime (include/trees_program.cuh):
+// the sum of n 32-bit keys as a task tree.  SUM(lo, hi) sums keys[lo, hi):
+// a range of at most `chunk` keys is one map unit that a whole block
+// reduces; a longer range forks k = min(arity, ceil(len / chunk)) children
+// over equal parts (part i = [lo + len*i/k, lo + len*(i+1)/k)) and joins
+// ADD, which adds the children's results.  Parameters: ptr[0] = the keys
+// (device, u32), val[0] = chunk, val[1] = arity.
+#include "trees_program.cuh"
+
+struct ChunkSum {
+    static constexpr uint32_t SUM = 1, ADD = 2;
+
+    __device__ static uint32_t parts(uint32_t lo, uint32_t hi, const trees_user_env &env) {
+        const uint64_t len = hi - lo, chunk = env.val[0], arity = env.val[1];
+        const uint64_t need = (len + chunk - 1) / chunk;
+        return (uint32_t)(need < arity ? need : arity);
+    }
+
+    __device__ static trees_user_plan plan(const trees_user_task &t, const trees_user_env &env) {
+        trees_user_plan q = {};
+        if (t.type == SUM) {
+            if ((uint64_t)(t.a1 - t.a0) <= env.val[0]) {
+                if (t.a1 > t.a0) {
+                    q.map_units = 1;
+                    q.map_a = t.a0;
+                    q.map_b = t.a1;
+                } else {
+                    q.emit = 1;  // an empty range sums to 0
+                }
+            } else {
+                q.forks = parts(t.a0, t.a1, env);
+            }
+        } else {  // ADD: the children's results
+            const uint32_t k = parts(t.a0, t.a1, env);
+            uint64_t sum = 0;
+            for (uint32_t i = 0; i < k; ++i) sum += env.result[t.link + i];
+            q.emit = 1;
+            q.value = sum;
+        }
+        return q;
+    }
+
+    __device__ static trees_user_child child(const trees_user_task &t, uint32_t i, const trees_user_env &env) {
+        const uint32_t k = parts(t.a0, t.a1, env);
+        const uint64_t len = t.a1 - t.a0;
+        return {SUM, t.a0 + (uint32_t)(len * i / k), t.a0 + (uint32_t)(len * (i + 1) / k)};
+    }
+
+    __device__ static trees_user_child join(const trees_user_task &t, const trees_user_env &) {
+        return {ADD, t.a0, t.a1};
+    }
+
+    // One block sums keys[m.a, m.b): per-thread partial sums, a warp
+    // reduction, then one word per warp through shared memory.
+    template <int BS>
+    __device__ static void map(const trees_user_map &m, uint32_t, const trees_user_env &env, void *smem) {
+        const uint32_t *keys = static_cast<const uint32_t *>(env.ptr[0]);
+        unsigned long long s = 0;
+        for (uint32_t i = m.a + threadIdx.x; i < m.b; i += BS) s += keys[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        unsigned long long *red = static_cast<unsigned long long *>(smem);
+        if ((threadIdx.x & 31u) == 0u) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long tot = 0;
+            for (int w = 0; w < BS / 32; ++w) tot += red[w];
+            env.result[m.slot] = tot;
+        }
+    }
+};
+
+TREES_DEFINE_PROGRAM(trees_chunk_sum, ChunkSum)

@@ -493,3 +493,45 @@ def test_fft_tvm_single_leaf_is_the_definition():
     r = oracle.tvm_run(oracle.FFT, x=x, fft_leaf=16)
     assert r["stats"]["tasks"] == 1 and r["stats"]["epochs"] == 1
     assert np.allclose(r["X"], oracle.dft(x), rtol=0, atol=1e-13)
+
+
+# ------------------------------------------------------------ the user-program example (chunked sum)
+
+@pytest.mark.parametrize("chunk,arity,k", [(4096, 8, 0), (4096, 8, 1), (4096, 8, 3), (1000, 2, 5), (7, 3, 4)])
+def test_chunk_sum_tree_perfect_closed_forms(chunk, arity, k):
+    """n = chunk * arity^k: a perfect arity-ary tree of depth k."""
+    st, tr = oracle.chunk_sum_tree(chunk * arity ** k, chunk, arity)
+    internal = (arity ** k - 1) // (arity - 1)
+    assert st["maps"] == arity ** k and st["joins"] == internal
+    assert st["epochs"] == 2 * k + 1 and st["tasks"] == arity ** k + 2 * internal
+    assert st["peak_slots"] == arity ** k + internal
+    assert [t["valid"] for t in tr[:k + 1]] == [arity ** d for d in range(k + 1)]
+
+
+def test_chunk_sum_tree_brute_force_leaves():
+    """The leaves partition [0, n) into ranges of at most chunk keys, every
+    internal range has the stated arity, for many small (n, chunk, arity)."""
+    for n in range(0, 60):
+        for chunk in (1, 2, 5, 16):
+            for arity in (2, 3, 8):
+                st, tr = oracle.chunk_sum_tree(n, chunk, arity)
+                # enumerate by hand: a plain recursion of the definition
+                leaves, internal, depth = [], 0, 0
+
+                def rec(lo, hi, d):
+                    nonlocal internal, depth
+                    depth = max(depth, d)
+                    if hi - lo <= chunk:
+                        leaves.append((lo, hi))
+                        return
+                    internal += 1
+                    kk = min(arity, -(-(hi - lo) // chunk))
+                    cuts = [lo + (hi - lo) * i // kk for i in range(kk + 1)]
+                    for a, b in zip(cuts, cuts[1:]):
+                        rec(a, b, d + 1)
+
+                rec(0, n, 0)
+                assert sorted(leaves) == leaves and leaves[0][0] == 0 and leaves[-1][1] == n
+                assert all(b - a <= chunk for a, b in leaves) and all(a < b for a, b in leaves[1:] if n)
+                assert st["maps"] == sum(1 for a, b in leaves if b > a) and st["joins"] == internal
+                assert st["epochs"] == 2 * depth + 1
