@@ -318,11 +318,13 @@ typedef struct {
 } trees_job_result_t;
 
 /* Task-vector slots a job needs at its peak.  *exact (may be NULL) is set to
- * 1 when the count is exact (fib, mergesort, traversal upper bound, BFS) and
- * 0 when it is an estimate (N-Queens: the backtracking tree is not known
- * before it is explored; SSSP: one slot per relax task, at least the vertex
- * count, more when distances drop again; a job that outgrows it ends with
- * CAPACITY). */
+ * 1 when the count is exact (fib, mergesort, traversal upper bound, BFS,
+ * FFT: 2^(D+1) - 1 for D = log2(n / leaf)) and 0 when it is an estimate
+ * (N-Queens: the backtracking tree is not known before it is explored; SSSP:
+ * one slot per relax task, at least the vertex count, more when distances
+ * drop again; a job that outgrows it ends with CAPACITY).  A user program's
+ * tree is unknown to the library: 0 slots, not exact (size its context from
+ * the program). */
 uint64_t trees_job_slots(const trees_job_t *job, int32_t *exact);
 
 /* Runs njobs jobs in one persistent launch on the context's task vector.
