@@ -45,6 +45,34 @@
 #include "trees.h"
 #include "trees_kernels.cuh"
 
+// The paper's four primitives (Sec. 4.2) as helpers for the records above:
+// plan fills a trees_user_plan with trees_emit / trees_fork / trees_map, and
+// child and join return trees_join's or a child's (type, a0, a1) record.
+//   emit v          -> trees_emit(q, v)
+//   fork f(args) xk -> trees_fork(q, k) in plan; child(t, i) returns trees_task(f, args of child i)
+//   join f(args)    -> join(t) returns trees_join(f, args)
+//   map f(args)     -> trees_map(q, units, a, b); the program's map runs each unit
+__device__ __forceinline__ void trees_emit(trees_user_plan &q, uint64_t v) {
+    q.emit = 1;
+    q.value = v;
+}
+__device__ __forceinline__ void trees_fork(trees_user_plan &q, uint32_t children) { q.forks = children; }
+__device__ __forceinline__ void trees_map(trees_user_plan &q, uint32_t units, uint32_t a, uint32_t b) {
+    q.map_units = units;
+    q.map_a = a;
+    q.map_b = b;
+}
+__device__ __forceinline__ trees_user_child trees_task(uint32_t type, uint32_t a0, uint32_t a1) {
+    trees_user_child c;
+    c.type = type;
+    c.a0 = a0;
+    c.a1 = a1;
+    return c;
+}
+__device__ __forceinline__ trees_user_child trees_join(uint32_t type, uint32_t a0, uint32_t a1) {
+    return trees_task(type, a0, a1);
+}
+
 #define TREES_DEFINE_PROGRAM(NAME, PROG)                                                                       \
     extern "C" int NAME(int32_t op, int32_t bs, int32_t tpt, void **args, int32_t grid, void *stream,         \
                         int32_t *out) {                                                                        \

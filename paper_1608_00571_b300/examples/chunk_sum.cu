@@ -20,22 +20,16 @@ struct ChunkSum {
         trees_user_plan q = {};
         if (t.type == SUM) {
             if ((uint64_t)(t.a1 - t.a0) <= env.val[0]) {
-                if (t.a1 > t.a0) {
-                    q.map_units = 1;
-                    q.map_a = t.a0;
-                    q.map_b = t.a1;
-                } else {
-                    q.emit = 1;  // an empty range sums to 0
-                }
+                if (t.a1 > t.a0) trees_map(q, 1, t.a0, t.a1);  // one block sums the chunk
+                else trees_emit(q, 0);                          // an empty range sums to 0
             } else {
-                q.forks = parts(t.a0, t.a1, env);
+                trees_fork(q, parts(t.a0, t.a1, env));
             }
         } else {  // ADD: the children's results
             const uint32_t k = parts(t.a0, t.a1, env);
             uint64_t sum = 0;
             for (uint32_t i = 0; i < k; ++i) sum += env.result[t.link + i];
-            q.emit = 1;
-            q.value = sum;
+            trees_emit(q, sum);
         }
         return q;
     }
@@ -43,11 +37,11 @@ struct ChunkSum {
     __device__ static trees_user_child child(const trees_user_task &t, uint32_t i, const trees_user_env &env) {
         const uint32_t k = parts(t.a0, t.a1, env);
         const uint64_t len = t.a1 - t.a0;
-        return {SUM, t.a0 + (uint32_t)(len * i / k), t.a0 + (uint32_t)(len * (i + 1) / k)};
+        return trees_task(SUM, t.a0 + (uint32_t)(len * i / k), t.a0 + (uint32_t)(len * (i + 1) / k));
     }
 
     __device__ static trees_user_child join(const trees_user_task &t, const trees_user_env &) {
-        return {ADD, t.a0, t.a1};
+        return trees_join(ADD, t.a0, t.a1);
     }
 
     // One block sums keys[m.a, m.b): per-thread partial sums, a warp
