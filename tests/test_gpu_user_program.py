@@ -31,14 +31,14 @@ def program():
     return lib.trees_chunk_sum
 
 
-def run_sum(program, keys, chunk, arity, cap=None, **cfg):
+def run_sum(program, keys, chunk, arity, cap=None, upk=0, **cfg):
     n = keys.shape[0]
     d = torch.from_numpy(keys.view(np.int32)).cuda() if n else torch.zeros(1, dtype=torch.int32, device="cuda")
     st_model, _ = oracle.chunk_sum_tree(n, chunk, arity)
     ctx = T.trees_create(cap or st_model["peak_slots"] + 64, T.trees_default_config(trace=1, **cfg))
     try:
         job = T.make_job(T.TREES_PROG_USER, user_program=program, user_type=1, user_a0=0, user_a1=n,
-                         user_ptr=(d,), user_val=(chunk, arity))
+                         user_ptr=(d,), user_val=(chunk, arity, upk))
         T.trees_run(ctx, job, torch.cuda.current_stream())
         status = T.trees_sync(ctx)
         stats = T.trees_stats(ctx)
@@ -66,6 +66,21 @@ def test_chunk_sum_against_oracle(program, n, chunk, arity):
             assert g[f] == o[f], (i, f, g, o)
 
 
+@pytest.mark.parametrize("n,chunk,arity,upk", [(1 << 20, 4096, 8, 1000), (100_000, 1000, 3, 7), (123_457, 7, 16, 2),
+                                                (4097, 4096, 8, 4096), (50_000, 50_000, 2, 333)])
+def test_chunk_sum_multi_unit_maps(program, n, chunk, arity, upk):
+    """Leaves emit 0 and map ceil(len / upk) units that add their partial sums:
+    maps of many units, each unit's index, and an emit together with a map."""
+    keys = gen.keys_u32(n + 11, n)
+    # map units count against the map capacity (default: the task-vector capacity)
+    status, result, stats, trace = run_sum(program, keys, chunk, arity, upk=upk, map_capacity=n // upk + 1024)
+    assert status == T.TREES_OK
+    assert result == int(keys.astype(np.uint64).sum())
+    st, tr = oracle.chunk_sum_tree(n, chunk, arity)
+    assert (stats["maps"], stats["epochs"], stats["tasks"]) == (st["maps"], st["epochs"], st["tasks"])
+    assert [t["maps"] for t in trace] == [t["maps"] for t in tr]
+
+
 @pytest.mark.parametrize("bs,tpt", [(128, 1), (256, 4), (512, 2), (1024, 1)])
 def test_chunk_sum_block_shapes(program, bs, tpt):
     n = 777_777
@@ -78,6 +93,8 @@ def test_chunk_sum_block_shapes(program, bs, tpt):
 def test_user_program_errors(program):
     keys = gen.keys_u32(1, 50_000)
     status, _, _, _ = run_sum(program, keys, 16, 4, cap=32)  # far fewer slots than tasks
+    assert status == T.TREES_ERR_CAPACITY
+    status, _, _, _ = run_sum(program, keys, 4096, 8, upk=10, map_capacity=64)  # more map units than map capacity
     assert status == T.TREES_ERR_CAPACITY
     d = torch.from_numpy(keys.view(np.int32)).cuda()
     for cfg, kw in [({}, dict(user_program=None, user_type=1)), ({}, dict(user_program=program, user_type=0)),
