@@ -24,7 +24,9 @@
  *       A task that forks nothing (and maps or emits) ends.
  *   static __device__ trees_user_child child(const trees_user_task &t, uint32_t i, const trees_user_env &env);
  *       Child i < forks (type and arguments); children occupy consecutive
- *       slots in this order, the first at the continuation's t.link.
+ *       slots in this order, the first at the continuation's t.link.  A
+ *       child whose type is outside 1..TREES_NUM_TASK_TYPES never runs (its
+ *       slot stays empty; its result word stays 0 only if nothing wrote it).
  *   static __device__ trees_user_child join(const trees_user_task &t, const trees_user_env &env);
  *       The continuation the task turns into after forking (Sec. 4.3.2:
  *       its own slot, same epoch number, run after every task forked under
@@ -39,6 +41,11 @@
  *
  * plan runs in every thread that holds a task; child and join in the thread
  * that forked.  They must not synchronise: only map is block-cooperative.
+ * A task that both forks and maps is treated as mapping (its forks are
+ * dropped); emitting and mapping together is allowed, the map running after
+ * the emit.  Size the context for the program: task-vector slots for its
+ * widest set of live tasks, and map_capacity (trees_config_t) for the map
+ * units of one epoch.
  */
 #pragma once
 
