@@ -26,7 +26,7 @@
  *       Child i < forks (type and arguments); children occupy consecutive
  *       slots in this order, the first at the continuation's t.link.  A
  *       child whose type is outside 1..TREES_NUM_TASK_TYPES never runs (its
- *       slot stays empty; its result word stays 0 only if nothing wrote it).
+ *       slot is left empty and its result word is not written).
  *   static __device__ trees_user_child join(const trees_user_task &t, const trees_user_env &env);
  *       The continuation the task turns into after forking (Sec. 4.3.2:
  *       its own slot, same epoch number, run after every task forked under
