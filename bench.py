@@ -493,6 +493,20 @@ def batch_and_serve(T, torch, np, gen, stream):
     return out
 
 
+def host_cpu():
+    """The host's logical CPU count and CPU model (first "model name" of /proc/cpuinfo)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
 def cpu_baseline(seconds):
     """The oracle's TVM simulator on fib(34), one host core, repeated for about
     `seconds` seconds."""
@@ -508,7 +522,7 @@ def cpu_baseline(seconds):
     dt = time.perf_counter() - t0
     return {"value": tasks / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",
             "sample": f"{runs} full runs of the sequential TVM simulator on fib({FIB_N}) "
-                      f"({tasks} task executions, {dt:.1f} s)"}
+                      f"({tasks} task executions, {dt:.1f} s)", **host_cpu()}
 
 
 def run_reference(args, rank, world):
@@ -532,7 +546,8 @@ def run_reference(args, rank, world):
             "data": "synthetic", "config": {"workload": f"fib({FIB_N}) uint64 task tree, no sequential cutoff",
                                             "n": FIB_N, "cutoff": 0},
             "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} timed runs of the sequential TVM simulator on fib({FIB_N})"},
+                             "sample": f"{args.steps} timed runs of the sequential TVM simulator on fib({FIB_N})",
+                             **host_cpu()},
             "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
