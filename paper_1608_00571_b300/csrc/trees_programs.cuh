@@ -342,7 +342,7 @@ __device__ __forceinline__ void plan_task(const Conf &c, const RunParams &rp, Pl
     }
     if constexpr ((PM & PM_FFT) != 0u) {
         // a leaf's transform and a combine done in its task run at the end of
-        // the tile (fft_task_body), out of this unrolled loop
+        // the tile (fft_task_bodies), out of this unrolled loop
         if (p.t == TREES_TASK_FFT) {
             if ((1u << (rp.lgn - a1)) <= rp.leaf) c.code[s] = 0u;
             else p.n = 2u;
