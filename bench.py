@@ -33,7 +33,9 @@ METRIC = "tasks/sec & µs/epoch (fib, sort, BFS); batched jobs/sec, p99 latency 
 FIB_N = 34
 FLUSH_BYTES = 256 << 20  # > 126 MB L2
 FFT_LG, FFT_LEAF, FFT_CUTOFF = 24, 16, 0  # 2^24 points; 16-point leaves; every combine a map
-SSSP_SLOTS_PER_VERTEX = 3  # task-vector slots per vertex for SSSP (measured 1.10-1.12 relax tasks per vertex)
+SSSP_SLOTS_PER_VERTEX = 3  # task-vector slots per vertex for SSSP (relax tasks per reached vertex are measured below)
+EPOCH_OVER_FLOOR_TARGET = 3.5  # target: fib(34) microseconds per epoch within 3.5x the bare grid-barrier floor
+CLOCK_WARM_S = 1.0  # the clock sampler runs through at least this much warm-up of the timed step
 
 
 def parse_args():
@@ -372,33 +374,58 @@ def timed_runs(T, torch, ctx, job, steps, warmup, stream, flush=None, setup=None
     return times
 
 
-def vfit(T, torch, stream, sms):
-    """Least-squares fit of T_P = V1*T1/P + Vinf*Tinf over fib n = 16..34,
-    cutoffs {0, 8, 12} and grids of P = SMs/4, SMs/2, SMs (one 1024-thread
-    block per SM used)."""
+def vfit(T, torch, stream, cfg, solo_slots):
+    """V1 and V-infinity of T_P = V1*T1/P + Vinf*Tinf (Sec. 1, Sec. 3), fitted
+    per epoch: each epoch e of fib(34) is one step of the critical path
+    (Tinf counts epochs), so its duration is modelled as
+    dt_e = V1 * valid_e / P + Vinf, with valid_e the tasks it ran (its share
+    of T1) and P the SMs working.  Runs the tuned block shape on P = 1/4,
+    1/2 and all of the SMs (trace on, per-epoch end times from globaltimer)
+    and fits the epochs that close with a grid barrier by least squares.
+    Epochs of at most `solo_slots` slots run in one block under block
+    barriers, so the model's P does not apply to them: their mean duration
+    is reported beside the fit as the solo-epoch Vinf."""
     import numpy as np
-    rows, ys = [], []
+    job = T.make_job(T.TREES_PROG_FIB, n=FIB_N)
+    rows, ys, solo, per_p = [], [], [], {}
+    probe = T.trees_create(1024, cfg)
+    full_grid, _, sms = T.trees_geometry(probe)
+    T.trees_destroy(probe)
+    per_sm = max(1, full_grid // sms)
     for frac in (4, 2, 1):
         P = max(1, sms // frac)
-        ctx = T.trees_create(20_000_000, T.trees_default_config(block_size=1024, grid_blocks=P))
+        c = T.trees_create(20_000_000, T.trees_default_config(
+            block_size=cfg.block_size, tasks_per_thread=cfg.tasks_per_thread, grid_blocks=P * per_sm, trace=1,
+            map_capacity=1))
         try:
-            for cutoff in (0, 8, 12):
-                for n in range(16, 35, 2):
-                    if cutoff and n <= cutoff + 2:
-                        continue
-                    job = T.make_job(T.TREES_PROG_FIB, n=n, cutoff=cutoff)
-                    t = min(timed_runs(T, torch, ctx, job, 3, 1, stream))
-                    st = T.trees_stats(ctx)
-                    rows.append([st["tasks"] / P, st["epochs"]])
-                    ys.append(t * 1000.0)  # us
+            timed_runs(T, torch, c, job, 2, 1, stream)
+            tr = T.trees_trace(c)
         finally:
-            T.trees_destroy(ctx)
-    A, y = np.array(rows, dtype=float), np.array(ys)
+            T.trees_destroy(c)
+        pr, py = [], []
+        for a, b in zip(tr, tr[1:]):
+            dt_us = (b["t_ns"] - a["t_ns"]) / 1000.0
+            if b["hi"] - b["lo"] <= solo_slots:
+                solo.append(dt_us)
+            else:
+                pr.append([b["valid"] / P, 1.0])
+                py.append(dt_us)
+        rows += pr
+        ys += py
+        A1, y1 = np.array(pr), np.array(py)
+        c1, *_ = np.linalg.lstsq(A1, y1, rcond=None)
+        per_p[str(P)] = {"V1_us_per_task_per_SM": float(c1[0]), "Vinf_us_per_epoch": float(c1[1]),
+                         "grid_epochs": len(py)}
+    A, y = np.array(rows), np.array(ys)
     coef, *_ = np.linalg.lstsq(A, y, rcond=None)
-    pred = A @ coef
-    r2 = 1.0 - float(((y - pred) ** 2).sum() / ((y - y.mean()) ** 2).sum())
-    return {"V1_us_per_task_per_SM": float(coef[0]), "Vinf_us_per_epoch": float(coef[1]), "r2": r2,
-            "points": len(ys), "P": "SMs used (1024-thread blocks, one per SM): 37, 74, 148"}
+    res = y - A @ coef
+    r2 = 1.0 - float((res ** 2).sum() / ((y - y.mean()) ** 2).sum())
+    return {"model": "per grid-barrier epoch: dt = V1 * valid / P + Vinf (P = SMs working)",
+            "V1_us_per_task_per_SM": float(coef[0]), "Vinf_us_per_epoch": float(coef[1]), "r2": r2,
+            "rms_residual_us": float(np.sqrt((res ** 2).mean())), "max_abs_residual_us": float(np.abs(res).max()),
+            "points": len(ys), "per_P": per_p, "solo_epoch_mean_us": float(np.mean(solo)) if solo else None,
+            "solo_epochs_per_run": len(solo) // 3,
+            "P": f"SMs: {sms // 4}, {sms // 2}, {sms} ({per_sm} block(s) of {cfg.block_size} threads per SM)"}
 
 
 def batch_and_serve(T, torch, np, gen, stream):
@@ -427,8 +454,15 @@ def batch_and_serve(T, torch, np, gen, stream):
         torch.cuda.synchronize()
 
     segs = [T.trees_job_slots(j)[0] for j in jobs]
+    # each sort job's expected output: its input sorted on the device (as unsigned values)
+    want = [torch.sort(k.to(torch.int64) & 0xFFFFFFFF).values for k in pristine]
+
+    def sorts_ok():
+        return all(torch.equal(d.to(torch.int64) & 0xFFFFFFFF, w) for d, w in zip(work, want))
+
     out = {}
     best = None
+    per_bs = {}
     for bs in (256, 512, 1024):  # the batch kernel's block size, tuned here
         cfg_b = T.trees_default_config(block_size=bs, map_capacity=1 << 22)
         ctx = T.trees_create(sum(segs) + 1024, cfg_b)
@@ -442,7 +476,9 @@ def batch_and_serve(T, torch, np, gen, stream):
             status, res, steps = T.trees_batch_results(ctx, 4096)
             assert status == T.TREES_OK and all(r["status"] == T.TREES_OK for r in res)
             times.append(a.elapsed_time(b))
+        assert sorts_ok(), f"batched sorts (block size {bs}) differ from their sorted inputs"
         T.trees_destroy(ctx)
+        per_bs[bs] = min(times)
         if best is None or min(times) < best[0]:
             best = (min(times), bs, res, steps)
     bms, bs, res, steps = best
@@ -454,9 +490,9 @@ def batch_and_serve(T, torch, np, gen, stream):
         elif kind[i] == gen.JOB_FIB:
             assert r["epochs"] == 2 * int(param[i]) - 1
     tasks = sum(r["tasks"] for r in res)
-    bms = min(times)
     out["batched"] = {"jobs": 4096, "ms": bms, "jobs_per_s": 4096 / (bms / 1000), "steps": steps,
-                      "tasks": tasks, "tasks_per_s": tasks / (bms / 1000), "block_size": bs}
+                      "tasks": tasks, "tasks_per_s": tasks / (bms / 1000), "block_size": bs,
+                      "ms_by_block_size": per_bs}
     # one job per launch, back to back
     reset()
     solo = T.trees_create(max(segs) + 1024, T.trees_default_config(block_size=bs, map_capacity=1 << 22))
@@ -507,46 +543,122 @@ def host_cpu():
     return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
-def cpu_baseline(seconds):
-    """The oracle's TVM simulator on fib(34), one host core, repeated for about
-    `seconds` seconds."""
-    import oracle
+def _timed_repeats(fn, seconds):
+    """Calls fn() until `seconds` have passed (at least once); returns (calls, elapsed s)."""
     t0 = time.perf_counter()
-    runs, tasks = 0, 0
+    runs = 0
     while True:
-        r = oracle.tvm_run(oracle.FIB, fib_n=FIB_N)
-        tasks += r["stats"]["tasks"]
+        fn()
         runs += 1
-        if time.perf_counter() - t0 >= seconds:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": tasks / dt, "unit": "tasks/s", "cores": 1, "kind": "oracle",
-            "sample": f"{runs} full runs of the sequential TVM simulator on fib({FIB_N}) "
-                      f"({tasks} task executions, {dt:.1f} s)", **host_cpu()}
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            return runs, dt
+
+
+def cpu_fib_rate(seconds):
+    """fib(34) by the oracle's plain recursion (the sequential program of
+    Sec. 6.2's comparison, one host core): jobs/s and calls/s."""
+    import oracle
+    v, calls = oracle.fib(FIB_N)
+    assert v == 5702887
+    runs, dt = _timed_repeats(lambda: oracle.fib(FIB_N), seconds)
+    return runs / dt, calls
+
+
+def cpu_baseline(seconds, gpu_tasks_per_job, extra=None):
+    """The oracle on one host core.  Headline: fib(34) by the plain recursion,
+    converted to the headline's unit as (fib(34) jobs/s) x (task executions
+    per fib(34) job as the task vector machine counts them), so both arms
+    divide the same work by their time.  Secondary: the oracle's sequential
+    TVM simulator on fib(34), and the plain recursions of the other
+    workloads (`extra`, timed by the caller next to their GPU runs)."""
+    import oracle
+    jobs_per_s, calls = cpu_fib_rate(min(seconds, 3.0))
+    sim_runs, sim_dt = _timed_repeats(lambda: oracle.tvm_run(oracle.FIB, fib_n=FIB_N), min(seconds, 2.0))
+    out = {"value": jobs_per_s * gpu_tasks_per_job, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+           "sample": f"fib({FIB_N}) by the oracle's plain recursion (oracle.fib, {calls} calls per job), repeated "
+                     f"for ~{min(seconds, 3.0):.0f} s on one host core; value = jobs/s x {gpu_tasks_per_job} task "
+                     f"executions per fib({FIB_N}) job",
+           "fib34_jobs_per_s": jobs_per_s, "fib34_calls_per_s": jobs_per_s * calls,
+           "tvm_simulator": {"value": sim_runs * gpu_tasks_per_job / sim_dt, "unit": "tasks/s",
+                             "sample": f"{sim_runs} runs of the oracle's sequential TVM simulator on fib({FIB_N})"},
+           **host_cpu()}
+    if extra:
+        out["workloads"] = extra
+    return out
+
+
+def cpu_sort_rate(seconds):
+    """The oracle's recursive top-down mergesort (1024-key leaves) on a
+    bounded sample: 2^24 splitmix64 keys, repeated for about `seconds`."""
+    import numpy as np
+    import oracle
+    from paper_1608_00571_b300 import gen
+    n = 1 << 24
+    keys = gen.keys_u32(1, n)
+    runs, dt = _timed_repeats(lambda: oracle.mergesort(keys), seconds)
+    return {"keys_per_s": runs * n / dt, "sample": f"{runs} oracle.mergesort runs on 2^24 keys (seed 1), "
+                                                   f"one core", "cores": 1}
+
+
+def cpu_bfs_rate(row_ptr, col, seconds):
+    """The oracle's FIFO-queue BFS on the R-MAT scale-22 graph from vertex 0."""
+    import oracle
+    box = {}
+
+    def one():
+        box["r"] = oracle.bfs(row_ptr, col, 0)[1]
+    runs, dt = _timed_repeats(one, seconds)
+    return {"ms": 1000 * dt / runs, "reached_per_s": box["r"] * runs / dt,
+            "sample": f"{runs} oracle.bfs runs on R-MAT 22, one core", "cores": 1}
+
+
+def cpu_nqueens_rate(seconds):
+    """The oracle's backtracking N-Queens(11) (166,926 row tasks)."""
+    import oracle
+    v, rows, joins = oracle.nqueens(11)
+    assert v == 2680
+    runs, dt = _timed_repeats(lambda: oracle.nqueens(11), seconds)
+    return {"jobs_per_s": runs / dt, "row_tasks_per_s": runs * rows / dt,
+            "sample": f"{runs} oracle.nqueens(11) runs, one core", "cores": 1}
+
+
+FIB34_TASKS = 27682393  # task executions of the fib(34) tree (fib tasks + joins), the TVM's count
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle's plain recursive fib(34) on one host
+    core, one fib(34) job per step, reported in the headline's unit."""
     if rank != 0:
         return
     import oracle
     oracle.build()
-    times, tasks = [], 0
+    v, calls = oracle.fib(FIB_N)
+    assert v == 5702887
+    times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        r = oracle.tvm_run(oracle.FIB, fib_n=FIB_N)
+        r, _ = oracle.fib(FIB_N)
         dt = time.perf_counter() - t0
+        assert r == 5702887
         if i >= args.warmup:
             times.append(dt)
-            tasks = r["stats"]["tasks"]
     total = sum(times)
-    value = args.steps * tasks / total
+    value = args.steps * FIB34_TASKS / total
+    sim_t0 = time.perf_counter()
+    oracle.tvm_run(oracle.FIB, fib_n=FIB_N)
+    sim_dt = time.perf_counter() - sim_t0
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "tasks/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64",
             "data": "synthetic", "config": {"workload": f"fib({FIB_N}) uint64 task tree, no sequential cutoff",
                                             "n": FIB_N, "cutoff": 0},
             "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} timed runs of the sequential TVM simulator on fib({FIB_N})",
+                             "sample": f"{args.steps} timed fib({FIB_N}) jobs by the oracle's plain recursion "
+                                       f"({calls} calls each); value = jobs/s x {FIB34_TASKS} task executions "
+                                       f"per job",
+                             "tvm_simulator": {"value": FIB34_TASKS / sim_dt, "unit": "tasks/s",
+                                               "sample": "one run of the oracle's sequential TVM simulator"},
                              **host_cpu()},
             "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -590,8 +702,14 @@ def main():
     job = T.make_job(T.TREES_PROG_FIB, n=FIB_N)
     cfg = tune(job, 20_000_000, f"fib:n={FIB_N}:cutoff=0", T.trees_default_config(map_capacity=1))
     ctx = T.trees_create(20_000_000, cfg)
-    timed_runs(T, torch, ctx, job, 0, args.warmup, stream, flush)
+    # the clock record covers the warm-up (at least CLOCK_WARM_S of the same step, and at least W steps)
+    # and the timed region: a timed region of a few milliseconds is shorter than the sampling interval
     clocks = ClockSampler(local)
+    t_w0 = time.perf_counter()
+    nwarm = 0
+    while nwarm < args.warmup or time.perf_counter() - t_w0 < CLOCK_WARM_S:
+        timed_runs(T, torch, ctx, job, 0, 1, stream, flush)
+        nwarm += 1
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -651,19 +769,25 @@ def main():
                    "scheduler": ["persistent", "graph", "hostloop"][cfg.scheduler], "block_size": bs,
                    "tasks_per_thread": cfg.tasks_per_thread, "grid_blocks": grid, "sms": sms,
                    "l2": "flushed between steps (256 MiB device write)"},
+        "headline2": None,  # mergesort of 2^26 keys, filled in below (kept near the front of the line)
         "us_per_epoch": us_epoch, "epochs": stats["epochs"], "tasks_per_step": tasks,
         "barrier_floor_us": floor_us, "epoch_over_floor": us_epoch / floor_us,
+        "epoch_over_floor_target": EPOCH_OVER_FLOOR_TARGET,
+        "epoch_over_floor_met": us_epoch / floor_us <= EPOCH_OVER_FLOOR_TARGET,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)",
                      "algorithmic_bytes_per_launch": alg,
                      "kernel": f"k_persistent<{bs},{cfg.tasks_per_thread},PM_FIB>"},
-        "clocks": clk, "wall_s_timed_region": wall,
+        "clocks": {**clk, "window": f"{nwarm} warm-up steps ({time.perf_counter() - t_w0 - wall:.2f} s, "
+                                    f"same step) and the {args.steps} timed steps"},
+        "wall_s_timed_region": wall,
         "e2e": {"value": e2e_value, "unit": "tasks/s", "h2d_bytes_per_step": 12, "d2h_bytes_per_step": 8},
         # per step: k_setup + the persistent kernel, or k_setup + 4 kernels per epoch in the graph
         "gpu_launches": args.steps * (2 if cfg.scheduler == T.TREES_SCHED_PERSISTENT else 1 + 4 * stats["epochs"]),
     }
 
+    cpu_extra = {}
     if not args.quick:
         workloads = {}
         # fib(34) with a leaf cutoff of 12
@@ -690,6 +814,7 @@ def main():
         s3 = T.trees_stats(c3)
         T.trees_destroy(c3)
         ok3 = bool(np.array_equal(kd.cpu().numpy().view(np.uint32), np.sort(keys)))
+        assert ok3, "mergesort 2^26: output differs from numpy's sort"
         m3 = statistics.mean(t3)
         ab3 = sort_alg_bytes(n)
         workloads["mergesort_2^26"] = {"ms": m3, "tasks": s3["tasks"], "epochs": s3["epochs"],
@@ -700,6 +825,12 @@ def main():
                                                     "frac": ab3 / (m3 / 1000) / 1e9 / hbm_peak,
                                                     "algorithmic_bytes": ab3}}
         del src, kd, sc
+        line["headline2"] = {"workload": "mergesort of 2^26 uint32 keys (splitmix64 seed 1), 1024-key leaves",
+                             "ms": m3, "tasks_per_s": s3["tasks"] / (m3 / 1000), "keys_per_s": n / (m3 / 1000),
+                             "us_per_epoch": 1000 * m3 / s3["epochs"],
+                             "hbm_frac": ab3 / (m3 / 1000) / 1e9 / hbm_peak, "sorted_equal_numpy": ok3}
+        if rank == 0:
+            cpu_extra["mergesort"] = cpu_sort_rate(min(args.cpu_seconds, 6.0))
         # BFS on R-MAT scale 22
         row_ptr, col, info = gen.rmat(22, 16, seed=2)
         rp = torch.from_numpy(row_ptr).cuda()
@@ -712,6 +843,7 @@ def main():
         T.trees_destroy(c4)
         level = lv.cpu().numpy()
         ok4 = bfs_certificate(row_ptr, col, 0, level)
+        assert ok4, "BFS R-MAT 22: the level certificate fails"
         m4 = statistics.mean(t4)
         ab4, edges = bfs_alg_bytes(row_ptr, level)
         workloads["bfs_rmat22"] = {"ms": m4, "tasks": s4["tasks"], "epochs": s4["epochs"],
@@ -721,6 +853,8 @@ def main():
                                    "roofline": {"bound": "hbm", "achieved": ab4 / (m4 / 1000) / 1e9, "peak": hbm_peak,
                                                 "unit": "GB/s", "frac": ab4 / (m4 / 1000) / 1e9 / hbm_peak,
                                                 "algorithmic_bytes": ab4}}
+        if rank == 0:
+            cpu_extra["bfs_rmat22"] = cpu_bfs_rate(row_ptr, col, 1.5)
         # SSSP on the same graph, symmetric weights in [1, 255] (Sec. 6.3's worklist relaxation as tasks)
         weight = gen.weights(3, row_ptr, col)
         wt = torch.from_numpy(weight.view(np.int32)).cuda()
@@ -735,6 +869,7 @@ def main():
         T.trees_destroy(c5)
         sssp_dist = dist_t.cpu().numpy().view(np.uint64)
         ok5 = sssp_certificate(row_ptr, col, weight, 0, sssp_dist, level)
+        assert ok5, "SSSP R-MAT 22: the shortest-path certificate fails"
         m5 = statistics.mean(t5)
         ab5, edges5 = sssp_alg_bytes(row_ptr, level >= 0, s5["tasks"])
         workloads["sssp_rmat22"] = {"ms": m5, "tasks": s5["tasks"], "epochs": s5["epochs"],
@@ -765,6 +900,7 @@ def main():
         rel = 24 * 8 * 2.0 ** -24 / (1 - 24 * 8 * 2.0 ** -24)           # radix-2 fp32 error bound
         ok6 = bool(np.all(np.isfinite(X6)) and abs(np.linalg.norm(X6) - norm_X) <= rel * norm_X and
                    np.all(np.abs(X6[ks] - dft_samples(x6, ks)) <= rel * norm_X))
+        assert ok6, "FFT 2^24: an output is not finite or outside the radix-2 error bound"
         m6 = statistics.mean(t6)
         ab6, lv6 = fft_alg_bytes(n6, FFT_LEAF)
         workloads[f"fft_2^{FFT_LG}"] = {
@@ -796,6 +932,7 @@ def main():
         t7 = timed_runs(T, torch, c7, j7, 5, 2, stream, flush)
         s7 = T.trees_stats(c7)
         ok7 = T.trees_result(c7, 0) == int(keys7.astype(np.uint64).sum())
+        assert ok7, "user program: the sum differs from numpy's"
         T.trees_destroy(c7)
         m7 = statistics.mean(t7)
         ab7 = 4 * n7
@@ -820,12 +957,13 @@ def main():
             sch[name] = {"ms": mm, "us_per_epoch": 1000 * mm / stats["epochs"], "tasks_per_s": tasks / (mm / 1000)}
         sch["persistent"] = {"ms": ms_step, "us_per_epoch": us_epoch, "tasks_per_s": tasks / (ms_step / 1000)}
         line["schedulers"] = sch
-        line["vfit"] = vfit(T, torch, stream, sms)
+        line["vfit"] = vfit(T, torch, stream, cfg, 2 * cfg.block_size * cfg.tasks_per_thread)
         line["batch_serve"] = batch_and_serve(T, torch, np, gen, stream)
     line["autotune"] = tuned
 
     if rank == 0:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        cpu_extra["nqueens11"] = cpu_nqueens_rate(1.0)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, tasks, cpu_extra)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -98,35 +98,50 @@ typedef struct {
     int32_t reserved;
 } trees_config_t;
 
-/* Fills *cfg with the defaults above. */
+/* Fills *cfg with the defaults above.  The block size default follows the
+ * work-group size of 256..512 work-items a TREES kernel is split into
+ * (Sec. 5.1.1).  No error: a NULL cfg is ignored. */
 void trees_default_config(trees_config_t *cfg);
 
 /* ------------------------------------------------------------ context */
 typedef struct trees_ctx trees_ctx;
 
 /* Device bytes a context with `capacity_slots` TV slots needs (TV columns,
- * map lists, trace, control block).  Returns 0 for invalid arguments. */
+ * map lists, trace, control block): the Task Vector of Sec. 4 / 5.1.2 laid
+ * out as a structure of arrays, 24 bytes per slot, plus the book-keeping
+ * words of Sec. 5.1.2 (nextFreeCore, joinScheduled, mapScheduled) and the
+ * epoch-range stack.  Returns 0 for invalid arguments. */
 size_t trees_bytes_for(size_t capacity_slots, const trees_config_t *cfg);
 
 /* Creates a context on the current CUDA device that owns a task vector of
- * capacity_slots entries (allocated with cudaMalloc).  cfg may be NULL
- * (defaults).  capacity_slots must be in [1, 2^32-1].  Errors: INVALID_ARG,
+ * capacity_slots entries (allocated with cudaMalloc): the Task Vector, Task
+ * Mask Stack and book-keeping structures of Sec. 4 and Sec. 5.1.2, all in GPU
+ * memory as Sec. 5.1.2 places them (the TMS as per-entry epoch numbers plus a
+ * stack of NDRanges).  TV slot i is TVM core i (Sec. 5.1.1).  cfg may be NULL
+ * (defaults).  capacity_slots must be in [1, 2^32-1].  *out receives the
+ * context, owned by the caller until trees_destroy.  Errors: INVALID_ARG,
  * CUDA (allocation failed). */
 int trees_create(size_t capacity_slots, const trees_config_t *cfg, trees_ctx **out);
 
-/* Same, but carves everything out of a caller-owned device buffer of `bytes`
- * bytes (256-byte aligned), e.g. a torch tensor; capacity is the largest that
- * fits.  The buffer must outlive the context. */
+/* Same structures (Sec. 5.1.2), but carved out of a caller-owned device
+ * buffer of `bytes` bytes (256-byte aligned), e.g. a torch tensor; capacity
+ * is the largest that fits.  The buffer must outlive the context and is never
+ * freed by the library.  Errors: INVALID_ARG (NULL, unaligned or too small),
+ * CUDA. */
 int trees_create_on(void *dev_buf, size_t bytes, const trees_config_t *cfg, trees_ctx **out);
 
-/* Releases everything the context allocated (not caller buffers). */
+/* Releases the Task Vector and book-keeping structures the context
+ * allocated (Sec. 5.1.2); never a caller buffer.  Call it once the context is
+ * idle (after trees_sync).  NULL is ignored. */
 void trees_destroy(trees_ctx *ctx);
 
-/* Task-vector capacity of the context, in slots. */
+/* Task-vector capacity of the context, in slots (TVM cores, Sec. 5.1.1). */
 size_t trees_capacity(const trees_ctx *ctx);
 
 /* Launch geometry the context uses: blocks in the persistent grid, threads
- * per block, SM count. */
+ * per block, SM count (the physical cores onto which Sec. 5.1.1 maps the
+ * TVM's abstract cores).  Any output pointer may be NULL.  Errors:
+ * INVALID_ARG (NULL context). */
 int trees_geometry(const trees_ctx *ctx, int32_t *grid_blocks, int32_t *block_size, int32_t *sms);
 
 /* ------------------------------------------------------------ one job */
@@ -186,11 +201,16 @@ typedef struct {
 int trees_run(trees_ctx *ctx, const trees_job_t *job, void *stream);
 
 /* Waits for the context's last run and returns its status (TREES_OK or the
- * first device-side error). */
+ * first device-side error).  This is the end of the run Sec. 5.2.4 detects
+ * when the NDRange stack is empty after Phase 3; the status words are the
+ * sticky flags the run sets instead of trapping. */
 int trees_sync(trees_ctx *ctx);
 
-/* Reads the result word of a TV slot after trees_sync (slot 0 = the root's
- * emitted value: fib(n), the N-Queens count).  Errors: INVALID_ARG. */
+/* Reads the result word of a TV slot after trees_sync: the value an `emit`
+ * stored in the task's own entry (Sec. 4.2, 4.3.2); slot 0 holds the root
+ * task's, e.g. fib(n) or the N-Queens count, since the root sits in TV entry 0
+ * (Sec. 5.2.1).  *out is host memory.  Errors: INVALID_ARG (NULL, or slot
+ * beyond the capacity), CUDA. */
 int trees_result(trees_ctx *ctx, uint32_t slot, uint64_t *out);
 
 typedef struct {

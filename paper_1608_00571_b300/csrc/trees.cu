@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1096,7 +1097,8 @@ constexpr size_t NOALLOC_BYTES = 26u << 20;     // 26 MiB: TV columns (24 MiB) +
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 struct NoallocDevice {
-    bool ready = false;
+    std::mutex mu;         // serialises the set-up of host threads making a first call at once
+    bool ready = false;    // written under mu; read under mu
     char *base = nullptr;  // device address of g_noalloc_scratch on this device
     int grid = 0, sms = 0;
 };
@@ -1104,8 +1106,10 @@ NoallocDevice g_noalloc_dev[64];
 
 // Once per device, with that device current: find the device address of the
 // static array (host code only sees a host-side stand-in for the symbol) and
-// the cooperative grid size.
+// the cooperative grid size.  Threads that race on a device's first call
+// wait on its mutex; a set-up that failed is tried again by the next call.
 int noalloc_setup(int dev, NoallocDevice *d) {
+    std::lock_guard<std::mutex> lock(d->mu);
     if (d->ready) return TREES_OK;
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {

@@ -46,3 +46,25 @@ def test_fft_alg_bytes_and_host_cpu():
 def test_nqueens_table_matches_the_oracle():
     for n, count in bench.NQUEENS_SOLUTIONS.items():
         assert oracle.nqueens(n)[0] == count
+
+
+def test_cpu_baseline_times_the_plain_recursion():
+    cb = bench.cpu_baseline(0.2, bench.FIB34_TASKS)
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["unit"] == "tasks/s"
+    assert abs(cb["value"] - cb["fib34_jobs_per_s"] * bench.FIB34_TASKS) <= 1e-6 * cb["value"]
+    assert cb["fib34_calls_per_s"] == cb["fib34_jobs_per_s"] * 18454929
+    assert cb["tvm_simulator"]["value"] > 0
+    assert bench.FIB34_TASKS == sum(oracle.fib_task_counts(34))
+
+
+def test_reference_arm_prints_one_line_on_rank_0(capsys):
+    import json
+
+    class A:
+        steps, warmup = 2, 1
+    bench.run_reference(A(), 0, 1)
+    lines = [x for x in capsys.readouterr().out.splitlines() if x.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "tasks/s" and d["steps"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0

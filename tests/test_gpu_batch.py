@@ -176,8 +176,8 @@ def test_server_replay_results_equal_alone_and_in_the_mix(plain):
 
 def test_full_job_mix_4096():
     """The batched configuration at full size: 4096 jobs (seed 42) in one launch,
-    checked against closed forms (fib), the oracle (N-Queens) and a sorted copy
-    (mergesort)."""
+    checked against closed forms (fib), the oracle (N-Queens, and the first 64
+    sorts) and, key for key, a sorted copy of every other sort's input."""
     kind, param, kseed = gen.jobs(42, 4096)
     jobs, keys = [], {}
     for i in range(4096):
@@ -209,11 +209,12 @@ def test_full_job_mix_4096():
                 sols, rows, joins = nq_cache.setdefault(n, oracle.nqueens(n))
                 assert r["result"] == sols and r["tasks"] == rows + joins and r["epochs"] == 2 * n + 1
         for n_checked, (i, (d, sc, k)) in enumerate(keys.items()):
-            got = d.cpu().numpy().view(np.uint32)
             if n_checked < 64:
-                assert np.array_equal(got, np.sort(k)), i
+                assert np.array_equal(d.cpu().numpy().view(np.uint32), oracle.mergesort(k)), i
             else:
-                assert bool((got[1:] >= got[:-1]).all()) and int(got.astype(np.uint64).sum()) == \
-                    int(k.astype(np.uint64).sum()), i
+                # every other sort against a sorted copy of its own input made on the device (torch.sort
+                # of the keys as unsigned values: int64 keeps their order), key for key
+                want = torch.sort(torch.from_numpy(k.astype(np.int64)).cuda()).values
+                assert torch.equal(d.to(torch.int64) & 0xFFFFFFFF, want), i
     finally:
         T.trees_destroy(ctx)

@@ -1,0 +1,280 @@
+"""Parity with the CPU oracle at the full workload sizes, and with grids so
+small that every block runs many tiles per epoch.
+
+Full sizes: fib(34) with no cutoff (27,682,393 task executions in 67
+epochs, Sec. 6.2), fib(34) with leaves n <= 12 computed in-task, mergesort
+of 2^26 uint32 keys drawn from splitmix64 seed 1 (Sec. 6.4, map leaf sorts
+and merge-path merges), BFS on the R-MAT scale-22 graph from source 0
+(Sec. 6.3) and SSSP on the same graph with weights in [1, 255].  Every
+block shape the autotuner may pick (block sizes 128..1024 by 1, 2 or 4 slots
+per thread) is run, so whichever configuration the benchmark times has been
+compared with the oracle: results exactly, and the whole per-epoch trace
+(epoch number, NDRange, valid tasks, forks, join flag, maps) against the
+sequential TVM simulator.
+
+Small grids (2 and 8 blocks) force each block through many Phase-2 tiles
+per epoch: the pipelined tile loads, the join-operand prefetch of the
+successor tile and the multi-tile merge and expansion paths.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1608_00571_b300 as T
+from paper_1608_00571_b300 import gen
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(bs, tpt) for bs in (128, 256, 512, 1024) for tpt in (1, 2, 4)]
+TRACE_FIELDS = ("cen", "lo", "hi", "valid", "forks", "joined", "maps")
+# a BFS visit's adjacency scan is a map on the GPU and a loop in the simulator: maps are not compared
+BFS_FIELDS = ("cen", "lo", "hi", "valid", "forks", "joined")
+BFS_KEYS = ("epochs", "tasks", "forks", "joins", "peak_slots", "final_slots")
+FIB34 = 5702887
+
+
+class Ctx:
+    def __init__(self, cap, **cfg):
+        self.h = T.trees_create(cap, T.trees_default_config(**cfg))
+
+    def __enter__(self):
+        return self.h
+
+    def __exit__(self, *a):
+        T.trees_destroy(self.h)
+
+
+def run(ctx, job):
+    T.trees_run(ctx, job, torch.cuda.current_stream())
+    return T.trees_sync(ctx)
+
+
+def check_run(ctx, sim, fields=TRACE_FIELDS,
+              keys=("epochs", "tasks", "forks", "joins", "maps", "peak_slots", "final_slots")):
+    st = T.trees_stats(ctx)
+    for k in keys:
+        assert st[k] == sim["stats"][k], (k, st[k], sim["stats"][k])
+    tr = T.trees_trace(ctx)
+    ref = sim["trace"]
+    assert len(tr) == len(ref)
+    for i, (g, o) in enumerate(zip(tr, ref)):
+        for f in fields:
+            assert g[f] == int(o[f]), (i, f, g, o)
+
+
+# ------------------------------------------------------------------ fib(34)
+
+@pytest.fixture(scope="module")
+def fib34_sim():
+    sim = oracle.tvm_run(oracle.FIB, fib_n=34)
+    assert sim["stats"]["root_result"] == FIB34 == oracle.fib(34)[0]
+    assert sim["stats"]["epochs"] == 67 and sim["stats"]["tasks"] == 27682393
+    return sim
+
+
+@pytest.fixture(scope="module")
+def fib34c12_sim():
+    sim = oracle.tvm_run(oracle.FIB, fib_n=34, fib_cutoff=12)
+    assert sim["stats"]["epochs"] == 45 and sim["stats"]["tasks"] == 139102
+    return sim
+
+
+@pytest.mark.parametrize("bs,tpt", SHAPES)
+def test_fib34_every_shape(fib34_sim, bs, tpt):
+    with Ctx(18_454_929, block_size=bs, tasks_per_thread=tpt, map_capacity=1, trace=1) as ctx:
+        for _ in range(2):  # a second run on the same context starts from a clean state
+            assert run(ctx, T.make_job(T.TREES_PROG_FIB, n=34)) == T.TREES_OK
+            assert T.trees_result(ctx, 0) == FIB34
+            check_run(ctx, fib34_sim)
+
+
+@pytest.mark.parametrize("sched", [T.TREES_SCHED_GRAPH, T.TREES_SCHED_HOSTLOOP])
+@pytest.mark.parametrize("bs,tpt", [(256, 4), (1024, 2)])
+def test_fib34_other_schedulers(fib34_sim, sched, bs, tpt):
+    with Ctx(18_454_929, scheduler=sched, block_size=bs, tasks_per_thread=tpt, map_capacity=1, trace=1) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_FIB, n=34)) == T.TREES_OK
+        assert T.trees_result(ctx, 0) == FIB34
+        check_run(ctx, fib34_sim)
+
+
+@pytest.mark.parametrize("bs,tpt", SHAPES)
+def test_fib34_cutoff12_every_shape(fib34c12_sim, bs, tpt):
+    with Ctx(92_735, block_size=bs, tasks_per_thread=tpt, map_capacity=1, trace=1) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_FIB, n=34, cutoff=12)) == T.TREES_OK
+        assert T.trees_result(ctx, 0) == FIB34
+        check_run(ctx, fib34c12_sim)
+
+
+def test_fib34_capacity_one_slot_short_is_an_error():
+    # the task vector's peak is the whole tree, 2F(35) - 1 = 18,454,929 slots
+    with Ctx(18_454_928, block_size=256, tasks_per_thread=4, map_capacity=1) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_FIB, n=34)) == T.TREES_ERR_CAPACITY
+    with Ctx(18_454_929, block_size=256, tasks_per_thread=4, map_capacity=1) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_FIB, n=34)) == T.TREES_OK
+        assert T.trees_result(ctx, 0) == FIB34
+
+
+# ------------------------------------------------------------------ mergesort of 2^26 keys
+
+@pytest.fixture(scope="module")
+def sort26():
+    keys = gen.keys_u32(1, 1 << 26)
+    sim = oracle.tvm_run(oracle.MERGESORT, keys=keys)
+    assert sim["stats"]["epochs"] == 33 and sim["stats"]["maps"] == 131071
+    src = torch.from_numpy(keys.view(np.int32)).cuda()
+    want = torch.from_numpy(sim["keys"].view(np.int32)).cuda()
+    return keys, sim, src, want
+
+
+def sort_on_gpu(sim, src, want, **cfg):
+    kd = src.clone()
+    sc = torch.empty_like(src)
+    with Ctx(1 << 18, **cfg, trace=1) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_MERGESORT, n=src.numel(), keys=kd, scratch=sc)) == T.TREES_OK
+        check_run(ctx, sim)
+    torch.cuda.synchronize()
+    assert torch.equal(kd, want)  # every key, bit for bit
+    del kd, sc
+
+
+@pytest.mark.parametrize("bs,tpt", SHAPES)
+def test_mergesort_2p26_every_shape(sort26, bs, tpt):
+    _, sim, src, want = sort26
+    sort_on_gpu(sim, src, want, block_size=bs, tasks_per_thread=tpt)
+
+
+@pytest.mark.parametrize("sched", [T.TREES_SCHED_GRAPH, T.TREES_SCHED_HOSTLOOP])
+def test_mergesort_2p26_other_schedulers(sort26, sched):
+    _, sim, src, want = sort26
+    sort_on_gpu(sim, src, want, block_size=256, tasks_per_thread=1, scheduler=sched)
+
+
+def test_mergesort_2p26_equals_plain_recursive_oracle(sort26):
+    keys, sim, _, _ = sort26
+    # the simulator's output is the recursive top-down mergesort's
+    assert np.array_equal(sim["keys"], oracle.mergesort(keys))
+
+
+# ------------------------------------------------------------------ BFS and SSSP on R-MAT scale 22
+
+@pytest.fixture(scope="module")
+def rmat22():
+    row_ptr, col, info = gen.rmat(22, 16, seed=2)
+    assert info["nv"] == 1 << 22 and info["m"] == 128_309_256
+    sim = oracle.tvm_run(oracle.BFS, row_ptr=row_ptr, col=col, src=0)
+    level, reached = oracle.bfs(row_ptr, col, 0)
+    assert np.array_equal(sim["level"], level)
+    rp, cl = torch.from_numpy(row_ptr).cuda(), torch.from_numpy(col).cuda()
+    return row_ptr, col, sim, level, reached, rp, cl
+
+
+@pytest.mark.parametrize("bs,tpt", SHAPES)
+def test_bfs_rmat22_every_shape(rmat22, bs, tpt):
+    row_ptr, col, sim, level, reached, rp, cl = rmat22
+    lv = torch.empty(row_ptr.size - 1, dtype=torch.int32, device="cuda")
+    with Ctx(1 << 23, block_size=bs, tasks_per_thread=tpt, trace=1) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_BFS, n=0, row_ptr=rp, col=cl, level=lv,
+                                   nv=row_ptr.size - 1)) == T.TREES_OK
+        check_run(ctx, sim, BFS_FIELDS, BFS_KEYS)
+        assert T.trees_stats(ctx)["tasks"] == reached
+    assert np.array_equal(lv.cpu().numpy(), level)
+
+
+@pytest.mark.parametrize("sched", [T.TREES_SCHED_GRAPH, T.TREES_SCHED_HOSTLOOP])
+def test_bfs_rmat22_other_schedulers(rmat22, sched):
+    row_ptr, col, sim, level, reached, rp, cl = rmat22
+    lv = torch.empty(row_ptr.size - 1, dtype=torch.int32, device="cuda")
+    with Ctx(1 << 23, scheduler=sched, block_size=256, tasks_per_thread=2, trace=1) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_BFS, n=0, row_ptr=rp, col=cl, level=lv,
+                                   nv=row_ptr.size - 1)) == T.TREES_OK
+        check_run(ctx, sim, BFS_FIELDS, BFS_KEYS)
+    assert np.array_equal(lv.cpu().numpy(), level)
+
+
+@pytest.fixture(scope="module")
+def sssp22(rmat22):
+    row_ptr, col, _, level, reached, rp, cl = rmat22
+    w = gen.weights(3, row_ptr, col)
+    dist, nreach = oracle.sssp_dijkstra(row_ptr, col, w, 0)
+    assert nreach == reached
+    return w, dist, torch.from_numpy(w.view(np.int32)).cuda()
+
+
+@pytest.mark.parametrize("bs,tpt", [(256, 1), (256, 2), (512, 1), (1024, 1), (128, 4)])
+def test_sssp_rmat22_distances_equal_dijkstra(rmat22, sssp22, bs, tpt):
+    row_ptr, col, _, level, reached, rp, cl = rmat22
+    w, want, wt = sssp22
+    nv = row_ptr.size - 1
+    dist = torch.empty(nv, dtype=torch.int64, device="cuda")
+    sched = torch.empty(nv, dtype=torch.int32, device="cuda")
+    with Ctx(3 * nv, block_size=bs, tasks_per_thread=tpt, trace=1) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_SSSP, n=0, row_ptr=rp, col=cl, weight=wt, nv=nv, dist=dist,
+                                   sched=sched)) == T.TREES_OK
+        st = T.trees_stats(ctx)
+        tr = T.trees_trace(ctx)
+    assert np.array_equal(dist.cpu().numpy().view(np.uint64), want)
+    # counts that depend on the order of races, by properties: every reached vertex is relaxed at
+    # least once, and each epoch's range is the previous epoch's forks
+    assert st["tasks"] >= reached and st["joins"] == 0
+    for a, b in zip(tr, tr[1:]):
+        assert (b["lo"], b["hi"]) == (a["hi"], a["hi"] + a["forks"]) or a["forks"] == 0
+
+
+# ------------------------------------------------------------------ many tiles per block
+
+@pytest.mark.parametrize("grid", [2, 8])
+@pytest.mark.parametrize("bs,tpt", [(128, 1), (256, 4), (512, 2), (1024, 4)])
+@pytest.mark.parametrize("sched", [T.TREES_SCHED_PERSISTENT, T.TREES_SCHED_GRAPH])
+def test_fib24_small_grid(grid, bs, tpt, sched):
+    sim = oracle.tvm_run(oracle.FIB, fib_n=24)
+    with Ctx(1 << 17, grid_blocks=grid, block_size=bs, tasks_per_thread=tpt, scheduler=sched, map_capacity=1,
+             trace=1) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_FIB, n=24)) == T.TREES_OK
+        assert T.trees_result(ctx, 0) == oracle.fib(24)[0] == 46368
+        assert T.trees_stats(ctx)["grid_blocks"] == grid
+        check_run(ctx, sim)
+
+
+@pytest.mark.parametrize("grid", [2, 8])
+@pytest.mark.parametrize("bs,tpt", [(256, 4), (1024, 1)])
+def test_fib24_cutoff_and_nqueens_small_grid(grid, bs, tpt):
+    cfg = dict(grid_blocks=grid, block_size=bs, tasks_per_thread=tpt, map_capacity=1, trace=1)
+    sim = oracle.tvm_run(oracle.FIB, fib_n=24, fib_cutoff=6)
+    with Ctx(1 << 17, **cfg) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_FIB, n=24, cutoff=6)) == T.TREES_OK
+        assert T.trees_result(ctx, 0) == 46368
+        check_run(ctx, sim)
+    sim = oracle.tvm_run(oracle.NQUEENS, nq_n=10)
+    with Ctx(1 << 17, **cfg) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_NQUEENS, n=10)) == T.TREES_OK
+        assert T.trees_result(ctx, 0) == oracle.nqueens(10)[0] == 724
+        check_run(ctx, sim)
+
+
+@pytest.mark.parametrize("grid", [2, 8])
+@pytest.mark.parametrize("bs,tpt", [(256, 1), (1024, 4), (128, 2)])
+@pytest.mark.parametrize("sched", [T.TREES_SCHED_PERSISTENT, T.TREES_SCHED_GRAPH])
+def test_mergesort_2p20_small_grid(grid, bs, tpt, sched):
+    n = (1 << 20) + 3
+    keys = gen.keys_u32(77, n)
+    sim = oracle.tvm_run(oracle.MERGESORT, keys=keys)
+    kd = torch.from_numpy(keys.view(np.int32)).cuda()
+    sc = torch.empty_like(kd)
+    with Ctx(1 << 14, grid_blocks=grid, block_size=bs, tasks_per_thread=tpt, scheduler=sched, trace=1) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_MERGESORT, n=n, keys=kd, scratch=sc)) == T.TREES_OK
+        check_run(ctx, sim)
+    assert np.array_equal(kd.cpu().numpy().view(np.uint32), sim["keys"])
+
+
+@pytest.mark.parametrize("grid", [2, 8])
+def test_bfs_rmat16_small_grid(grid):
+    row_ptr, col, _ = gen.rmat(16, 16, seed=2)
+    sim = oracle.tvm_run(oracle.BFS, row_ptr=row_ptr, col=col, src=0)
+    rp, cl = torch.from_numpy(row_ptr).cuda(), torch.from_numpy(col).cuda()
+    lv = torch.empty(row_ptr.size - 1, dtype=torch.int32, device="cuda")
+    with Ctx(1 << 17, grid_blocks=grid, block_size=256, tasks_per_thread=2, trace=1) as ctx:
+        assert run(ctx, T.make_job(T.TREES_PROG_BFS, n=0, row_ptr=rp, col=cl, level=lv,
+                                   nv=row_ptr.size - 1)) == T.TREES_OK
+        check_run(ctx, sim, BFS_FIELDS, BFS_KEYS)
+    assert np.array_equal(lv.cpu().numpy(), sim["level"])

@@ -1,5 +1,6 @@
-"""The allocation-free fib entry point (trees_fib_noalloc) against the
-regular entry point (trees_run on a context), through the C ABI.
+"""The allocation-free fib entry point (trees_fib_noalloc) against the CPU
+oracle's recursive Fibonacci and the regular entry point (trees_run on a
+context), through the C ABI.
 
 Callers that cannot allocate device memory while they run -- stream
 captures that must not allocate, hosts with a fixed GPU memory budget,
@@ -10,6 +11,7 @@ collected last so that a failure here never hides the other tests.
 import pytest
 import torch
 
+import oracle
 import paper_1608_00571_b300 as T
 
 pytestmark = pytest.mark.gpu
@@ -25,28 +27,33 @@ def regular_fib(n, cutoff):
         T.trees_destroy(ctx)
 
 
-def test_noalloc_matches_regular_entry_point_twice_in_a_row():
+def noalloc_fib(n, cutoff, out, status, stream):
+    out.fill_(-1)
+    status.fill_(-1)
+    assert T.trees_fib_noalloc(n, cutoff, out, status, stream) == T.TREES_OK
+    torch.cuda.synchronize()
+    assert int(status.item()) == T.TREES_OK
+    return int(out.item())
+
+
+def test_noalloc_matches_oracle_and_regular_entry_point_twice_in_a_row():
     stream = torch.cuda.current_stream()
     out = torch.zeros(1, dtype=torch.int64, device="cuda")
     status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
     for n, cutoff in ((27, 0), (28, 12)):  # two calls in a row share the static array
-        assert T.trees_fib_noalloc(n, cutoff, out, status, stream) == T.TREES_OK
-        torch.cuda.synchronize()
-        assert int(status.item()) == T.TREES_OK
-        assert int(out.item()) == regular_fib(n, cutoff)
+        got = noalloc_fib(n, cutoff, out, status, stream)
+        assert got == oracle.fib(n)[0] == regular_fib(n, cutoff)
     # the same job twice in a row gives the same answer (state left by the previous call is cleared)
     for _ in range(2):
-        out.zero_()
-        assert T.trees_fib_noalloc(25, 0, out, status, stream) == T.TREES_OK
-        torch.cuda.synchronize()
-        assert int(status.item()) == T.TREES_OK and int(out.item()) == regular_fib(25, 0) == 75025
+        assert noalloc_fib(25, 0, out, status, stream) == oracle.fib(25)[0] == regular_fib(25, 0) == 75025
 
 
-def test_noalloc_rejects_jobs_beyond_its_static_capacity():
+def test_noalloc_capacity_edge():
+    stream = torch.cuda.current_stream()
     out = torch.zeros(1, dtype=torch.int64, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    assert T.trees_fib_noalloc(29, 0, out, status, None) == T.TREES_ERR_CAPACITY   # 2F(30)-1 > 2^20
-    assert T.trees_fib_noalloc(34, 12, out, status, None) == T.TREES_OK           # 92,735 tasks fit
-    torch.cuda.synchronize()
-    assert int(out.item()) == 5702887 and int(status.item()) == T.TREES_OK
-    assert T.trees_fib_noalloc(20, 0, None, status, None) == T.TREES_ERR_INVALID_ARG
+    # fib(28) with no cutoff peaks at 2F(29) - 1 = 1,028,457 of the 1,048,576 static slots
+    assert noalloc_fib(28, 0, out, status, stream) == oracle.fib(28)[0] == 317811
+    assert T.trees_fib_noalloc(29, 0, out, status, stream) == T.TREES_ERR_CAPACITY  # 2F(30) - 1 > 2^20
+    assert noalloc_fib(34, 12, out, status, stream) == oracle.fib(34)[0] == 5702887  # 92,735 slots fit
+    assert T.trees_fib_noalloc(20, 0, None, status, stream) == T.TREES_ERR_INVALID_ARG
