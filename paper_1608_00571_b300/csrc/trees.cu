@@ -114,14 +114,16 @@ __global__ void __launch_bounds__(BS) k_epoch(Ctl *ctl, Conf c, unsigned long lo
     }
     Acc acc = {0u, 0u, 0u};
     int par = 0;
+    bool jn = false;
     for (unsigned long long t0 = (unsigned long long)lo + (unsigned long long)blockIdx.x * (BS * TPT); t0 < hi;
          t0 += (unsigned long long)gridDim.x * (BS * TPT)) {
         TileLoad<TPT> L;
         tile_load<BS, TPT, PM_ALL>(c, t0, hi, LOAD_ON_DEMAND, L);
-        epoch_tile<BS, TPT, PM_ALL>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, LOAD_ON_DEMAND, L,
-                                    hi - lo <= (uint32_t)(BS * TPT), 0u);
+        jn |= epoch_tile<BS, TPT, PM_ALL>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, LOAD_ON_DEMAND, L,
+                                          hi - lo <= (uint32_t)(BS * TPT), 0u).joined;
         par ^= 1;
     }
+    publish_join(ctl, ep, jn);
     trace_valid_add<BS>(c, e, acc.valid, sm);
     block_add_stats<BS>(blk, acc, sm);
 }
@@ -442,13 +444,19 @@ static int finish_create(trees_ctx *x) {
     return TREES_OK;
 }
 
-// Co-resident grid for a kernel under the context's limits (cached).
-static int kernel_grid(trees_ctx *x, const void *kern) {
+// Co-resident grid for a kernel launched with `smem` bytes of dynamic shared
+// memory, under the context's limits (cached).  Raises the kernel's dynamic
+// shared memory limit on this device first when smem needs it.
+static int kernel_grid(trees_ctx *x, const void *kern, size_t smem = 0) {
     if (!kern) return 0;
     auto it = x->grid_cache.find(kern);
     if (it != x->grid_cache.end()) return it->second;
+    if (smem && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, x->bs, 0) != cudaSuccess || occ < 1) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, x->bs, smem) != cudaSuccess || occ < 1) return 0;
     const int per_sm = x->cfg.blocks_per_sm > 0 ? std::min(x->cfg.blocks_per_sm, occ) : occ;
     int g = x->sms * per_sm;
     if (x->cfg.grid_blocks > 0) g = std::min(x->cfg.grid_blocks, x->sms * occ);
@@ -881,10 +889,11 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
             return TREES_OK;
         }
         const void *kern = persistent_kernel(job->program, x->bs, x->cfg.tasks_per_thread);
-        const int grid = kernel_grid(x, kern);
+        const size_t smem = persistent_smem_bytes(program_mask(job->program), x->bs, x->cfg.tasks_per_thread);
+        const int grid = kernel_grid(x, kern, smem);
         if (!kern || grid < 1) return TREES_ERR_CUDA;
         x->last_grid = grid;
-        if (cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(x->bs), args, 0, st) != cudaSuccess) {
+        if (cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(x->bs), args, smem, st) != cudaSuccess) {
             cudaGetLastError();
             return TREES_ERR_CUDA;
         }
@@ -1118,7 +1127,13 @@ int noalloc_setup(int dev, NoallocDevice *d) {
     }
     int sms = 0, occ = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TREES_ERR_CUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel_fib(1024, 2), 1024, 0) !=
+    const size_t smem = persistent_smem_bytes(PM_FIB, 1024, 2);
+    if (smem && cudaFuncSetAttribute(persistent_kernel_fib(1024, 2), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return TREES_ERR_CUDA;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_kernel_fib(1024, 2), 1024, smem) !=
             cudaSuccess || occ < 1)
         return TREES_ERR_CUDA;
     if (make_layout(NOALLOC_CAP, 1, 1, STK_CAP).total > NOALLOC_BYTES) return TREES_ERR_CUDA;
@@ -1183,7 +1198,8 @@ extern "C" int trees_fib_noalloc(uint32_t n, uint32_t cutoff, uint64_t *dev_resu
     k_setup<<<1, 256, 0, st>>>(ctl, c, TREES_TASK_FIB, n, 0u);
     if (cudaGetLastError() != cudaSuccess) return TREES_ERR_CUDA;
     void *args[] = {&ctl, &c, &blk};
-    if (cudaLaunchCooperativeKernel(persistent_kernel_fib(1024, 2), dim3(d->grid), dim3(1024), args, 0, st) !=
+    if (cudaLaunchCooperativeKernel(persistent_kernel_fib(1024, 2), dim3(d->grid), dim3(1024), args,
+                                    persistent_smem_bytes(PM_FIB, 1024, 2), st) !=
         cudaSuccess) {
         cudaGetLastError();
         return TREES_ERR_CUDA;

@@ -59,12 +59,64 @@ __host__ __device__ constexpr int persistent_min_blocks(int bs, uint32_t pm, int
     return tps / bs > 0 ? tps / bs : 1;
 }
 
-// Scheduler state a persistent block carries between epochs (thread 0's).
+// Dynamic shared memory of a persistent kernel.  The fib kernels run their
+// join ranges through a ring of asynchronous copies there (fib_join_tiles):
+// NA stages of (code, link) and NB of result pairs, 8 and 16 bytes per slot,
+// (NA, NB) = (4, 3) when that fits beside the kernel's static shared memory
+// at the residency its register budget targets (228 KB per SM, 1 KB of it
+// reserved per block), else (3, 2), else no ring (the register path).
+constexpr int SMEM_PER_SM = 228 * 1024, SMEM_RESERVED_PER_BLOCK = 1024;
+
+template <int BS, int TPT, uint32_t PM>
+__host__ __device__ constexpr int ring_budget() {
+    return PM != PM_FIB ? 0
+                        : SMEM_PER_SM / persistent_min_blocks(BS, PM, TPT) - SMEM_RESERVED_PER_BLOCK -
+                              ((int)sizeof(Smem<BS>) + 256);  // the block's static shared memory, rounded up
+}
+
+// (NA, NB) packed as NA * 16 + NB, or 0.
+template <int BS, int TPT, uint32_t PM>
+__host__ __device__ constexpr int ring_depths() {
+    return ring_budget<BS, TPT, PM>() >= 80 * BS * TPT ? 4 * 16 + 3
+           : ring_budget<BS, TPT, PM>() >= 56 * BS * TPT ? 3 * 16 + 2
+                                                         : 0;
+}
+
+template <int BS, int TPT, uint32_t PM>
+__host__ __device__ constexpr size_t ring_bytes() {
+    return (size_t)((ring_depths<BS, TPT, PM>() >> 4) * 8 + (ring_depths<BS, TPT, PM>() & 15) * 16) * BS * TPT;
+}
+
+// Dynamic shared memory bytes k_persistent<bs, tpt, program mask pm> is launched with.
+inline size_t persistent_smem_bytes(uint32_t pm, int bs, int tpt) {
+    if (pm != PM_FIB) return 0;
+    switch (bs * 10 + tpt) {
+    case 1281: return ring_bytes<128, 1, PM_FIB>();
+    case 1282: return ring_bytes<128, 2, PM_FIB>();
+    case 1284: return ring_bytes<128, 4, PM_FIB>();
+    case 2561: return ring_bytes<256, 1, PM_FIB>();
+    case 2562: return ring_bytes<256, 2, PM_FIB>();
+    case 2564: return ring_bytes<256, 4, PM_FIB>();
+    case 5121: return ring_bytes<512, 1, PM_FIB>();
+    case 5122: return ring_bytes<512, 2, PM_FIB>();
+    case 5124: return ring_bytes<512, 4, PM_FIB>();
+    case 10241: return ring_bytes<1024, 1, PM_FIB>();
+    case 10242: return ring_bytes<1024, 2, PM_FIB>();
+    case 10244: return ring_bytes<1024, 4, PM_FIB>();
+    default: return 0;
+    }
+}
+
+// Scheduler state a persistent block carries between epochs.  Only thread 0
+// touches it, so it lives in shared memory rather than in every thread's
+// registers.
 struct SchedState {
     unsigned long long forks_total;
     uint32_t peak;
+    uint32_t bar;  // grid barriers passed
     // trace timestamps (block 0): previous epoch's end, end of Phase 2, of partition, of maps
     unsigned long long t_prev, t_p2, t_pt, t_mp;
+    unsigned long long t_solo;  // start of the current solo run
 };
 
 // Phase 1 (thread 0): pop (CEN, NDRange) for epoch e and set
@@ -159,7 +211,7 @@ __device__ __forceinline__ bool solo_range(const Conf &c, uint32_t lo, uint32_t 
 // other blocks.
 template <int BS, int TPT, uint32_t PM>
 __device__ uint32_t solo_epochs(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t e, Acc &acc, SchedState &st) {
-    const unsigned long long t_start = threadIdx.x == 0 ? globaltimer() : 0ull;
+    if (threadIdx.x == 0) st.t_solo = globaltimer();
     for (;;) {
         const uint32_t cen = sm.cen, lo = sm.lo, hi = sm.hi, base = sm.base, ep = e % 3u;
         const int mode = sm.rjoin ? LOAD_JOIN : LOAD_FRESH;
@@ -172,6 +224,14 @@ __device__ uint32_t solo_epochs(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t 
         for (uint32_t t0 = lo; t0 < hi; t0 += (uint32_t)(BS * TPT)) {
             const bool more = t0 + (uint32_t)(BS * TPT) < hi;
             if (more) tile_load<BS, TPT, PM>(c, t0 + (uint32_t)(BS * TPT), hi, mode, nxt);
+            if constexpr (joins_never_fork<PM>()) {
+                if (mode == LOAD_JOIN) {  // continuations only: no scan, no allocation
+                    join_tile<BS, TPT, PM>(c, sm, t0, cen, e, acc, par, cur, false, nullptr);
+                    if (more) cur = nxt;
+                    par ^= 1;
+                    continue;
+                }
+            }
             const TileOut t = epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode, cur,
                                                       true, o.forks);
             o.forks += t.forks;
@@ -188,7 +248,7 @@ __device__ uint32_t solo_epochs(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t 
             phase3<BS>(c, ctl, sm, e, o.forks, jf, 0ull, 0ull, st);
             phase1<BS>(c, ctl, sm, e + 1u);
             if (o.over) sm.stop = 3;  // the capacity error is set; the grid barrier reports it
-            sm.solo_late = globaltimer() - t_start > c.timeout_ns / 4u;
+            sm.solo_late = globaltimer() - st.t_solo > c.timeout_ns / 4u;
         }
         ++e;  // on every thread: the epoch number picks the counter slot and the trace entry
         __syncthreads();
@@ -237,10 +297,11 @@ template <int BS, int TPT, uint32_t PM, typename UP = NoUserProgram>
 __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_persistent(Ctl *ctl, Conf c, unsigned long long *blk) {
     __shared__ Smem<BS> sm;
     __shared__ uint32_t sm_e;
-    uint32_t bar = 0;
+    __shared__ SchedState st;
+    extern __shared__ __align__(16) uint32_t ring[];  // ring_bytes<BS, TPT, PM>() of dynamic shared memory
     Acc acc = {0u, 0u, 0u};
-    SchedState st = {0ull, 1u, 0ull, 0ull, 0ull, 0ull};
     if (threadIdx.x == 0) {
+        st = SchedState{0ull, 1u, 0u, 0ull, 0ull, 0ull, 0ull, 0ull};
         sm.sp = 1;
         sm.stk[0] = Range{0u, 0u, 1u, 0u};
         sm.next = 1u;
@@ -261,7 +322,7 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
                     const uint32_t ne = solo_epochs<BS, TPT, PM>(c, ctl, sm, e, acc, st);
                     if (threadIdx.x == 0) sm_e = ne;
                 }
-                if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, e % 3u)) break;
+                if (!grid_sync_ep<BS>(ctl, &st.bar, c.timeout_ns, sm, e % 3u)) break;
                 if (blockIdx.x != 0) {
                     const uint32_t ne = adopt_solo_state<BS>(c, ctl, sm);
                     if (threadIdx.x == 0) sm_e = ne;
@@ -281,34 +342,68 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
         const bool solo = hi - lo <= (uint32_t)(BS * TPT);  // only block 0 has a tile
         const unsigned long long step = (unsigned long long)gridDim.x * (BS * TPT);
         unsigned long long t0 = (unsigned long long)lo + (unsigned long long)blockIdx.x * (BS * TPT);
-        TileLoad<TPT> cur, nxt;
-        if (t0 < hi) tile_load<BS, TPT, PM>(c, t0, hi, mode, cur);
-        const bool jr = mode == LOAD_JOIN;  // fib: prefetch the successor tile's join operands
-        bool jr_use = false;
-        for (; t0 < hi; t0 += step) {
-            const bool more = t0 + step < hi;
-            if (more) tile_load<BS, TPT, PM>(c, t0 + step, hi, mode, nxt);
-            epoch_tile<BS, TPT, PM, UP>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode, cur, solo, 0u, jr_use,
-                                        jr && more ? &nxt : nullptr);
-            jr_use = jr && more;
-            if (more) cur = nxt;
-            par ^= 1;
+        bool jn = false;     // some task of this thread joined (joinScheduled)
+        bool done = false;   // Phase 2 ran on one of the specialised paths
+        if constexpr (PM == PM_FIB) {
+            if (mode == LOAD_FRESH && !solo) {  // count, one reservation per chunk, write
+                jn = fib_fresh_tiles<BS, TPT>(c, ctl, sm, t0, step, hi, cen, base, ep, e, acc);
+                done = true;
+            }
+        }
+        if constexpr (PM == PM_FIB && ring_depths<BS, TPT, PM>() != 0) {
+            if (mode == LOAD_JOIN) {  // sums through the ring of asynchronous copies
+                constexpr int RD = ring_depths<BS, TPT, PM>();
+                fib_join_tiles<BS, TPT, (RD >> 4), (RD & 15)>(c, t0, step, hi, cen, e, acc, ring);
+                done = true;
+            }
+        }
+        if constexpr (joins_never_fork<PM>()) {
+            if (!done && mode == LOAD_JOIN) {  // continuations only: no scan, no allocation, no block barrier
+                TileLoad<TPT> cur, nxt;
+                if (t0 < hi) tile_load<BS, TPT, PM>(c, t0, hi, mode, cur);
+                bool jr_use = false;  // fib: the successor tile's join operands are prefetched
+                for (; t0 < hi; t0 += step) {
+                    const bool more = t0 + step < hi;
+                    if (more) tile_load<BS, TPT, PM>(c, t0 + step, hi, mode, nxt);
+                    join_tile<BS, TPT, PM>(c, sm, t0, cen, e, acc, par, cur, jr_use, more ? &nxt : nullptr);
+                    jr_use = more;
+                    if (more) cur = nxt;
+                    par ^= 1;
+                }
+                done = true;
+            }
+        }
+        if (!done) {
+            TileLoad<TPT> cur, nxt;
+            if (t0 < hi) tile_load<BS, TPT, PM>(c, t0, hi, mode, cur);
+            const bool jr = mode == LOAD_JOIN;  // fib: prefetch the successor tile's join operands
+            bool jr_use = false;
+            for (; t0 < hi; t0 += step) {
+                const bool more = t0 + step < hi;
+                if (more) tile_load<BS, TPT, PM>(c, t0 + step, hi, mode, nxt);
+                jn |= epoch_tile<BS, TPT, PM, UP>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode, cur, solo, 0u,
+                                                  jr_use, jr && more ? &nxt : nullptr).joined;
+                jr_use = jr && more;
+                if (more) cur = nxt;
+                par ^= 1;
+            }
         }
         trace_valid_add<BS>(c, e, acc.valid - v0, sm);
+        publish_join(ctl, ep, jn);
         if ((int32_t)e == c.stall_epoch && blockIdx.x == gridDim.x - 1) return;  // test hook: never arrives
-        if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, ep)) break;
+        if (!grid_sync_ep<BS>(ctl, &st.bar, c.timeout_ns, sm, ep)) break;
         if (stamp) st.t_p2 = st.t_pt = st.t_mp = globaltimer();
         const unsigned long long mt = sm.ep_mt, me = sm.ep_me;
         if (mt | me) {  // the map operations of this epoch run before the next one (Sec. 5.2.4)
             if constexpr ((PM & PM_MS) != 0u) {
                 if (needs_partition(mt)) {
                     partition_phase<BS>(c, mt, nullptr, 0u);
-                    if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, ep)) break;
+                    if (!grid_sync_ep<BS>(ctl, &st.bar, c.timeout_ns, sm, ep)) break;
                     if (stamp) st.t_pt = st.t_mp = globaltimer();
                 }
             }
             map_phase<BS, PM, UP>(c, ctl, sm, ep, e, cen, base, mt, me);
-            if (!grid_sync_ep<BS>(ctl, &bar, c.timeout_ns, sm, ep)) break;
+            if (!grid_sync_ep<BS>(ctl, &st.bar, c.timeout_ns, sm, ep)) break;
             if (stamp) st.t_mp = globaltimer();
         }
         // Phase 3: push the join range, then the fork range; or give the range back

@@ -749,8 +749,7 @@ __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> 
             }
         }
         acc.joins += joined;
-        if (__any_sync(0xffffffffu, joined != 0u) && (threadIdx.x & 31) == 0) ctl->join[ep] = 1u;  // joinScheduled
-        out.joined = joined != 0u;
+        out.joined = joined != 0u;  // the caller sets joinScheduled once per block (publish_join)
         out.over = over0 != 0u;
     }
     if constexpr ((PM & PM_MAPS) != 0u) {
@@ -760,6 +759,338 @@ __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> 
         if (PM == PM_FFT || c.rp.program == TREES_PROG_FFT) fft_task_bodies<PM, TPT>(c.rp, p);
     }
     return out;
+}
+
+// joinScheduled (Sec. 5.2.3) for one block: set once if any of its threads
+// joined this epoch, instead of once per warp and tile (every store to the
+// flag shares an L2 line with the fork counter's atomics).  Every thread of
+// the block calls it.
+__device__ __forceinline__ void publish_join(Ctl *ctl, uint32_t ep, bool joined) {
+    if (__syncthreads_or(joined) && threadIdx.x == 0) ctl->join[ep] = 1u;
+}
+
+// Programs whose join continuations never fork and never map (fib's sum,
+// N-Queens' sum, the traversals' visitAfter): a join range revisited holds
+// only continuations (each task of the range ran when the range was fresh
+// and either died or rewrote itself as its continuation; no other entry of
+// the range gets the range's epoch number), so its tiles allocate nothing and
+// need no block scan.
+template <uint32_t PM>
+__host__ __device__ constexpr bool joins_never_fork() {
+    return (PM & ~(PM_FIB | PM_NQ | PM_TRAV)) == 0u;
+}
+
+// One tile of a join range of such a program: every thread runs its own
+// continuations with no block barrier, so the warps of a block (and the
+// tiles of a thread) stream independently.  The join-operand prefetch works
+// as in epoch_tile: jr_use says this tile's operands are in jr[par], pf is the
+// successor tile (its operands go to jr[par ^ 1]); a thread only reads the
+// copies it issued itself.
+template <int BS, int TPT, uint32_t PM>
+__device__ __forceinline__ void join_tile(const Conf &c, Smem<BS> &sm, unsigned long long t0, uint32_t cen, uint32_t e,
+                                          Acc &acc, int par, const TileLoad<TPT> &L, bool jr_use,
+                                          const TileLoad<TPT> *pf) {
+    static_assert(joins_never_fork<PM>(), "only for programs whose continuations neither fork nor map");
+    // the columns tile_load brought in LOAD_JOIN mode for these programs
+    constexpr bool join_a0 = (PM & (PM_NQ | PM_TRAV)) != 0u;
+    constexpr bool join_a1 = (PM & PM_NQ) != 0u;
+    constexpr bool join_link = (PM & (PM_FIB | PM_NQ)) != 0u;
+    if constexpr (join_prefetch<BS, TPT, PM>()) {
+        if (jr_use) cp_async_wait_all();  // this thread's operands for this tile have landed
+    }
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+        const uint32_t s = (uint32_t)(t0 + (unsigned long long)k * BS + threadIdx.x);
+        const uint32_t t = task_type(L.cd[k], cen);
+        if (!t) continue;
+        acc.valid++;
+        if constexpr (join_prefetch<BS, TPT, PM>()) {
+            if (jr_use && t == TREES_TASK_FIB_SUM) {
+                const unsigned long long *r = sm.u.jr[par][k * BS + threadIdx.x];
+                c.result[s] = r[0] + r[1];
+                c.code[s] = 0u;
+                continue;
+            }
+        }
+        Plan p;
+        p.s = s;
+        p.t = t;
+        p.n = 0u;
+        p.m = 0u;
+        const uint32_t a0 = needs_a0(t) && !join_a0 ? c.a0[s] : L.a0[k];
+        const uint32_t a1 = needs_a1(t) && !join_a1 ? c.a1[s] : L.a1[k];
+        const uint32_t lk = needs_link(t) && !join_link ? c.link[s] : L.lk[k];
+        plan_task<PM, merge_tile(BS)>(c, c.rp, p, cen, e, a0, a1, lk);
+    }
+    if constexpr (join_prefetch<BS, TPT, PM>()) {
+        if (pf) {  // the successor tile's sums: copy their operands now
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                if (task_type(pf->cd[k], cen) == TREES_TASK_FIB_SUM) {
+                    unsigned long long *r = sm.u.jr[par ^ 1][k * BS + threadIdx.x];
+                    cp_async_8(r, c.result + pf->lk[k]);
+                    cp_async_8(r + 1, c.result + pf->lk[k] + 1);
+                }
+            }
+            cp_async_commit();
+        }
+    }
+}
+
+// A fresh range of fib tasks (Sec. 6.2: a leaf emits, an internal task forks
+// fib(n-1), fib(n-2) and joins their sum): the block's tiles (t0, t0 + step,
+// ...), taken in chunks of up to FIB_CHUNK_SLOTS / tile tiles, each in two
+// passes with one slot reservation between them:
+//  1. count: every warp streams through the chunk's tiles on its own (no
+//     block barrier): it loads code and n, lets the leaves emit in their own
+//     slot (Sec. 4.3.2), and records with one ballot per slot row which lanes
+//     fork (fib forks exactly two children, so a warp's prefix is twice a
+//     popcount), plus each internal task's n, in shared memory;
+//  2. one block scan over the per-warp fork counts and one atomic on
+//     nextFreeCore for the whole chunk (Sec. 5.2.3's cooperative allocation:
+//     a scan, then a single atomic for the group);
+//  3. write: every warp writes its internal tasks' children (k-major, so a
+//     warp's children are contiguous) and rewrites those tasks as their join
+//     continuations, from shared memory alone (no loads, no block barrier).
+// Returns whether this thread's tasks joined.
+constexpr uint32_t FIB_CHUNK_SLOTS = 16384;  // slots per chunk: their n fit a 16 KB byte array
+
+template <int BS, int TPT>
+__host__ __device__ constexpr uint32_t fib_chunk_tiles() {
+    return FIB_CHUNK_SLOTS / (uint32_t)(BS * TPT) < 64u ? FIB_CHUNK_SLOTS / (uint32_t)(BS * TPT) : 64u;
+}
+
+// Tiles of loads a thread keeps in flight in the count pass (registers:
+// 2 * TPT words per tile).
+template <int TPT>
+__host__ __device__ constexpr int fib_prefetch_tiles() {
+    return TPT >= 2 ? 2 : 8;
+}
+
+template <int BS, int TPT>
+struct FibChunk {
+    static constexpr uint32_t CT = fib_chunk_tiles<BS, TPT>(), NW = BS / 32;
+    uint8_t n[CT * BS * TPT];       // n of each slot's task (internal tasks only are read)
+    uint32_t mask[CT * TPT * NW];   // per (tile, slot row, warp): lanes whose task forks
+    uint32_t off[CT * TPT * NW];    // their exclusive prefix of children inside the chunk
+};
+
+template <int BS, int TPT>
+__device__ __forceinline__ bool fib_fresh_tiles(const Conf &c, Ctl *ctl, Smem<BS> &sm, unsigned long long t0,
+                                                unsigned long long step, uint32_t hi, uint32_t cen, uint32_t base,
+                                                uint32_t ep, uint32_t e, Acc &acc) {
+    using FC = FibChunk<BS, TPT>;
+    constexpr uint32_t CT = FC::CT, NW = FC::NW, TILE = BS * TPT;
+    static_assert(sizeof(FC) <= sizeof(sm.u), "the chunk's records fit the shared union");
+    static_assert(CT >= 1u, "at least one tile per chunk");
+    FC &fc = *reinterpret_cast<FC *>(&sm.u);
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;  // lanes below this one
+    const uint32_t fe = enc(cen + 1u, TREES_TASK_FIB), fj = enc(cen, TREES_TASK_FIB_SUM);
+    bool joined = false;
+    for (; t0 < hi; t0 += (unsigned long long)CT * step) {  // one chunk per iteration (block-uniform)
+        // tiles of this chunk: t0 + j * step, j < nt
+        const uint32_t nt = (uint32_t)min((unsigned long long)CT, (hi - t0 + step - 1ull) / step);
+        // ---- pass 1: count.  The loads of the next PD-1 tiles are in flight while a tile is decoded
+        // (a ring of PD tiles of code and n in registers).
+        constexpr int PD = fib_prefetch_tiles<TPT>();
+        uint32_t rc[PD][TPT], rn[PD][TPT];
+#pragma unroll
+        for (int u = 0; u < PD - 1; ++u) {
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                const unsigned long long s = t0 + (unsigned long long)u * step + (unsigned long long)k * BS + threadIdx.x;
+                const bool in = (uint32_t)u < nt && s < hi;
+                rc[u][k] = in ? c.code[s] : 0u;
+                rn[u][k] = in ? c.a0[s] : 0u;
+            }
+        }
+        for (uint32_t j0 = 0; j0 < nt; j0 += PD) {
+#pragma unroll
+            for (int u = 0; u < PD; ++u) {
+                const uint32_t j = j0 + (uint32_t)u;
+                if (j < nt) {  // block-uniform
+                {   // tile j + PD - 1 into the ring slot tile j - 1 used
+                    const int un = (u + PD - 1) % PD;  // a constant once the loop is unrolled
+                    const unsigned long long tn = t0 + (unsigned long long)(j + PD - 1) * step;
+#pragma unroll
+                    for (int k = 0; k < TPT; ++k) {
+                        const unsigned long long s = tn + (unsigned long long)k * BS + threadIdx.x;
+                        const bool in = j + PD - 1 < nt && s < hi;
+                        rc[un][k] = in ? c.code[s] : 0u;
+                        rn[un][k] = in ? c.a0[s] : 0u;
+                    }
+                }
+                const unsigned long long tj = t0 + (unsigned long long)j * step;
+#pragma unroll
+                for (int k = 0; k < TPT; ++k) {
+                    const uint32_t s = (uint32_t)(tj + (unsigned long long)k * BS + threadIdx.x);  // < hi when valid
+                    const uint32_t t = task_type(rc[u][k], cen), n = rn[u][k];
+                    bool fork = false;
+                    if (t == TREES_TASK_FIB) {
+                        acc.valid++;
+                        if (n < 2u || n <= c.rp.cutoff) {  // a leaf emits: fib(n) in its own slot, entry dead
+                            c.result[s] = n < 2u ? (unsigned long long)n : fib_leaf(n);
+                            c.code[s] = 0u;
+                        } else {
+                            fork = true;
+                        }
+                    } else if (t) {  // not produced in a fresh range; run it as the general path would
+                        acc.valid++;
+                        Plan p;
+                        p.s = s;
+                        p.t = t;
+                        p.n = 0u;
+                        p.m = 0u;
+                        plan_task<PM_FIB, merge_tile(BS)>(c, c.rp, p, cen, e, n, 0u, c.link[s]);
+                    }
+                    const uint32_t m = __ballot_sync(0xffffffffu, fork);
+                    if (lane == 0u) fc.mask[(j * TPT + k) * NW + wid] = m;
+                    if (fork) fc.n[j * TILE + k * BS + threadIdx.x] = (uint8_t)n;  // n <= 93 (host check)
+                }
+                }
+            }
+        }
+        __syncthreads();
+        // ---- pass 2: one scan over the chunk's per-warp counts, one reservation for the chunk
+        constexpr uint32_t NE = CT * TPT * NW, PER = (NE + BS - 1u) / BS;
+        const uint32_t ne = nt * TPT * NW;
+        uint32_t loc[PER], lsum = 0u;
+#pragma unroll
+        for (uint32_t q = 0; q < PER; ++q) {
+            const uint32_t i = threadIdx.x * PER + q;
+            loc[q] = i < ne ? 2u * (uint32_t)__popc(fc.mask[i]) : 0u;
+            lsum += loc[q];
+        }
+        uint32_t total;
+        int any;
+        uint32_t pre = block_scan_u32<BS>(lsum, 0, &total, &any, sm);
+#pragma unroll
+        for (uint32_t q = 0; q < PER; ++q) {
+            const uint32_t i = threadIdx.x * PER + q;
+            if (i < ne) fc.off[i] = pre;
+            pre += loc[q];
+        }
+        if (threadIdx.x == 0) {
+            const uint32_t b = total ? atomicAdd(&ctl->cnt[ep], total) : 0u;  // one atomic per chunk
+            const bool over = (unsigned long long)base + b + total > c.cap;
+            if (over) set_err(ctl, TREES_ERR_CAPACITY, e);
+            sm.bc32[0] = b;
+            sm.bc32[1] = over;
+        }
+        __syncthreads();
+        // ---- pass 3: children and continuations, warp by warp
+        if (total && !sm.bc32[1]) {
+            const uint32_t cbase = base + sm.bc32[0];
+            for (uint32_t j = 0; j < nt; ++j) {
+#pragma unroll
+                for (int k = 0; k < TPT; ++k) {
+                    const uint32_t i = (j * TPT + k) * NW + wid;
+                    const uint32_t m = fc.mask[i];
+                    if (!((m >> lane) & 1u)) continue;
+                    const uint32_t s = (uint32_t)(t0 + (unsigned long long)j * step + (unsigned long long)k * BS +
+                                                  threadIdx.x);
+                    const uint32_t n = fc.n[j * TILE + k * BS + threadIdx.x];
+                    const uint32_t child = cbase + fc.off[i] + 2u * (uint32_t)__popc(m & lt);
+                    c.code[child] = fe;
+                    c.a0[child] = n - 1u;
+                    c.code[child + 1] = fe;
+                    c.a0[child + 1] = n - 2u;
+                    c.link[s] = child;
+                    c.code[s] = fj;
+                    acc.joins++;
+                    joined = true;
+                }
+            }
+        }
+        __syncthreads();  // the records are the next chunk's
+    }
+    return joined;
+}
+
+// The join ranges of fib (Sec. 6.2's sum continuations, Sec. 4.1: a join
+// reads its children's results through its link), all of the block's tiles
+// (t0, t0 + step, ...) with a two-level pipeline of asynchronous copies
+// (cp.async) per thread: the code and link columns of the thread's slots of
+// tile j+LA and the children's two results of tile j+LB's sums (their links
+// are in shared memory by then) are in flight while tile j is summed.  Each
+// thread reads only what it copied, so no block barrier is needed, and no
+// register or load scoreboard holds the data in flight.  `ring` is this
+// block's dynamic shared memory: NA stages of (code, link) and NB stages of
+// result pairs, TILE slots each.
+template <int BS, int TPT, int NA, int NB>
+__device__ __forceinline__ void fib_join_tiles(const Conf &c, unsigned long long t0, unsigned long long step,
+                                               uint32_t hi, uint32_t cen, uint32_t e, Acc &acc, uint32_t *ring) {
+    constexpr uint32_t TILE = BS * TPT;
+    constexpr int LA = NA - 1, LB = NB - 1;
+    static_assert(LA > LB && LB >= 1, "links land before the operands they locate are copied");
+    uint32_t *const ra = ring;  // stage q: code at [2 q TILE + slot], link at [(2 q + 1) TILE + slot]
+    unsigned long long *const rb = reinterpret_cast<unsigned long long *>(ring + 2u * NA * TILE);  // 2 per slot
+    const uint32_t nt = t0 < hi ? (uint32_t)((hi - t0 + step - 1ull) / step) : 0u;  // this block's tiles
+    const auto slot = [&](uint32_t j, int k) { return t0 + (unsigned long long)j * step + (unsigned long long)k * BS + threadIdx.x; };
+    const auto issue_a = [&](uint32_t j) {
+        if (j < nt) {
+            uint32_t *q = ra + (j % (uint32_t)NA) * 2u * TILE + threadIdx.x;
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                const unsigned long long s = slot(j, k);
+                if (s < hi) {
+                    cp_async_4(q + k * BS, c.code + s);
+                    cp_async_4(q + TILE + k * BS, c.link + s);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    const auto issue_b = [&](uint32_t j) {  // tile j's (code, link) have landed
+        if (j < nt) {
+            const uint32_t *q = ra + (j % (uint32_t)NA) * 2u * TILE + threadIdx.x;
+            unsigned long long *r = rb + 2u * ((j % (uint32_t)NB) * TILE + threadIdx.x);
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                if (slot(j, k) < hi && task_type(q[k * BS], cen) == TREES_TASK_FIB_SUM) {
+                    const uint32_t lk = q[TILE + k * BS];
+                    cp_async_8(r + 2 * k * BS, c.result + lk);
+                    cp_async_8(r + 2 * k * BS + 1, c.result + lk + 1);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    // prologue: the links of tiles 0..LB-1 land, then their operands are copied; tiles up to LA-1 stream in
+#pragma unroll
+    for (int j = 0; j < LA; ++j) issue_a((uint32_t)j);
+    cp_async_wait_all();
+#pragma unroll
+    for (int j = 0; j < LB; ++j) issue_b((uint32_t)j);
+    for (uint32_t j = 0; j < nt; ++j) {
+        issue_a(j + LA);
+        cp_async_wait_group<2 * (LA - LB)>();  // tile j+LB's (code, link)
+        issue_b(j + LB);
+        cp_async_wait_group<2 * LB>();          // tile j's operands
+        const uint32_t *q = ra + (j % (uint32_t)NA) * 2u * TILE + threadIdx.x;
+        const unsigned long long *r = rb + 2u * ((j % (uint32_t)NB) * TILE + threadIdx.x);
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            const unsigned long long sl = slot(j, k);
+            if (sl >= hi) continue;
+            const uint32_t s = (uint32_t)sl, t = task_type(q[k * BS], cen);
+            if (!t) continue;
+            acc.valid++;
+            if (t == TREES_TASK_FIB_SUM) {
+                c.result[s] = r[2 * k * BS] + r[2 * k * BS + 1];
+                c.code[s] = 0u;
+            } else {  // not produced in a join range; run it as the general path would
+                Plan p;
+                p.s = s;
+                p.t = t;
+                p.n = 0u;
+                p.m = 0u;
+                plan_task<PM_FIB, merge_tile(BS)>(c, c.rp, p, cen, e, c.a0[s], 0u, q[TILE + k * BS]);
+            }
+        }
+    }
+    cp_async_wait_all();  // the trailing empty groups
 }
 
 // ------------------------------------------------------------------ map operations

@@ -228,7 +228,7 @@ def test_sssp_rmat22_distances_equal_dijkstra(rmat22, sssp22, bs, tpt):
 @pytest.mark.parametrize("sched", [T.TREES_SCHED_PERSISTENT, T.TREES_SCHED_GRAPH])
 def test_fib24_small_grid(grid, bs, tpt, sched):
     sim = oracle.tvm_run(oracle.FIB, fib_n=24)
-    with Ctx(1 << 17, grid_blocks=grid, block_size=bs, tasks_per_thread=tpt, scheduler=sched, map_capacity=1,
+    with Ctx(1 << 18, grid_blocks=grid, block_size=bs, tasks_per_thread=tpt, scheduler=sched, map_capacity=1,
              trace=1) as ctx:
         assert run(ctx, T.make_job(T.TREES_PROG_FIB, n=24)) == T.TREES_OK
         assert T.trees_result(ctx, 0) == oracle.fib(24)[0] == 46368
@@ -241,12 +241,12 @@ def test_fib24_small_grid(grid, bs, tpt, sched):
 def test_fib24_cutoff_and_nqueens_small_grid(grid, bs, tpt):
     cfg = dict(grid_blocks=grid, block_size=bs, tasks_per_thread=tpt, map_capacity=1, trace=1)
     sim = oracle.tvm_run(oracle.FIB, fib_n=24, fib_cutoff=6)
-    with Ctx(1 << 17, **cfg) as ctx:
+    with Ctx(1 << 18, **cfg) as ctx:
         assert run(ctx, T.make_job(T.TREES_PROG_FIB, n=24, cutoff=6)) == T.TREES_OK
         assert T.trees_result(ctx, 0) == 46368
         check_run(ctx, sim)
     sim = oracle.tvm_run(oracle.NQUEENS, nq_n=10)
-    with Ctx(1 << 17, **cfg) as ctx:
+    with Ctx(1 << 18, **cfg) as ctx:
         assert run(ctx, T.make_job(T.TREES_PROG_NQUEENS, n=10)) == T.TREES_OK
         assert T.trees_result(ctx, 0) == oracle.nqueens(10)[0] == 724
         check_run(ctx, sim)
