@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="headline only (no secondary workloads / fit)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
+    ap.add_argument("--clock-warm-s", type=float, default=CLOCK_WARM_S,
+                    help="least seconds of headline warm-up steps the clock sampler sees before the timed steps")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file for the autotuner's choices (default: tune afresh every run)")
     ap.add_argument("--profile-case", default=None,
@@ -707,7 +709,7 @@ def main():
     clocks = ClockSampler(local)
     t_w0 = time.perf_counter()
     nwarm = 0
-    while nwarm < args.warmup or time.perf_counter() - t_w0 < CLOCK_WARM_S:
+    while nwarm < args.warmup or time.perf_counter() - t_w0 < args.clock_warm_s:
         timed_runs(T, torch, ctx, job, 0, 1, stream, flush)
         nwarm += 1
     if dist is not None:
