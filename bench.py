@@ -140,12 +140,14 @@ def measured_peaks():
 
 
 def source_hash():
+    """Hash of the kernel sources: the library's csrc/ and the engine headers
+    under include/trees_impl/."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1608_00571_b300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(name.encode())
-            h.update(f.read())
+    for d in (os.path.join(ROOT, "paper_1608_00571_b300", "csrc"), os.path.join(ROOT, "include", "trees_impl")):
+        for name in sorted(os.listdir(d)):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
     return h.hexdigest()[:16]
 
 

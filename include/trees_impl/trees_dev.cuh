@@ -13,7 +13,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "trees.h"
+#include "../trees.h"
 
 namespace trees {
 

@@ -4,8 +4,11 @@
  * The built-in programs (fib, mergesort, N-Queens, BFS, SSSP, traversals,
  * FFT) are compiled into libtrees.  A user program is a struct of four
  * device functions compiled by the user, with nvcc for sm_103a and this
- * directory plus the library's csrc directory on the include path, into the
- * user's own shared library; TREES_DEFINE_PROGRAM(name, Prog) instantiates
+ * directory alone on the include path (the engine's device code is in
+ * trees_impl/), into the user's own shared library (for example
+ *   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -std=c++17 -shared
+ *        -Xcompiler -fPIC -I include prog.cu -o libprog.so);
+ * TREES_DEFINE_PROGRAM(name, Prog) instantiates
  * the runtime's persistent epoch kernel for it (the persistent scheduler:
  * one grid barrier per epoch) and exports `name` with the trees_program_fn
  * signature of trees.h.  A job with program = TREES_PROG_USER, user_program
@@ -50,7 +53,7 @@
 #pragma once
 
 #include "trees.h"
-#include "trees_kernels.cuh"
+#include "trees_impl/trees_kernels.cuh"
 
 // The paper's four primitives (Sec. 4.2) as helpers for the records above:
 // plan fills a trees_user_plan with trees_emit / trees_fork / trees_map, and

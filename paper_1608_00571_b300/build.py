@@ -28,7 +28,8 @@ def sources():
 
 def _deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
-        glob.glob(os.path.join(INCLUDE, "*.h"))
+        glob.glob(os.path.join(INCLUDE, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.cuh")) + \
+        glob.glob(os.path.join(INCLUDE, "trees_impl", "*.cuh"))
 
 
 def stale() -> bool:
@@ -75,12 +76,13 @@ if __name__ == "__main__":
 def build_program(source: str, output: str, force: bool = False) -> str:
     """Compiles a user task program (a .cu file written against
     include/trees_program.cuh, ending in TREES_DEFINE_PROGRAM) into the
-    shared library ``output`` with the library's own flags, unless it is
-    newer than its source and the runtime headers.  Returns ``output``."""
-    deps = [source] + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*"))
+    shared library ``output`` with the library's own flags and the public
+    include directory alone on the include path, unless it is newer than its
+    source and the SDK headers.  Returns ``output``."""
+    deps = [source] + glob.glob(os.path.join(INCLUDE, "*")) + glob.glob(os.path.join(INCLUDE, "trees_impl", "*"))
     if not force and os.path.exists(output) and all(os.path.getmtime(output) >= os.path.getmtime(d) for d in deps):
         return output
     tmp = output + ".tmp"
-    subprocess.check_call(["nvcc", *NVCC_FLAGS, "-I", INCLUDE, "-I", CSRC, source, "-o", tmp])
+    subprocess.check_call(["nvcc", *NVCC_FLAGS, "-I", INCLUDE, source, "-o", tmp])
     os.replace(tmp, output)
     return output

@@ -23,10 +23,10 @@
 #include <vector>
 
 #include "trees.h"
-#include "trees_dev.cuh"
-#include "trees_programs.cuh"
+#include "trees_impl/trees_dev.cuh"
+#include "trees_impl/trees_programs.cuh"
 #include "trees_batch.cuh"
-#include "trees_kernels.cuh"
+#include "trees_impl/trees_kernels.cuh"
 
 #include <chrono>
 #include <deque>

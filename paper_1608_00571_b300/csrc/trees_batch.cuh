@@ -11,8 +11,8 @@
 // Included by trees.cu (one translation unit).
 #pragma once
 
-#include "trees_dev.cuh"
-#include "trees_programs.cuh"
+#include "trees_impl/trees_dev.cuh"
+#include "trees_impl/trees_programs.cuh"
 
 namespace trees {
 

@@ -1,6 +1,6 @@
 // Persistent epoch-loop kernels for one program (PM_MS), every block size and
 // slots-per-thread setting.
-#include "trees_kernels.cuh"
+#include "trees_impl/trees_kernels.cuh"
 
 namespace trees {
 
