@@ -69,6 +69,9 @@ struct RunParams {
     const uint32_t *weight;    // SSSP edge weights (aligned with col)
     unsigned long long *dist;  // SSSP distances
     uint32_t *sched;           // SSSP: the last epoch each vertex was forked for
+    // SSSP: per vertex, (e + 1) << 40 | the largest distance of it that a relaxation of its
+    // out-edges used in epoch e, e its last relax epoch (0 = never relaxed; context-owned)
+    unsigned long long *used;
     const float2 *fx;          // FFT input, N complex points
     float2 *fX;                // FFT output
     uint32_t lgn;              // FFT: log2 N
@@ -196,7 +199,7 @@ struct Smem {
         struct {
             uint32_t base[EXPAND_TILE + 2];
             uint32_t v[EXPAND_TILE + 2];
-            uint32_t src[EXPAND_TILE + 2];
+            unsigned long long d[EXPAND_TILE + 2];  // SSSP: the source's distance, read once per tile
         } ex;
         unsigned long long jr[2][JR_SLOTS][2];  // fib joins: the next tile's children's results, prefetched
     } u;

@@ -62,6 +62,11 @@ struct Plan {
     uint32_t s, t, n, m, a0, a1;
 };
 
+// SSSP relax records pack (epoch + 1) above the low SSSP_USED_SHIFT bits of
+// a distance; distances of 2^40 or more are never recorded (their vertices
+// are simply relaxed again when forked).
+constexpr uint32_t SSSP_USED_SHIFT = 40;
+
 // Leaf of the fib cutoff variant: the naive recursion run inside the task
 // with an explicit stack (depth <= n + 1; n <= 30 is enforced by the host).
 __device__ __forceinline__ unsigned long long fib_leaf(uint32_t n) {
@@ -330,7 +335,12 @@ __device__ __forceinline__ void plan_task(const Conf &c, const RunParams &rp, Pl
     if constexpr ((PM & PM_SSSP) != 0u) {
         if (p.t == TREES_TASK_SSSP_RELAX) {  // relax(v): a map over v's out-edges (Sec. 6.3)
             const int32_t rb = __ldg(rp.row_ptr + a0), re = __ldg(rp.row_ptr + a0 + 1);
-            if (re > rb) {
+            // v's relaxation in the previous epoch already propagated its current distance along
+            // every out-edge: nothing is left to relax, the task ends at once
+            const unsigned long long dv = rp.dist[a0];
+            const bool done = cen > 0u && dv < (1ull << SSSP_USED_SHIFT) &&  // record 0 = never relaxed
+                              rp.used[a0] == ((unsigned long long)cen << SSSP_USED_SHIFT | dv);
+            if (re > rb && !done) {
                 p.m = MAP_EXPAND;
                 p.a0 = (uint32_t)rb;
                 p.a1 = a0;
@@ -1670,12 +1680,16 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
     for (uint32_t j = 0; j < EPT; ++j) uu[j] = ed[j] != 0xFFFFFFFFu ? __ldg(c.rp.col + ed[j]) : -1;
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j) lv[j] = uu[j] >= 0 ? c.rp.level[uu[j]] : 0;
-    // stage 3: claim unvisited neighbours (the CAS decides between competing visits)
+    // stage 3: claim unvisited neighbours (the CAS decides between competing visits); all of the
+    // thread's CASes are issued before any answer is examined, so their round trips overlap
     const int32_t nlev = (int32_t)(cen + 1u);
+    int32_t prev[EPT];
+#pragma unroll
+    for (uint32_t j = 0; j < EPT; ++j) prev[j] = uu[j] >= 0 && lv[j] < 0 ? atomicCAS(c.rp.level + uu[j], -1, nlev) : 0;
     uint32_t cmask = 0u;
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j)
-        if (uu[j] >= 0 && lv[j] < 0 && atomicCAS(c.rp.level + uu[j], -1, nlev) == -1) cmask |= 1u << j;
+        if (uu[j] >= 0 && lv[j] < 0 && prev[j] == -1) cmask |= 1u << j;
     const uint32_t nc = (uint32_t)__popc(cmask);
     uint32_t ftot;
     int any;
@@ -1706,13 +1720,17 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
 }
 
 // One SSSP relaxation tile (Sec. 6.3's worklist relaxation as a map): the
-// same element-balanced layout as a BFS expansion tile.  For each out-edge
-// (v, u, w) of the epoch's frontier, nd = dist[v] + w; an atomic minimum
-// shortens dist[u] if nd is smaller, and the thread whose minimum took
-// effect forks relax(u) for epoch CEN+1 unless another already did this
-// epoch (an atomic maximum on sched[u]).  dist[v] may be read after another
-// relaxation in this epoch has shortened it further; v is then forked again
-// for the next epoch, so the final distances are the shortest ones.
+// same element-balanced layout as a BFS expansion tile.  Each source vertex
+// v of the tile has its distance read once for the tile; for each of its
+// out-edges (v, u, w) here, nd = dist[v] + w; an atomic minimum shortens
+// dist[u] if nd is smaller, and the thread whose minimum took effect forks
+// relax(u) for epoch CEN+1 unless another already did this epoch (an atomic
+// maximum on sched[u]).  dist[v] may have been shortened after the tile
+// read it; v is then forked again for the next epoch, so the final
+// distances are the shortest ones.  Each tile also records, per source
+// vertex, the distance its edges used (an atomic maximum of
+// (CEN+1) << 40 | distance), so that a relax(v) forked again whose distance
+// is still the one every edge of v used in the previous epoch ends at once.
 template <int BS>
 __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, uint32_t nd, uint32_t ne, uint32_t nt,
                            uint32_t cen, uint32_t base, uint32_t ep, uint32_t e) {
@@ -1721,19 +1739,21 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
     const uint32_t dfirst = c.me_tfd[t];
     const uint32_t dlast = (t + 1u < nt) ? c.me_tfd[t + 1u] : nd - 1u;
     const uint32_t nloc = dlast - dfirst + 1u;
+    // the tile's descriptors, and each source vertex's distance read once for the whole tile
     for (uint32_t k = threadIdx.x; k < nloc; k += BS) {
         sm.u.ex.base[k] = c.me_base[dfirst + k];
         sm.u.ex.v[k] = c.me_v[dfirst + k];
-        sm.u.ex.src[k] = c.me_src[dfirst + k];
+        sm.u.ex.d[k] = c.rp.dist[c.me_src[dfirst + k]];
     }
     __syncthreads();
-    // stage 1: every element's adjacency index and source vertex (load-balanced search)
-    uint32_t ed[EPT], sv[EPT];
+    // stage 1: every element's adjacency index and its source's distance (load-balanced search)
+    uint32_t ed[EPT];
+    unsigned long long dv[EPT];
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j) {
         const uint32_t g = g0 + j * BS + threadIdx.x;
         ed[j] = 0xFFFFFFFFu;
-        sv[j] = 0u;
+        dv[j] = 0ull;
         if (g < g1) {
             uint32_t lo = 0, hi = nloc;
             while (hi - lo > 1u) {
@@ -1742,10 +1762,10 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
                 else hi = mid;
             }
             ed[j] = sm.u.ex.v[lo] + (g - sm.u.ex.base[lo]);
-            sv[j] = sm.u.ex.src[lo];
+            dv[j] = sm.u.ex.d[lo];
         }
     }
-    // stage 2: neighbours, weights and both distances in flight together
+    // stage 2: neighbours, weights and the neighbours' distances in flight together
     int32_t uu[EPT];
     unsigned long long cand[EPT], du[EPT];
 #pragma unroll
@@ -1755,18 +1775,24 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
         cand[j] = ~0ull;
         du[j] = 0ull;
         if (uu[j] >= 0) {
-            cand[j] = c.rp.dist[sv[j]] + (unsigned long long)__ldg(c.rp.weight + ed[j]);
+            cand[j] = dv[j] + (unsigned long long)__ldg(c.rp.weight + ed[j]);
             du[j] = c.rp.dist[uu[j]];
         }
     }
-    // stage 3: shorten, and fork the neighbours this thread shortened first this epoch
+    // stage 3: shorten, and fork the neighbours this thread shortened first this epoch.  All of the
+    // thread's atomic minima are issued before any answer is examined, then all of its atomic maxima,
+    // so each stage costs one overlapped round trip instead of one per edge.
+    unsigned long long old[EPT];
+#pragma unroll
+    for (uint32_t j = 0; j < EPT; ++j) old[j] = uu[j] >= 0 && cand[j] < du[j] ? atomicMin(c.rp.dist + uu[j], cand[j]) : 0ull;
+    uint32_t prev[EPT];
+#pragma unroll
+    for (uint32_t j = 0; j < EPT; ++j)
+        prev[j] = uu[j] >= 0 && cand[j] < du[j] && cand[j] < old[j] ? atomicMax(c.rp.sched + uu[j], cen + 1u) : ~0u;
     uint32_t cmask = 0u;
 #pragma unroll
-    for (uint32_t j = 0; j < EPT; ++j) {
-        if (uu[j] >= 0 && cand[j] < du[j] && cand[j] < atomicMin(c.rp.dist + uu[j], cand[j]) &&
-            atomicMax(c.rp.sched + uu[j], cen + 1u) < cen + 1u)
-            cmask |= 1u << j;
-    }
+    for (uint32_t j = 0; j < EPT; ++j)
+        if (prev[j] < cen + 1u) cmask |= 1u << j;
     const uint32_t nc = (uint32_t)__popc(cmask);
     uint32_t ftot;
     int any;
@@ -1792,6 +1818,13 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
                 }
             }
         }
+    }
+    // record, per source vertex of the tile, the distance its edges here used (the largest over the
+    // epoch's tiles wins; a descriptor listed for the tile without edges in it only raises it)
+    for (uint32_t k = threadIdx.x; k < nloc; k += BS) {
+        const unsigned long long d = sm.u.ex.d[k];
+        if (d < (1ull << SSSP_USED_SHIFT))
+            atomicMax(c.rp.used + c.me_src[dfirst + k], (unsigned long long)(cen + 1u) << SSSP_USED_SHIFT | d);
     }
     __syncthreads();
 }

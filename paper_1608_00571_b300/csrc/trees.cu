@@ -72,10 +72,12 @@ __global__ void k_bfs_init(int32_t *level, int32_t nv, int32_t src) {
 
 // SSSP start: every distance unknown but the source's; no vertex forked yet
 // (the root task relaxes the source in epoch 0).
-__global__ void k_sssp_init(unsigned long long *dist, uint32_t *sched, int32_t nv, int32_t src) {
+__global__ void k_sssp_init(unsigned long long *dist, uint32_t *sched, unsigned long long *used, int32_t nv,
+                            int32_t src) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
         dist[v] = (v == src) ? 0ull : ~0ull;
         sched[v] = 0u;
+        used[v] = 0ull;  // never relaxed
     }
 }
 
@@ -348,6 +350,8 @@ struct trees_ctx {
     std::map<const void *, int> grid_cache;
     uint32_t *own_scratch = nullptr;
     size_t own_scratch_n = 0;
+    unsigned long long *own_used = nullptr;  // SSSP relax records (one word per vertex)
+    size_t own_used_n = 0;
     uint32_t *own_smp = nullptr;  // mergesort splitter samples (n/64 + 1 keys)
     size_t own_smp_n = 0;
     // graph scheduler
@@ -552,6 +556,7 @@ void trees_destroy(trees_ctx *x) {
     if (x->gexec) cudaGraphExecDestroy(x->gexec);
     if (x->graph) cudaGraphDestroy(x->graph);
     if (x->own_scratch) cudaFree(x->own_scratch);
+    if (x->own_used) cudaFree(x->own_used);
     if (x->own_smp) cudaFree(x->own_smp);
     if (x->pinned_ctl) cudaFreeHost(x->pinned_ctl);
     if (x->d_jobs) cudaFree(x->d_jobs);
@@ -810,6 +815,14 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
         rp.dist = reinterpret_cast<unsigned long long *>(job->dist);
         rp.sched = job->sched;
         rp.nv = job->nv;
+        if (x->own_used_n < (size_t)job->nv) {  // the relax records, one word per vertex, owned by the context
+            if (x->own_used) cudaFree(x->own_used);
+            x->own_used = nullptr;
+            x->own_used_n = 0;
+            if (cudaMalloc(&x->own_used, (size_t)job->nv * 8) != cudaSuccess) return TREES_ERR_CUDA;
+            x->own_used_n = (size_t)job->nv;
+        }
+        rp.used = x->own_used;
         type = TREES_TASK_SSSP_RELAX;
         a0 = job->n;
         break;
@@ -864,7 +877,7 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
     }
     if (job->program == TREES_PROG_SSSP) {
         const int nb = std::min<int64_t>((job->nv + 255) / 256, 65536);
-        k_sssp_init<<<nb, 256, 0, st>>>(rp.dist, job->sched, job->nv, (int32_t)job->n);
+        k_sssp_init<<<nb, 256, 0, st>>>(rp.dist, job->sched, rp.used, job->nv, (int32_t)job->n);
     }
     if (job->program == TREES_PROG_POSTORDER || job->program == TREES_PROG_PREORDER) {
         if (job->n && cudaMemsetAsync(job->visit_epoch, 0xFF, (size_t)job->n * 4, st) != cudaSuccess)
