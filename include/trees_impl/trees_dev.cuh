@@ -109,11 +109,19 @@ struct Conf {
 // epoch index: epoch e allocates from slot e%3, block 0 clears slot (e+1)%3
 // during epoch e (its last readers finished before the barrier that opened
 // epoch e), so one grid barrier per epoch is enough.
+//
+// ew[q], the epoch word of slot q: the high 32 bits are the epoch's forks
+// (nextFreeCore - oldNextFreeCore, the counter the cooperative allocation
+// adds to); the low 32 bits serve the epoch barrier of the programs without
+// maps (epoch_barrier): arrivals in bits 0..15, the blocks that joined in
+// bits 16..30, and bit 31 set once any device-side error was raised.
+constexpr unsigned long long EW_ARRIVALS = 0xFFFFull, EW_ERROR = 0x80000000ull;
+constexpr uint32_t EW_JOIN_SHIFT = 16;
 struct Ctl {
     unsigned int bar_count;          // monotonic arrival counter of the grid barrier
     unsigned int pad0[63];
-    unsigned int cnt[3];             // forks this epoch (nextFreeCore - oldNextFreeCore)
-    unsigned int join[3];            // joinScheduled
+    unsigned long long ew[3];        // epoch words (above)
+    unsigned int join[3];            // joinScheduled (schedulers and programs that read it apart)
     unsigned long long mt_ctr[3];    // tiled maps: (descriptors << 40) | tiles
     unsigned long long me_ctr[3];    // element maps: (descriptors << 40) | elements
     int err;                         // first device-side error (sticky)
@@ -164,8 +172,28 @@ __device__ __forceinline__ T vload(const T *p) {
     return *(const volatile T *)p;
 }
 
+// The allocation counter of epoch slot ep: the high half of its epoch word.
+__host__ __device__ __forceinline__ unsigned int *fork_ctr(Ctl *ctl, uint32_t ep) {
+    return reinterpret_cast<unsigned int *>(&ctl->ew[ep]) + 1;
+}
+
 __device__ __forceinline__ void set_err(Ctl *ctl, int code, uint32_t epoch) {
     if (atomicCAS(&ctl->err, 0, code) == 0) ctl->err_epoch = epoch;
+    for (int q = 0; q < 3; ++q) atomicOr(&ctl->ew[q], EW_ERROR);  // seen by the next epoch barrier
+}
+
+// Clears epoch slot q for reuse, keeping its error flag.
+__device__ __forceinline__ void clear_epoch_slot(Ctl *ctl, uint32_t q) {
+    atomicAnd(&ctl->ew[q], EW_ERROR);
+    ctl->join[q] = 0u;
+    ctl->mt_ctr[q] = 0ull;
+    ctl->me_ctr[q] = 0ull;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
 // ------------------------------------------------------------------ shared memory
@@ -485,11 +513,52 @@ __device__ __forceinline__ bool grid_sync_ep(Ctl *ctl, uint32_t *bar_idx, unsign
         }
         fence_acq_rel();  // acquire for the whole SM: no stale L1 line of data written before the barrier
         const int err = vload(&ctl->err);
-        sm.ep_cnt = vload(&ctl->cnt[ep]);
+        sm.ep_cnt = vload(fork_ctr(ctl, ep));
         sm.ep_join = vload(&ctl->join[ep]);
         sm.ep_mt = vload(&ctl->mt_ctr[ep]);
         sm.ep_me = vload(&ctl->me_ctr[ep]);
         sm.bar_ok = ok && err == 0;
+    }
+    __syncthreads();
+    return sm.bar_ok != 0;
+}
+
+// The barrier that closes Phase 2 of an epoch, for programs without maps:
+// thread 0 of each block adds one arrival (and, if any of its threads
+// joined, one joined block) to the low half of epoch slot ep's word with
+// release semantics and polls the whole 64-bit word with acquire loads until
+// every block has arrived; the same load that ends the wait delivers the
+// epoch's forks (the high half), its join flag and the error flag, so no
+// further round trip is needed before Phase 3.  Bounded by timeout_ns like
+// grid_sync.  Every thread calls it; returns false on a timeout or error.
+template <int BS>
+__device__ __forceinline__ bool epoch_barrier(Ctl *ctl, unsigned long long timeout_ns, Smem<BS> &sm, uint32_t ep,
+                                              bool joined) {
+    const int jb = __syncthreads_or(joined);  // also orders the block's writes before thread 0's release
+    if (threadIdx.x == 0) {
+        red_release_add(reinterpret_cast<unsigned int *>(&ctl->ew[ep]), 1u + (jb ? 1u << EW_JOIN_SHIFT : 0u));
+        int ok = 1;
+        uint32_t spins = 0;
+        uint64_t t0 = 0;
+        unsigned long long w;
+        while (((w = ld_acquire_u64(&ctl->ew[ep])) & EW_ARRIVALS) < gridDim.x) {
+            if ((++spins & 63u) == 0u) {
+                const uint64_t now = globaltimer();
+                if (t0 == 0) {
+                    t0 = now;
+                } else if (now - t0 > timeout_ns) {
+                    set_err(ctl, TREES_ERR_TIMEOUT, ep);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        fence_acq_rel();  // acquire for the whole SM: no stale L1 line of data written before the barrier
+        sm.ep_cnt = (uint32_t)(w >> 32);
+        sm.ep_join = (uint32_t)((w >> EW_JOIN_SHIFT) & 0x7FFFull) != 0u;
+        sm.ep_mt = 0ull;
+        sm.ep_me = 0ull;
+        sm.bar_ok = ok && (w & EW_ERROR) == 0ull;
     }
     __syncthreads();
     return sm.bar_ok != 0;

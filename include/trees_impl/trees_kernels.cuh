@@ -139,13 +139,7 @@ __device__ __forceinline__ void phase1(const Conf &c, Ctl *ctl, Smem<BS> &sm, ui
         sm.base = sm.next;
     }
     sm.stop = stop;
-    if (!stop && blockIdx.x == 0) {
-        const uint32_t q = (e + 1u) % 3u;
-        ctl->cnt[q] = 0u;
-        ctl->join[q] = 0u;
-        ctl->mt_ctr[q] = 0ull;
-        ctl->me_ctr[q] = 0ull;
-    }
+    if (!stop && blockIdx.x == 0) clear_epoch_slot(ctl, (e + 1u) % 3u);
 }
 
 // Phase 3 (thread 0): push the join range, then the fork range; or give the
@@ -389,9 +383,13 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
             }
         }
         trace_valid_add<BS>(c, e, acc.valid - v0, sm);
-        publish_join(ctl, ep, jn);
         if ((int32_t)e == c.stall_epoch && blockIdx.x == gridDim.x - 1) return;  // test hook: never arrives
-        if (!grid_sync_ep<BS>(ctl, &st.bar, c.timeout_ns, sm, ep)) break;
+        if constexpr ((PM & PM_MAPS) == 0u) {  // the epoch word carries the counters Phase 3 needs
+            if (!epoch_barrier<BS>(ctl, c.timeout_ns, sm, ep, jn)) break;
+        } else {
+            publish_join(ctl, ep, jn);
+            if (!grid_sync_ep<BS>(ctl, &st.bar, c.timeout_ns, sm, ep)) break;
+        }
         if (stamp) st.t_p2 = st.t_pt = st.t_mp = globaltimer();
         const unsigned long long mt = sm.ep_mt, me = sm.ep_me;
         if (mt | me) {  // the map operations of this epoch run before the next one (Sec. 5.2.4)

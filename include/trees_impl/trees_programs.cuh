@@ -734,12 +734,12 @@ __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> 
         if (known) {
             over0 = (unsigned long long)base + known_off + all > c.cap;
             if (threadIdx.x == 0) {
-                atomicAdd(&ctl->cnt[ep], all);  // result unused: a fire-and-forget reduction
+                atomicAdd(fork_ctr(ctl, ep), all);  // result unused: a fire-and-forget reduction
                 if (over0) set_err(ctl, TREES_ERR_CAPACITY, e);
             }
         } else {
             if (threadIdx.x == 0) {
-                const uint32_t b = atomicAdd(&ctl->cnt[ep], all);  // one atomic per block (Sec. 5.2.3)
+                const uint32_t b = atomicAdd(fork_ctr(ctl, ep), all);  // one atomic per block (Sec. 5.2.3)
                 const bool over = (unsigned long long)base + b + all > c.cap;
                 if (over) set_err(ctl, TREES_ERR_CAPACITY, e);
                 sm.bc32[par] = b;
@@ -982,7 +982,7 @@ __device__ __forceinline__ bool fib_fresh_tiles(const Conf &c, Ctl *ctl, Smem<BS
             pre += loc[q];
         }
         if (threadIdx.x == 0) {
-            const uint32_t b = total ? atomicAdd(&ctl->cnt[ep], total) : 0u;  // one atomic per chunk
+            const uint32_t b = total ? atomicAdd(fork_ctr(ctl, ep), total) : 0u;  // one atomic per chunk
             const bool over = (unsigned long long)base + b + total > c.cap;
             if (over) set_err(ctl, TREES_ERR_CAPACITY, e);
             sm.bc32[0] = b;
@@ -1696,7 +1696,7 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
     const uint32_t off = block_scan_u32<BS>(nc, 0, &ftot, &any, sm);
     if (ftot) {
         if (threadIdx.x == 0) {
-            const uint32_t b = atomicAdd(&ctl->cnt[ep], ftot);
+            const uint32_t b = atomicAdd(fork_ctr(ctl, ep), ftot);
             const bool over = (unsigned long long)base + b + ftot > c.cap;
             if (over) set_err(ctl, TREES_ERR_CAPACITY, e);
             sm.bc32[0] = b;
@@ -1799,7 +1799,7 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
     const uint32_t off = block_scan_u32<BS>(nc, 0, &ftot, &any, sm);
     if (ftot) {
         if (threadIdx.x == 0) {
-            const uint32_t b = atomicAdd(&ctl->cnt[ep], ftot);
+            const uint32_t b = atomicAdd(fork_ctr(ctl, ep), ftot);
             const bool over = (unsigned long long)base + b + ftot > c.cap;
             if (over) set_err(ctl, TREES_ERR_CAPACITY, e);
             sm.bc32[0] = b;

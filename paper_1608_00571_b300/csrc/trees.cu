@@ -107,13 +107,7 @@ __global__ void __launch_bounds__(BS) k_epoch(Ctl *ctl, Conf c, unsigned long lo
     __syncthreads();
     if (sm.stop) return;
     const uint32_t cen = sm.cen, lo = sm.lo, hi = sm.hi, base = sm.base, e = sm.next, ep = e % 3u;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const uint32_t q = (e + 1u) % 3u;
-        ctl->cnt[q] = 0u;
-        ctl->join[q] = 0u;
-        ctl->mt_ctr[q] = 0ull;
-        ctl->me_ctr[q] = 0ull;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) clear_epoch_slot(ctl, (e + 1u) % 3u);
     Acc acc = {0u, 0u, 0u};
     int par = 0;
     bool jn = false;
@@ -169,7 +163,7 @@ __global__ void k_phase3(Ctl *ctl, Conf c, cudaGraphConditionalHandle h) {
     } else {
         const uint32_t e = ctl->g_e, ep = e % 3u;
         const uint32_t cen = ctl->g_cen, lo = ctl->g_lo, hi = ctl->g_hi, base = ctl->g_base;
-        const uint32_t f = ctl->cnt[ep], jf = ctl->join[ep];
+        const uint32_t f = *fork_ctr(ctl, ep), jf = ctl->join[ep];
         const unsigned long long mt = ctl->mt_ctr[ep], me = ctl->me_ctr[ep];
         uint32_t sp = ctl->g_sp, next = base;
         int ok = 1;
@@ -694,7 +688,7 @@ static int run_hostloop(trees_ctx *x, cudaStream_t st) {
                 break;
             }
         }
-        const uint32_t f = h->cnt[ep], jf = h->join[ep];
+        const uint32_t f = (uint32_t)(h->ew[ep] >> 32), jf = h->join[ep];
         if (jf) stk.push_back(R{cen, lo, hi});
         if (f) {
             stk.push_back(R{cen + 1u, base, base + f});
