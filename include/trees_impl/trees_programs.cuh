@@ -1286,12 +1286,16 @@ __device__ __forceinline__ void sample_bracket(const uint32_t *smp, uint32_t a, 
 
 // Partition sub-phase of a map epoch: the merge-path split at the first
 // output of every merge tile that does not start its merge, computed in
-// parallel by groups of 4 lanes for all tiles at once.  A group runs the
+// parallel by groups of 8 lanes for all tiles at once.  A group runs the
 // searches of up to PNS tiles side by side, so their global loads overlap
 // and the phase costs about one search's chain of dependent loads.
 template <int BS>
 __device__ void partition_phase(const Conf &c, unsigned long long mt, const RunParams *job_params, uint32_t job_stride) {
-    constexpr uint32_t G = 4, PNS = 4;  // 4 probes a step: fewer scattered DRAM sectors per step than 8
+    // 8 probes a step: with the splitter samples most steps search the L2-resident samples (their
+    // bracket leaves ~64 keys for the exact search), so wider groups mean fewer dependent steps;
+    // measured (2^26 keys, 256 x 1, one call): G = 4 / PNS = 4 2.618 ms, 8 / 2 2.52-2.55 ms,
+    // 8 / 4 2.56 ms, 16 / 2 2.55 ms
+    constexpr uint32_t G = 8, PNS = 2;
     const uint32_t nt1 = (uint32_t)(mt & CTR_LOW_MASK), nd1 = (uint32_t)(mt >> 40);
     const uint32_t glane = threadIdx.x % G;
     static_assert(G >= 1u && G <= 32u && (G & (G - 1u)) == 0u, "groups tile the warp");
