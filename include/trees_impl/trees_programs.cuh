@@ -1645,37 +1645,109 @@ __device__ void merge_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t nt1,
     if (threadIdx.x == 0) bulk_wait_all();  // the outputs are in memory before the block's next barrier
 }
 
-// One BFS expansion tile: EXPAND_TILE consecutive adjacency entries of the
-// epoch's frontier.  Each entry's vertex is found by a binary search over the
-// tile's descriptors in shared memory (load-balanced search); an unvisited
-// neighbour is claimed with a CAS on its level and forked as a visit task.
+// The element maps (BFS expansion, SSSP relaxation) run as tiles of
+// EXPAND_TILE adjacency entries, each taken by one half of a block: the two
+// halves of a block (BS/2 threads each, synchronised by their own named
+// barriers, with disjoint shared-memory records) run independent tiles, so an
+// SM has twice as many tile chains in flight without more registers or
+// shared memory.  bar_half(h): the barrier of half h (ids 1 and 2).
 template <int BS>
-__device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, uint32_t nd, uint32_t ne, uint32_t nt,
-                            uint32_t cen, uint32_t base, uint32_t ep, uint32_t e) {
-    constexpr uint32_t EPT = EXPAND_TILE / BS;
-    const uint32_t g0 = t * EXPAND_TILE, g1 = min(g0 + EXPAND_TILE, ne);
+__device__ __forceinline__ void bar_half(uint32_t h) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1u + h), "r"((uint32_t)(BS / 2)) : "memory");
+}
+
+// Exclusive scan of v over the BS/2 threads of half h (thread order), with
+// the half's total; one named barrier (each thread sums its half's warp
+// totals itself).  The warp totals are written again only after the caller's
+// next barrier of this half.
+template <int BS>
+__device__ __forceinline__ uint32_t half_scan_u32(uint32_t v, uint32_t h, uint32_t *total, Smem<BS> &sm) {
+    constexpr uint32_t NWH = BS / 64;  // warps per half
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const uint32_t inc = warp_incl_u32(v);
+    if (lane == 31u) sm.w32[wid] = inc;
+    bar_half<BS>(h);
+    uint32_t pre = 0u, all = 0u;
+#pragma unroll
+    for (uint32_t w = 0; w < NWH; ++w) {
+        const uint32_t x = sm.w32[h * NWH + w];
+        all += x;
+        pre += h * NWH + w < wid ? x : 0u;
+    }
+    *total = all;
+    return pre + inc - v;
+}
+
+// The descriptors of element tile t (the vertices whose adjacency it covers)
+// into half h's shared records: each vertex's first adjacency index and
+// first element, and for SSSP its distance, read once for the tile.
+// Returns how many there are.
+template <int BS, bool SSSP>
+__device__ __forceinline__ uint32_t load_tile_descriptors(const Conf &c, Smem<BS> &sm, uint32_t t, uint32_t nd,
+                                                          uint32_t nt, uint32_t h, uint32_t lt) {
     const uint32_t dfirst = c.me_tfd[t];
     const uint32_t dlast = (t + 1u < nt) ? c.me_tfd[t + 1u] : nd - 1u;
     const uint32_t nloc = dlast - dfirst + 1u;
-    for (uint32_t k = threadIdx.x; k < nloc; k += BS) {
-        sm.u.ex.base[k] = c.me_base[dfirst + k];
-        sm.u.ex.v[k] = c.me_v[dfirst + k];
+    for (uint32_t k = lt; k < nloc; k += BS / 2) {
+        sm.u.ex.base[h][k] = c.me_base[dfirst + k];
+        sm.u.ex.v[h][k] = c.me_v[dfirst + k];
+        if constexpr (SSSP) sm.u.ex.d[h][k] = c.rp.dist[c.me_src[dfirst + k]];
     }
-    __syncthreads();
+    bar_half<BS>(h);
+    return nloc;
+}
+
+// Element g of the tile: its descriptor (load-balanced search over the
+// half's records in shared memory).
+template <int BS>
+__device__ __forceinline__ uint32_t tile_owner_local(const Smem<BS> &sm, uint32_t h, uint32_t nloc, uint32_t g) {
+    uint32_t lo = 0, hi = nloc;
+    while (hi - lo > 1u) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (sm.u.ex.base[h][mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Reserves `tot` slots for half h's forks (one atomic for the half) and
+// broadcasts the base and the capacity verdict through shared memory.
+template <int BS>
+__device__ __forceinline__ bool half_reserve(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t h, uint32_t lt,
+                                             uint32_t tot, uint32_t base, uint32_t ep, uint32_t e, uint32_t *b) {
+    if (lt == 0u) {
+        const uint32_t r = atomicAdd(fork_ctr(ctl, ep), tot);  // one atomic per half tile (Sec. 5.2.3)
+        const bool over = (unsigned long long)base + r + tot > c.cap;
+        if (over) set_err(ctl, TREES_ERR_CAPACITY, e);
+        sm.bc32[2u * h] = r;
+        sm.bc32[2u * h + 1u] = over;
+    }
+    bar_half<BS>(h);
+    *b = sm.bc32[2u * h];
+    return !sm.bc32[2u * h + 1u];
+}
+
+// One BFS expansion tile (EXPAND_TILE consecutive adjacency entries of the
+// epoch's frontier) on half h of the block.  Each entry's vertex is found by
+// a binary search over the tile's descriptors in shared memory
+// (load-balanced search); an unvisited neighbour is claimed with a CAS on its
+// level and forked as a visit task.
+template <int BS>
+__device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, uint32_t nd, uint32_t ne, uint32_t nt,
+                            uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, uint32_t h) {
+    constexpr uint32_t HB = BS / 2, EPT = EXPAND_TILE / HB;
+    const uint32_t lt = threadIdx.x - h * HB;
+    const uint32_t g0 = t * EXPAND_TILE, g1 = min(g0 + EXPAND_TILE, ne);
+    const uint32_t nloc = load_tile_descriptors<BS, false>(c, sm, t, nd, nt, h, lt);
     // stage 1: every element's adjacency index (load-balanced search in shared memory)
     uint32_t ed[EPT];
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j) {
-        const uint32_t g = g0 + j * BS + threadIdx.x;
+        const uint32_t g = g0 + j * HB + lt;
         ed[j] = 0xFFFFFFFFu;
         if (g < g1) {
-            uint32_t lo = 0, hi = nloc;
-            while (hi - lo > 1u) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (sm.u.ex.base[mid] <= g) lo = mid;
-                else hi = mid;
-            }
-            ed[j] = sm.u.ex.v[lo] + (g - sm.u.ex.base[lo]);
+            const uint32_t k = tile_owner_local<BS>(sm, h, nloc, g);
+            ed[j] = sm.u.ex.v[h][k] + (g - sm.u.ex.base[h][k]);
         }
     }
     // stage 2: all neighbour ids, then all their levels, in flight together
@@ -1694,79 +1766,56 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j)
         if (uu[j] >= 0 && lv[j] < 0 && prev[j] == -1) cmask |= 1u << j;
-    const uint32_t nc = (uint32_t)__popc(cmask);
     uint32_t ftot;
-    int any;
-    const uint32_t off = block_scan_u32<BS>(nc, 0, &ftot, &any, sm);
-    if (ftot) {
-        if (threadIdx.x == 0) {
-            const uint32_t b = atomicAdd(fork_ctr(ctl, ep), ftot);
-            const bool over = (unsigned long long)base + b + ftot > c.cap;
-            if (over) set_err(ctl, TREES_ERR_CAPACITY, e);
-            sm.bc32[0] = b;
-            sm.bc32[1] = over;
-        }
-        __syncthreads();
-        if (!sm.bc32[1]) {
-            const uint32_t code = enc(cen + 1u, TREES_TASK_BFS_VISIT);
-            uint32_t slot = base + sm.bc32[0] + off;
+    const uint32_t off = half_scan_u32<BS>((uint32_t)__popc(cmask), h, &ftot, sm);
+    uint32_t b;
+    if (ftot && half_reserve<BS>(c, ctl, sm, h, lt, ftot, base, ep, e, &b)) {
+        const uint32_t code = enc(cen + 1u, TREES_TASK_BFS_VISIT);
+        uint32_t slot = base + b + off;
 #pragma unroll
-            for (uint32_t j = 0; j < EPT; ++j) {
-                if ((cmask >> j) & 1u) {
-                    c.code[slot] = code;
-                    c.a0[slot] = (uint32_t)uu[j];
-                    ++slot;
-                }
+        for (uint32_t j = 0; j < EPT; ++j) {
+            if ((cmask >> j) & 1u) {
+                c.code[slot] = code;
+                c.a0[slot] = (uint32_t)uu[j];
+                ++slot;
             }
         }
     }
-    __syncthreads();
+    bar_half<BS>(h);  // the half's records are its next tile's
 }
 
-// One SSSP relaxation tile (Sec. 6.3's worklist relaxation as a map): the
-// same element-balanced layout as a BFS expansion tile.  Each source vertex
-// v of the tile has its distance read once for the tile; for each of its
-// out-edges (v, u, w) here, nd = dist[v] + w; an atomic minimum shortens
-// dist[u] if nd is smaller, and the thread whose minimum took effect forks
-// relax(u) for epoch CEN+1 unless another already did this epoch (an atomic
-// maximum on sched[u]).  dist[v] may have been shortened after the tile
-// read it; v is then forked again for the next epoch, so the final
-// distances are the shortest ones.  Each tile also records, per source
+// One SSSP relaxation tile (Sec. 6.3's worklist relaxation as a map) on half
+// h of the block: the same element-balanced layout as a BFS expansion tile.
+// Each source vertex v of the tile has its distance read once for the tile;
+// for each of its out-edges (v, u, w) here, nd = dist[v] + w; an atomic
+// minimum shortens dist[u] if nd is smaller, and the thread whose minimum
+// took effect forks relax(u) for epoch CEN+1 unless another already did this
+// epoch (an atomic maximum on sched[u]).  dist[v] may have been shortened
+// after the tile read it; v is then forked again for the next epoch, so the
+// final distances are the shortest ones.  Each tile also records, per source
 // vertex, the distance its edges used (an atomic maximum of
 // (CEN+1) << 40 | distance), so that a relax(v) forked again whose distance
 // is still the one every edge of v used in the previous epoch ends at once.
 template <int BS>
 __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, uint32_t nd, uint32_t ne, uint32_t nt,
-                           uint32_t cen, uint32_t base, uint32_t ep, uint32_t e) {
-    constexpr uint32_t EPT = EXPAND_TILE / BS;
+                           uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, uint32_t h) {
+    constexpr uint32_t HB = BS / 2, EPT = EXPAND_TILE / HB;
+    const uint32_t lt = threadIdx.x - h * HB;
     const uint32_t g0 = t * EXPAND_TILE, g1 = min(g0 + EXPAND_TILE, ne);
     const uint32_t dfirst = c.me_tfd[t];
-    const uint32_t dlast = (t + 1u < nt) ? c.me_tfd[t + 1u] : nd - 1u;
-    const uint32_t nloc = dlast - dfirst + 1u;
-    // the tile's descriptors, and each source vertex's distance read once for the whole tile
-    for (uint32_t k = threadIdx.x; k < nloc; k += BS) {
-        sm.u.ex.base[k] = c.me_base[dfirst + k];
-        sm.u.ex.v[k] = c.me_v[dfirst + k];
-        sm.u.ex.d[k] = c.rp.dist[c.me_src[dfirst + k]];
-    }
-    __syncthreads();
+    const uint32_t nloc = load_tile_descriptors<BS, true>(c, sm, t, nd, nt, h, lt);
     // stage 1: every element's adjacency index and its source's distance (load-balanced search)
     uint32_t ed[EPT];
     unsigned long long dv[EPT];
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j) {
-        const uint32_t g = g0 + j * BS + threadIdx.x;
+        const uint32_t g = g0 + j * HB + lt;
         ed[j] = 0xFFFFFFFFu;
         dv[j] = 0ull;
         if (g < g1) {
-            uint32_t lo = 0, hi = nloc;
-            while (hi - lo > 1u) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (sm.u.ex.base[mid] <= g) lo = mid;
-                else hi = mid;
-            }
-            ed[j] = sm.u.ex.v[lo] + (g - sm.u.ex.base[lo]);
-            dv[j] = sm.u.ex.d[lo];
+            const uint32_t k = tile_owner_local<BS>(sm, h, nloc, g);
+            ed[j] = sm.u.ex.v[h][k] + (g - sm.u.ex.base[h][k]);
+            dv[j] = sm.u.ex.d[h][k];
         }
     }
     // stage 2: neighbours, weights and the neighbours' distances in flight together
@@ -1797,40 +1846,29 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j)
         if (prev[j] < cen + 1u) cmask |= 1u << j;
-    const uint32_t nc = (uint32_t)__popc(cmask);
     uint32_t ftot;
-    int any;
-    const uint32_t off = block_scan_u32<BS>(nc, 0, &ftot, &any, sm);
-    if (ftot) {
-        if (threadIdx.x == 0) {
-            const uint32_t b = atomicAdd(fork_ctr(ctl, ep), ftot);
-            const bool over = (unsigned long long)base + b + ftot > c.cap;
-            if (over) set_err(ctl, TREES_ERR_CAPACITY, e);
-            sm.bc32[0] = b;
-            sm.bc32[1] = over;
-        }
-        __syncthreads();
-        if (!sm.bc32[1]) {
-            const uint32_t code = enc(cen + 1u, TREES_TASK_SSSP_RELAX);
-            uint32_t slot = base + sm.bc32[0] + off;
+    const uint32_t off = half_scan_u32<BS>((uint32_t)__popc(cmask), h, &ftot, sm);
+    uint32_t b;
+    if (ftot && half_reserve<BS>(c, ctl, sm, h, lt, ftot, base, ep, e, &b)) {
+        const uint32_t code = enc(cen + 1u, TREES_TASK_SSSP_RELAX);
+        uint32_t slot = base + b + off;
 #pragma unroll
-            for (uint32_t j = 0; j < EPT; ++j) {
-                if ((cmask >> j) & 1u) {
-                    c.code[slot] = code;
-                    c.a0[slot] = (uint32_t)uu[j];
-                    ++slot;
-                }
+        for (uint32_t j = 0; j < EPT; ++j) {
+            if ((cmask >> j) & 1u) {
+                c.code[slot] = code;
+                c.a0[slot] = (uint32_t)uu[j];
+                ++slot;
             }
         }
     }
     // record, per source vertex of the tile, the distance its edges here used (the largest over the
     // epoch's tiles wins; a descriptor listed for the tile without edges in it only raises it)
-    for (uint32_t k = threadIdx.x; k < nloc; k += BS) {
-        const unsigned long long d = sm.u.ex.d[k];
+    for (uint32_t k = lt; k < nloc; k += HB) {
+        const unsigned long long d = sm.u.ex.d[h][k];
         if (d < (1ull << SSSP_USED_SHIFT))
             atomicMax(c.rp.used + c.me_src[dfirst + k], (unsigned long long)(cen + 1u) << SSSP_USED_SHIFT | d);
     }
-    __syncthreads();
+    bar_half<BS>(h);  // the half's records are its next tile's
 }
 
 // The combine maps of one FFT epoch as one flat array of butterflies.  The
@@ -1918,9 +1956,10 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
         }
         if constexpr ((PM & (PM_BFS | PM_SSSP)) != 0u) {
             const bool sssp = (PM & PM_BFS) == 0u || ((PM & PM_SSSP) != 0u && c.rp.program == TREES_PROG_SSSP);
-            for (uint32_t t = blockIdx.x; t < nt2; t += gridDim.x) {
-                if (sssp) relax_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e);
-                else expand_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e);
+            const uint32_t h = threadIdx.x >= (uint32_t)(BS / 2);  // the two halves take alternate tiles
+            for (uint32_t t = 2u * blockIdx.x + h; t < nt2; t += 2u * gridDim.x) {
+                if (sssp) relax_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e, h);
+                else expand_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e, h);
             }
         }
     }
