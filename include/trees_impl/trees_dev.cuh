@@ -38,7 +38,9 @@ __host__ __device__ constexpr uint32_t merge_stage(int bs) { return merge_tile(b
 // Merge tiles staged per block (a ring of TMA buffers): one merging while the
 // next streams in.
 __host__ __device__ constexpr int merge_nst(int) { return 2; }
-constexpr uint32_t EXPAND_TILE = 1024;          // adjacency entries of one BFS / SSSP expansion tile (half a block's)
+constexpr uint32_t EXPAND_TILE = 512;           // adjacency entries of one BFS / SSSP expansion tile (a block part's)
+// Parts of a block that run expansion tiles independently (8 entries per thread per tile).
+#define EXPAND_PARTS(BS) ((BS) >= 256 ? 4u : 2u)
 constexpr uint32_t JR_SLOTS = 1024;             // tile slots whose join operands can be prefetched
 constexpr uint32_t SMP_SHIFT = 6;               // mergesort splitter samples: every 64th key of a run
 constexpr int MCHUNK = 64;                      // merge tiles a block resolves at once
@@ -224,10 +226,10 @@ struct Smem {
     unsigned int solo_late;  // a solo run has used its share of the barrier timeout
     union alignas(16) {
         uint32_t mg[merge_nst(BS)][merge_stage(BS)];  // staged merge tile inputs (TMA destinations)
-        struct {  // one set of records per half block (its current expansion tile)
-            uint32_t base[2][EXPAND_TILE + 2];
-            uint32_t v[2][EXPAND_TILE + 2];
-            unsigned long long d[2][EXPAND_TILE + 2];  // SSSP: the source's distance, read once per tile
+        struct {  // one set of records per block part (its current expansion tile)
+            uint32_t base[4][EXPAND_TILE + 2];
+            uint32_t v[4][EXPAND_TILE + 2];
+            unsigned long long d[4][EXPAND_TILE + 2];  // SSSP: the source's distance, read once per tile
         } ex;
         unsigned long long jr[2][JR_SLOTS][2];  // fib joins: the next tile's children's results, prefetched
     } u;

@@ -1646,27 +1646,28 @@ __device__ void merge_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t nt1,
 }
 
 // The element maps (BFS expansion, SSSP relaxation) run as tiles of
-// EXPAND_TILE adjacency entries, each taken by one half of a block: the two
-// halves of a block (BS/2 threads each, synchronised by their own named
-// barriers, with disjoint shared-memory records) run independent tiles, so an
-// SM has twice as many tile chains in flight without more registers or
-// shared memory.  bar_half(h): the barrier of half h (ids 1 and 2).
+// EXPAND_TILE adjacency entries, each taken by one part of a block: the
+// EXPAND_PARTS(BS) parts of a block (BS / parts threads each, synchronised by
+// their own named barriers, with disjoint shared-memory records) run
+// independent tiles, so an SM has several tile chains in flight per block
+// without more registers or shared memory.  bar_part(h): the barrier of part h
+// (ids 1..parts).
 template <int BS>
-__device__ __forceinline__ void bar_half(uint32_t h) {
-    asm volatile("bar.sync %0, %1;" ::"r"(1u + h), "r"((uint32_t)(BS / 2)) : "memory");
+__device__ __forceinline__ void bar_part(uint32_t h) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1u + h), "r"((uint32_t)(BS / EXPAND_PARTS(BS))) : "memory");
 }
 
-// Exclusive scan of v over the BS/2 threads of half h (thread order), with
-// the half's total; one named barrier (each thread sums its half's warp
+// Exclusive scan of v over the threads of block part h (thread order), with
+// the part's total; one named barrier (each thread sums its part's warp
 // totals itself).  The warp totals are written again only after the caller's
-// next barrier of this half.
+// next barrier of this part.
 template <int BS>
-__device__ __forceinline__ uint32_t half_scan_u32(uint32_t v, uint32_t h, uint32_t *total, Smem<BS> &sm) {
-    constexpr uint32_t NWH = BS / 64;  // warps per half
+__device__ __forceinline__ uint32_t part_scan_u32(uint32_t v, uint32_t h, uint32_t *total, Smem<BS> &sm) {
+    constexpr uint32_t NWH = BS / 32 / EXPAND_PARTS(BS);  // warps per part
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     const uint32_t inc = warp_incl_u32(v);
     if (lane == 31u) sm.w32[wid] = inc;
-    bar_half<BS>(h);
+    bar_part<BS>(h);
     uint32_t pre = 0u, all = 0u;
 #pragma unroll
     for (uint32_t w = 0; w < NWH; ++w) {
@@ -1679,7 +1680,7 @@ __device__ __forceinline__ uint32_t half_scan_u32(uint32_t v, uint32_t h, uint32
 }
 
 // The descriptors of element tile t (the vertices whose adjacency it covers)
-// into half h's shared records: each vertex's first adjacency index and
+// into part h's shared records: each vertex's first adjacency index and
 // first element, and for SSSP its distance, read once for the tile.
 // Returns how many there are.
 template <int BS, bool SSSP>
@@ -1688,17 +1689,17 @@ __device__ __forceinline__ uint32_t load_tile_descriptors(const Conf &c, Smem<BS
     const uint32_t dfirst = c.me_tfd[t];
     const uint32_t dlast = (t + 1u < nt) ? c.me_tfd[t + 1u] : nd - 1u;
     const uint32_t nloc = dlast - dfirst + 1u;
-    for (uint32_t k = lt; k < nloc; k += BS / 2) {
+    for (uint32_t k = lt; k < nloc; k += BS / EXPAND_PARTS(BS)) {
         sm.u.ex.base[h][k] = c.me_base[dfirst + k];
         sm.u.ex.v[h][k] = c.me_v[dfirst + k];
         if constexpr (SSSP) sm.u.ex.d[h][k] = c.rp.dist[c.me_src[dfirst + k]];
     }
-    bar_half<BS>(h);
+    bar_part<BS>(h);
     return nloc;
 }
 
 // Element g of the tile: its descriptor (load-balanced search over the
-// half's records in shared memory).
+// part's records in shared memory).
 template <int BS>
 __device__ __forceinline__ uint32_t tile_owner_local(const Smem<BS> &sm, uint32_t h, uint32_t nloc, uint32_t g) {
     uint32_t lo = 0, hi = nloc;
@@ -1710,32 +1711,32 @@ __device__ __forceinline__ uint32_t tile_owner_local(const Smem<BS> &sm, uint32_
     return lo;
 }
 
-// Reserves `tot` slots for half h's forks (one atomic for the half) and
-// broadcasts the base and the capacity verdict through shared memory.
+// Reserves `tot` slots for part h's forks (one atomic for the part's tile)
+// and broadcasts the base and the capacity verdict through shared memory.
 template <int BS>
-__device__ __forceinline__ bool half_reserve(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t h, uint32_t lt,
+__device__ __forceinline__ bool part_reserve(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t h, uint32_t lt,
                                              uint32_t tot, uint32_t base, uint32_t ep, uint32_t e, uint32_t *b) {
     if (lt == 0u) {
-        const uint32_t r = atomicAdd(fork_ctr(ctl, ep), tot);  // one atomic per half tile (Sec. 5.2.3)
+        const uint32_t r = atomicAdd(fork_ctr(ctl, ep), tot);  // one atomic per part tile (Sec. 5.2.3)
         const bool over = (unsigned long long)base + r + tot > c.cap;
         if (over) set_err(ctl, TREES_ERR_CAPACITY, e);
         sm.bc32[2u * h] = r;
         sm.bc32[2u * h + 1u] = over;
     }
-    bar_half<BS>(h);
+    bar_part<BS>(h);
     *b = sm.bc32[2u * h];
     return !sm.bc32[2u * h + 1u];
 }
 
 // One BFS expansion tile (EXPAND_TILE consecutive adjacency entries of the
-// epoch's frontier) on half h of the block.  Each entry's vertex is found by
+// epoch's frontier) on part h of the block.  Each entry's vertex is found by
 // a binary search over the tile's descriptors in shared memory
 // (load-balanced search); an unvisited neighbour is claimed with a CAS on its
 // level and forked as a visit task.
 template <int BS>
 __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, uint32_t nd, uint32_t ne, uint32_t nt,
                             uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, uint32_t h) {
-    constexpr uint32_t HB = BS / 2, EPT = EXPAND_TILE / HB;
+    constexpr uint32_t HB = BS / EXPAND_PARTS(BS), EPT = EXPAND_TILE / HB;
     const uint32_t lt = threadIdx.x - h * HB;
     const uint32_t g0 = t * EXPAND_TILE, g1 = min(g0 + EXPAND_TILE, ne);
     const uint32_t nloc = load_tile_descriptors<BS, false>(c, sm, t, nd, nt, h, lt);
@@ -1767,9 +1768,9 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
     for (uint32_t j = 0; j < EPT; ++j)
         if (uu[j] >= 0 && lv[j] < 0 && prev[j] == -1) cmask |= 1u << j;
     uint32_t ftot;
-    const uint32_t off = half_scan_u32<BS>((uint32_t)__popc(cmask), h, &ftot, sm);
+    const uint32_t off = part_scan_u32<BS>((uint32_t)__popc(cmask), h, &ftot, sm);
     uint32_t b;
-    if (ftot && half_reserve<BS>(c, ctl, sm, h, lt, ftot, base, ep, e, &b)) {
+    if (ftot && part_reserve<BS>(c, ctl, sm, h, lt, ftot, base, ep, e, &b)) {
         const uint32_t code = enc(cen + 1u, TREES_TASK_BFS_VISIT);
         uint32_t slot = base + b + off;
 #pragma unroll
@@ -1781,10 +1782,10 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
             }
         }
     }
-    bar_half<BS>(h);  // the half's records are its next tile's
+    bar_part<BS>(h);  // the part's records are its next tile's
 }
 
-// One SSSP relaxation tile (Sec. 6.3's worklist relaxation as a map) on half
+// One SSSP relaxation tile (Sec. 6.3's worklist relaxation as a map) on part
 // h of the block: the same element-balanced layout as a BFS expansion tile.
 // Each source vertex v of the tile has its distance read once for the tile;
 // for each of its out-edges (v, u, w) here, nd = dist[v] + w; an atomic
@@ -1799,7 +1800,7 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
 template <int BS>
 __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, uint32_t nd, uint32_t ne, uint32_t nt,
                            uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, uint32_t h) {
-    constexpr uint32_t HB = BS / 2, EPT = EXPAND_TILE / HB;
+    constexpr uint32_t HB = BS / EXPAND_PARTS(BS), EPT = EXPAND_TILE / HB;
     const uint32_t lt = threadIdx.x - h * HB;
     const uint32_t g0 = t * EXPAND_TILE, g1 = min(g0 + EXPAND_TILE, ne);
     const uint32_t dfirst = c.me_tfd[t];
@@ -1847,9 +1848,9 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
     for (uint32_t j = 0; j < EPT; ++j)
         if (prev[j] < cen + 1u) cmask |= 1u << j;
     uint32_t ftot;
-    const uint32_t off = half_scan_u32<BS>((uint32_t)__popc(cmask), h, &ftot, sm);
+    const uint32_t off = part_scan_u32<BS>((uint32_t)__popc(cmask), h, &ftot, sm);
     uint32_t b;
-    if (ftot && half_reserve<BS>(c, ctl, sm, h, lt, ftot, base, ep, e, &b)) {
+    if (ftot && part_reserve<BS>(c, ctl, sm, h, lt, ftot, base, ep, e, &b)) {
         const uint32_t code = enc(cen + 1u, TREES_TASK_SSSP_RELAX);
         uint32_t slot = base + b + off;
 #pragma unroll
@@ -1868,7 +1869,7 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
         if (d < (1ull << SSSP_USED_SHIFT))
             atomicMax(c.rp.used + c.me_src[dfirst + k], (unsigned long long)(cen + 1u) << SSSP_USED_SHIFT | d);
     }
-    bar_half<BS>(h);  // the half's records are its next tile's
+    bar_part<BS>(h);  // the part's records are its next tile's
 }
 
 // The combine maps of one FFT epoch as one flat array of butterflies.  The
@@ -1956,8 +1957,9 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
         }
         if constexpr ((PM & (PM_BFS | PM_SSSP)) != 0u) {
             const bool sssp = (PM & PM_BFS) == 0u || ((PM & PM_SSSP) != 0u && c.rp.program == TREES_PROG_SSSP);
-            const uint32_t h = threadIdx.x >= (uint32_t)(BS / 2);  // the two halves take alternate tiles
-            for (uint32_t t = 2u * blockIdx.x + h; t < nt2; t += 2u * gridDim.x) {
+            constexpr uint32_t P = EXPAND_PARTS(BS);
+            const uint32_t h = threadIdx.x / (uint32_t)(BS / P);  // the parts take interleaved tiles
+            for (uint32_t t = P * blockIdx.x + h; t < nt2; t += P * gridDim.x) {
                 if (sssp) relax_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e, h);
                 else expand_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e, h);
             }
