@@ -62,9 +62,12 @@ __host__ __device__ constexpr int persistent_min_blocks(int bs, uint32_t pm, int
 // Dynamic shared memory of a persistent kernel.  The fib kernels run their
 // join ranges through a ring of asynchronous copies there (fib_join_tiles):
 // NA stages of (code, link) and NB of result pairs, 8 and 16 bytes per slot,
-// (NA, NB) = (4, 3) when that fits beside the kernel's static shared memory
+// (NA, NB) = (5, 3) when that fits beside the kernel's static shared memory
 // at the residency its register budget targets (228 KB per SM, 1 KB of it
-// reserved per block), else (3, 2), else no ring (the register path).
+// reserved per block), else (4, 3), else (3, 2), else no ring (the register
+// path).  NA - NB tiles of lookahead hide the (code, link) copies, NB - 1 the
+// operand copies: (5, 3) measured 0.4403 ms per fib(34) at 512 x 2 against
+// 0.4464 ms for (4, 3) in one A/B call; (6, 3) and (7, 4) gave the same as (5, 3).
 constexpr int SMEM_PER_SM = 228 * 1024, SMEM_RESERVED_PER_BLOCK = 1024;
 
 template <int BS, int TPT, uint32_t PM>
@@ -77,7 +80,8 @@ __host__ __device__ constexpr int ring_budget() {
 // (NA, NB) packed as NA * 16 + NB, or 0.
 template <int BS, int TPT, uint32_t PM>
 __host__ __device__ constexpr int ring_depths() {
-    return ring_budget<BS, TPT, PM>() >= 80 * BS * TPT ? 4 * 16 + 3
+    return ring_budget<BS, TPT, PM>() >= 88 * BS * TPT ? 5 * 16 + 3
+           : ring_budget<BS, TPT, PM>() >= 80 * BS * TPT ? 4 * 16 + 3
            : ring_budget<BS, TPT, PM>() >= 56 * BS * TPT ? 3 * 16 + 2
                                                          : 0;
 }

@@ -871,10 +871,15 @@ __host__ __device__ constexpr uint32_t fib_chunk_tiles() {
 }
 
 // Tiles of loads a thread keeps in flight in the count pass (registers:
-// 2 * TPT words per tile).
-template <int TPT>
+// 2 * TPT words per tile).  Blocks of 512 threads run one per SM with up to
+// 128 registers a thread, so they hold eight slots' loads in flight (fib(34)
+// at 512 x 2: 0.4342 ms with four tiles against 0.4403 ms with two); smaller
+// blocks share the SM's registers with two or more others, and 1024-thread
+// blocks have 64 a thread, so they keep two tiles (four measured 0.4874
+// against 0.469 ms at 256 x 2).
+template <int BS, int TPT>
 __host__ __device__ constexpr int fib_prefetch_tiles() {
-    return TPT >= 2 ? 2 : 8;
+    return TPT == 1 ? 8 : BS == 512 ? 8 / TPT : 2;
 }
 
 template <int BS, int TPT>
@@ -903,7 +908,7 @@ __device__ __forceinline__ bool fib_fresh_tiles(const Conf &c, Ctl *ctl, Smem<BS
         const uint32_t nt = (uint32_t)min((unsigned long long)CT, (hi - t0 + step - 1ull) / step);
         // ---- pass 1: count.  The loads of the next PD-1 tiles are in flight while a tile is decoded
         // (a ring of PD tiles of code and n in registers).
-        constexpr int PD = fib_prefetch_tiles<TPT>();
+        constexpr int PD = fib_prefetch_tiles<BS, TPT>();
         uint32_t rc[PD][TPT], rn[PD][TPT];
 #pragma unroll
         for (int u = 0; u < PD - 1; ++u) {
@@ -1067,12 +1072,18 @@ __device__ __forceinline__ void fib_join_tiles(const Conf &c, unsigned long long
         }
         cp_async_commit();
     };
-    // prologue: the links of tiles 0..LB-1 land, then their operands are copied; tiles up to LA-1 stream in
+    // prologue: the links of tiles 0..LB-1 land, then their operands are copied; tiles up to LA-1 stream in.
+    // Each operand group is followed by an empty group, standing for the (code, link) group the loop
+    // commits between two operand groups, so that the loop's wait counts below hold from tile 0 on for
+    // any depths (without it, tile 0's operands are waited for only when LB >= 2 (LA - LB)).
 #pragma unroll
     for (int j = 0; j < LA; ++j) issue_a((uint32_t)j);
     cp_async_wait_all();
 #pragma unroll
-    for (int j = 0; j < LB; ++j) issue_b((uint32_t)j);
+    for (int j = 0; j < LB; ++j) {
+        issue_b((uint32_t)j);
+        cp_async_commit();
+    }
     for (uint32_t j = 0; j < nt; ++j) {
         issue_a(j + LA);
         cp_async_wait_group<2 * (LA - LB)>();  // tile j+LB's (code, link)
