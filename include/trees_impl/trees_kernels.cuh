@@ -70,6 +70,13 @@ __host__ __device__ constexpr int persistent_min_blocks(int bs, uint32_t pm, int
 // 0.4464 ms for (4, 3) in one A/B call; (6, 3) and (7, 4) gave the same as (5, 3).
 constexpr int SMEM_PER_SM = 228 * 1024, SMEM_RESERVED_PER_BLOCK = 1024;
 
+// Ranges of at most SOLO_TILES tiles, for programs without map operations,
+// are worked by block 0 alone, epoch after epoch, each closed by a block
+// barrier instead of a grid barrier: the same epochs, ranges and fork counts
+// without the grid-wide round trip, which costs more than a tile or two of
+// work.
+constexpr uint32_t SOLO_TILES = 2;  // measured: 1 or 2 tiles best; 4 already slower
+
 template <int BS, int TPT, uint32_t PM>
 __host__ __device__ constexpr int ring_budget() {
     return PM != PM_FIB ? 0
@@ -87,8 +94,29 @@ __host__ __device__ constexpr int ring_depths() {
 }
 
 template <int BS, int TPT, uint32_t PM>
-__host__ __device__ constexpr size_t ring_bytes() {
+__host__ __device__ constexpr size_t join_ring_bytes() {
     return (size_t)((ring_depths<BS, TPT, PM>() >> 4) * 8 + (ring_depths<BS, TPT, PM>() & 15) * 16) * BS * TPT;
+}
+
+// After the join ring, the rest of the budget holds block 0's shadow of the
+// task vector's first slots for fib's solo runs (fib_solo_epoch): code, n,
+// link and result, 20 bytes per slot, for up to 2 * SOLO_TILES tiles of slots
+// (the most a run of solo fresh epochs allocates from slot 0: each range at
+// most SOLO_TILES tiles, each the children of the one before).
+constexpr uint32_t SHADOW_BYTES_PER_SLOT = 20;
+
+template <int BS, int TPT, uint32_t PM>
+__host__ __device__ constexpr uint32_t shadow_slots() {
+    return PM != PM_FIB || ring_budget<BS, TPT, PM>() <= (int)join_ring_bytes<BS, TPT, PM>() ? 0u
+           : ((uint32_t)(ring_budget<BS, TPT, PM>() - (int)join_ring_bytes<BS, TPT, PM>()) / SHADOW_BYTES_PER_SLOT <
+                      2u * SOLO_TILES * (uint32_t)(BS * TPT)
+                  ? (uint32_t)(ring_budget<BS, TPT, PM>() - (int)join_ring_bytes<BS, TPT, PM>()) / SHADOW_BYTES_PER_SLOT
+                  : 2u * SOLO_TILES * (uint32_t)(BS * TPT)) & ~3u;
+}
+
+template <int BS, int TPT, uint32_t PM>
+__host__ __device__ constexpr size_t ring_bytes() {
+    return join_ring_bytes<BS, TPT, PM>() + (size_t)SHADOW_BYTES_PER_SLOT * shadow_slots<BS, TPT, PM>();
 }
 
 // Dynamic shared memory bytes k_persistent<bs, tpt, program mask pm> is launched with.
@@ -121,6 +149,7 @@ struct SchedState {
     // trace timestamps (block 0): previous epoch's end, end of Phase 2, of partition, of maps
     unsigned long long t_prev, t_p2, t_pt, t_mp;
     unsigned long long t_solo;  // start of the current solo run
+    uint32_t sh_hi;             // fib: slots [0, sh_hi) have a current shadow entry (fib_solo_epoch)
 };
 
 // Phase 1 (thread 0): pop (CEN, NDRange) for epoch e and set
@@ -190,15 +219,209 @@ __device__ __forceinline__ void phase3(const Conf &c, Ctl *ctl, Smem<BS> &sm, ui
     }
 }
 
-// Ranges of at most SOLO_TILES tiles, for programs without map operations,
-// are worked by block 0 alone, epoch after epoch, each closed by a block
-// barrier instead of a grid barrier: the same epochs, ranges and fork counts
-// without the grid-wide round trip, which costs more than a tile or two of
-// work.
-constexpr uint32_t SOLO_TILES = 2;  // measured: 1 or 2 tiles best; 4 already slower
 template <int BS, int TPT, uint32_t PM>
 __device__ __forceinline__ bool solo_range(const Conf &c, uint32_t lo, uint32_t hi) {
     return (PM & PM_MAPS) == 0u && c.stall_epoch < 0 && hi - lo <= SOLO_TILES * (uint32_t)(BS * TPT);
+}
+
+// Block 0's shadow of the task vector's slots [0, cap) (fib; the dynamic
+// shared memory after the join ring).  Slots below SchedState::sh_hi hold the
+// current code, n, link and result there: those slots are written by block 0
+// alone from the solo epoch that brought them in until a grid epoch whose
+// range starts at or below them (a grid epoch writes only its own range and
+// the children above it, so it lowers sh_hi to its range's start).
+struct FibShadow {
+    unsigned long long *res;
+    uint32_t *code, *a0, *link;
+    uint32_t cap;
+};
+
+template <int BS, int TPT, uint32_t PM>
+__device__ __forceinline__ FibShadow fib_shadow(uint32_t *ring) {
+    constexpr uint32_t S = shadow_slots<BS, TPT, PM>();
+    FibShadow sh;
+    sh.res = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(ring) + join_ring_bytes<BS, TPT, PM>());
+    sh.code = reinterpret_cast<uint32_t *>(sh.res + S);
+    sh.a0 = sh.code + S;
+    sh.link = sh.a0 + S;
+    sh.cap = S;
+    return sh;
+}
+
+// One solo epoch of fib (Sec. 6.2's tasks; the range is at most SOLO_TILES
+// tiles): every thread loads all its slots of the range at once, from the
+// shadow where it holds them, else from the task vector; a fresh range's
+// internal tasks take their children after one block-wide count (block 0
+// forks all of the epoch's children, so no atomic is needed: they start at
+// oldNextFreeCore, row by row of the range, each warp's children of a row
+// contiguous so its stores coalesce), a join range's sums read their
+// operands from the shadow or the task vector.  Every write goes to the task
+// vector and, for slots below cap, to the shadow.  A fresh range starting at
+// sh_hi is copied into the shadow as it is read and raises sh_hi to its end;
+// children placed at sh_hi raise it past them.  Thread 0 updates sh_hi
+// (every thread reads it after the block barrier that closes the epoch).
+template <int BS, int TPT>
+__device__ __forceinline__ TileOut fib_solo_epoch(const Conf &c, Ctl *ctl, Smem<BS> &sm, const FibShadow &sh,
+                                                  uint32_t &sh_hi, uint32_t lo, uint32_t hi, uint32_t cen,
+                                                  uint32_t base, uint32_t e, int mode, Acc &acc) {
+    constexpr int R = (int)SOLO_TILES * TPT;  // rows of BS slots: the range is slots lo + j * BS + thread, j < R
+    const uint32_t hv = sh_hi, tid = threadIdx.x;
+    uint32_t cd[R], x[R];  // code, and n (fresh) or link (join)
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const uint32_t s = lo + (uint32_t)j * BS + tid;
+        const bool in = s < hi, shd = s < hv;
+        cd[j] = !in ? 0u : shd ? sh.code[s] : c.code[s];
+        x[j] = !in ? 0u : mode == LOAD_FRESH ? (shd ? sh.a0[s] : c.a0[s]) : (shd ? sh.link[s] : c.link[s]);
+    }
+    TileOut out = {0u, false, false};
+    if (mode == LOAD_FRESH) {
+        const bool fill = lo == hv;  // block-uniform
+        uint32_t fm = 0u;  // which of this thread's rows fork
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const uint32_t s = lo + (uint32_t)j * BS + tid;
+            if (fill && s < hi && s < sh.cap) {
+                sh.code[s] = cd[j];
+                sh.a0[s] = x[j];
+            }
+            const uint32_t t = task_type(cd[j], cen);
+            if (!t) continue;
+            acc.valid++;
+            if (t == TREES_TASK_FIB) {
+                const uint32_t n = x[j];
+                if (n < 2u || n <= c.rp.cutoff) {  // a leaf emits in its own slot; the entry is dead
+                    const unsigned long long r = n < 2u ? (unsigned long long)n : fib_leaf(n);
+                    c.result[s] = r;
+                    c.code[s] = 0u;
+                    if (s < sh.cap) {
+                        sh.res[s] = r;
+                        sh.code[s] = 0u;
+                    }
+                } else {
+                    fm |= 1u << j;
+                }
+            } else {  // not produced in a fresh range: run it as the general path would
+                Plan p;
+                p.s = s;
+                p.t = t;
+                p.n = 0u;
+                p.m = 0u;
+                plan_task<PM_FIB, merge_tile(BS)>(c, c.rp, p, cen, e, x[j], 0u, c.link[s]);
+                if (s < sh.cap) {  // this thread's own writes, read back
+                    sh.code[s] = c.code[s];
+                    sh.res[s] = c.result[s];
+                }
+            }
+        }
+        // forking tasks per (row, warp): one ballot per row, the warp counts in the shared union, one barrier,
+        // then every warp scans a row's warp counts with shuffles; rows past the range are skipped
+        constexpr int NW = BS / 32;
+        const uint32_t lane = tid & 31u, wid = tid >> 5, lt = (1u << lane) - 1u;
+        const uint32_t nrow = (hi - lo + (uint32_t)BS - 1u) / (uint32_t)BS;  // block-uniform, at most R
+        uint32_t *wc = reinterpret_cast<uint32_t *>(&sm.u);  // [R][NW]
+        uint32_t m[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            m[j] = 0u;
+            if ((uint32_t)j < nrow) {
+                m[j] = __ballot_sync(0xffffffffu, (fm >> j) & 1u);
+                if (lane == (uint32_t)j) wc[j * NW + wid] = (uint32_t)__popc(m[j]);
+            }
+        }
+        __syncthreads();
+        uint32_t pre[R], tot[R], total = 0u;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            pre[j] = tot[j] = 0u;
+            if ((uint32_t)j < nrow) {
+                const uint32_t q = lane < (uint32_t)NW ? wc[j * NW + lane] : 0u, inc = warp_incl_u32(q);
+                tot[j] = __shfl_sync(0xffffffffu, inc, NW - 1);
+                pre[j] = __shfl_sync(0xffffffffu, inc - q, (int)wid);
+                total += 2u * tot[j];
+            }
+        }
+        const bool over = (unsigned long long)base + total > c.cap;
+        if (over && tid == 0) set_err(ctl, TREES_ERR_CAPACITY, e);
+        if (!over && fm) {
+            const uint32_t fe = enc(cen + 1u, TREES_TASK_FIB), fj = enc(cen, TREES_TASK_FIB_SUM);
+            uint32_t rbase = base;  // children of row j start after those of rows 0..j-1
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const uint32_t child = rbase + 2u * (pre[j] + (uint32_t)__popc(m[j] & lt));
+                rbase += 2u * tot[j];
+                if (!((fm >> j) & 1u)) continue;
+                const uint32_t s = lo + (uint32_t)j * BS + tid, n = x[j];
+                c.code[child] = fe;
+                c.a0[child] = n - 1u;
+                c.code[child + 1] = fe;
+                c.a0[child + 1] = n - 2u;
+                c.link[s] = child;
+                c.code[s] = fj;
+                if (child < sh.cap) {
+                    sh.code[child] = fe;
+                    sh.a0[child] = n - 1u;
+                }
+                if (child + 1u < sh.cap) {
+                    sh.code[child + 1] = fe;
+                    sh.a0[child + 1] = n - 2u;
+                }
+                if (s < sh.cap) {
+                    sh.link[s] = child;
+                    sh.code[s] = fj;
+                }
+                acc.joins++;
+            }
+            out.joined = true;
+        }
+        if (tid == 0) {  // every thread has read sh_hi before the count's barrier
+            uint32_t h = hv;
+            if (fill) h = hi < sh.cap ? hi : sh.cap;
+            if (!over && total && base == h) h = base + total < sh.cap ? base + total : sh.cap;
+            sh_hi = h;
+        }
+        out.forks = total;
+        out.over = over;
+        return out;
+    }
+    // a join range: sums only (fib's continuations never fork)
+    unsigned long long r0[R], r1[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        r0[j] = r1[j] = 0ull;
+        if (task_type(cd[j], cen) == TREES_TASK_FIB_SUM) {
+            const uint32_t lk = x[j];
+            r0[j] = lk < hv ? sh.res[lk] : c.result[lk];
+            r1[j] = lk + 1u < hv ? sh.res[lk + 1] : c.result[lk + 1];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const uint32_t s = lo + (uint32_t)j * BS + tid, t = task_type(cd[j], cen);
+        if (!t) continue;
+        acc.valid++;
+        if (t == TREES_TASK_FIB_SUM) {
+            const unsigned long long v = r0[j] + r1[j];
+            c.result[s] = v;
+            c.code[s] = 0u;
+            if (s < sh.cap) {
+                sh.res[s] = v;
+                sh.code[s] = 0u;
+            }
+        } else {  // not produced in a join range; run it as the general path would
+            Plan p;
+            p.s = s;
+            p.t = t;
+            p.n = 0u;
+            p.m = 0u;
+            plan_task<PM_FIB, merge_tile(BS)>(c, c.rp, p, cen, e, c.a0[s], 0u, x[j]);
+            if (s < sh.cap) {
+                sh.code[s] = c.code[s];
+                sh.res[s] = c.result[s];
+            }
+        }
+    }
+    return out;
 }
 
 // Block 0's run of solo epochs, starting at epoch e with its range popped.
@@ -208,35 +431,41 @@ __device__ __forceinline__ bool solo_range(const Conf &c, uint32_t lo, uint32_t 
 // state (stack, nextFreeCore, popped range, stop) is then published for the
 // other blocks.
 template <int BS, int TPT, uint32_t PM>
-__device__ uint32_t solo_epochs(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t e, Acc &acc, SchedState &st) {
+__device__ uint32_t solo_epochs(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t e, Acc &acc, SchedState &st,
+                                uint32_t *ring) {
     if (threadIdx.x == 0) st.t_solo = globaltimer();
     for (;;) {
         const uint32_t cen = sm.cen, lo = sm.lo, hi = sm.hi, base = sm.base, ep = e % 3u;
         const int mode = sm.rjoin ? LOAD_JOIN : LOAD_FRESH;
         const uint32_t v0 = acc.valid;
         TileOut o = {0u, false, false};
-        // the range's tiles in order, each forking after the children of the ones before it
-        TileLoad<TPT> cur, nxt;
-        if (lo < hi) tile_load<BS, TPT, PM>(c, lo, hi, mode, cur);
-        int par = 0;
-        for (uint32_t t0 = lo; t0 < hi; t0 += (uint32_t)(BS * TPT)) {
-            const bool more = t0 + (uint32_t)(BS * TPT) < hi;
-            if (more) tile_load<BS, TPT, PM>(c, t0 + (uint32_t)(BS * TPT), hi, mode, nxt);
-            if constexpr (joins_never_fork<PM>()) {
-                if (mode == LOAD_JOIN) {  // continuations only: no scan, no allocation
-                    join_tile<BS, TPT, PM>(c, sm, t0, cen, e, acc, par, cur, false, nullptr);
-                    if (more) cur = nxt;
-                    par ^= 1;
-                    continue;
+        if constexpr (PM == PM_FIB) {
+            o = fib_solo_epoch<BS, TPT>(c, ctl, sm, fib_shadow<BS, TPT, PM>(ring), st.sh_hi, lo, hi, cen, base, e,
+                                        mode, acc);
+        } else {
+            // the range's tiles in order, each forking after the children of the ones before it
+            TileLoad<TPT> cur, nxt;
+            if (lo < hi) tile_load<BS, TPT, PM>(c, lo, hi, mode, cur);
+            int par = 0;
+            for (uint32_t t0 = lo; t0 < hi; t0 += (uint32_t)(BS * TPT)) {
+                const bool more = t0 + (uint32_t)(BS * TPT) < hi;
+                if (more) tile_load<BS, TPT, PM>(c, t0 + (uint32_t)(BS * TPT), hi, mode, nxt);
+                if constexpr (joins_never_fork<PM>()) {
+                    if (mode == LOAD_JOIN) {  // continuations only: no scan, no allocation
+                        join_tile<BS, TPT, PM>(c, sm, t0, cen, e, acc, par, cur, false, nullptr);
+                        if (more) cur = nxt;
+                        par ^= 1;
+                        continue;
+                    }
                 }
+                const TileOut t = epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode,
+                                                          cur, true, o.forks);
+                o.forks += t.forks;
+                o.joined |= t.joined;
+                o.over |= t.over;
+                if (more) cur = nxt;
+                par ^= 1;
             }
-            const TileOut t = epoch_tile<BS, TPT, PM>(c, ctl, sm, t0, hi, cen, base, ep, e, acc, par, mode, cur,
-                                                      true, o.forks);
-            o.forks += t.forks;
-            o.joined |= t.joined;
-            o.over |= t.over;
-            if (more) cur = nxt;
-            par ^= 1;
         }
         trace_valid_add<BS>(c, e, acc.valid - v0, sm);
         // the whole epoch is this block's tile: its fork total and join flag close the epoch
@@ -299,7 +528,7 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
     extern __shared__ __align__(16) uint32_t ring[];  // ring_bytes<BS, TPT, PM>() of dynamic shared memory
     Acc acc = {0u, 0u, 0u};
     if (threadIdx.x == 0) {
-        st = SchedState{0ull, 1u, 0u, 0ull, 0ull, 0ull, 0ull, 0ull};
+        st = SchedState{0ull, 1u, 0u, 0ull, 0ull, 0ull, 0ull, 0ull, 0u};
         sm.sp = 1;
         sm.stk[0] = Range{0u, 0u, 1u, 0u};
         sm.next = 1u;
@@ -317,7 +546,7 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
         if constexpr ((PM & PM_MAPS) == 0u) {
             if (solo_range<BS, TPT, PM>(c, sm.lo, sm.hi)) {
                 if (blockIdx.x == 0) {
-                    const uint32_t ne = solo_epochs<BS, TPT, PM>(c, ctl, sm, e, acc, st);
+                    const uint32_t ne = solo_epochs<BS, TPT, PM>(c, ctl, sm, e, acc, st, ring);
                     if (threadIdx.x == 0) sm_e = ne;
                 }
                 if (!grid_sync_ep<BS>(ctl, &st.bar, c.timeout_ns, sm, e % 3u)) break;
@@ -333,6 +562,9 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
         }
         const uint32_t cen = sm.cen, lo = sm.lo, hi = sm.hi, base = sm.base, ep = e % 3u;
         const int mode = sm.rjoin ? LOAD_JOIN : LOAD_FRESH;
+        if constexpr (PM == PM_FIB) {  // this grid epoch writes slots from lo up: the shadow ends below them
+            if (threadIdx.x == 0 && st.sh_hi > lo) st.sh_hi = lo;
+        }
         // Phase 2: every entry of [lo, hi)
         const uint32_t v0 = acc.valid;
         // tiles grid-stride over [lo, hi); the next tile's columns load while this one runs
