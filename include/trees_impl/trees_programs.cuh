@@ -853,15 +853,21 @@ __device__ __forceinline__ void join_tile(const Conf &c, Smem<BS> &sm, unsigned 
 // passes with one slot reservation between them:
 //  1. count: every warp streams through the chunk's tiles on its own (no
 //     block barrier): it loads code and n, lets the leaves emit in their own
-//     slot (Sec. 4.3.2), and records with one ballot per slot row which lanes
-//     fork (fib forks exactly two children, so a warp's prefix is twice a
-//     popcount), plus each internal task's n, in shared memory;
+//     slot (Sec. 4.3.2), rewrites the internal tasks as their continuations
+//     (code, and a zero result the join overwrites, so the code and result
+//     rows are written whole in this pass), and records with one ballot per
+//     slot row which lanes fork (fib forks exactly two children, so a warp's
+//     prefix is twice a popcount), plus each internal task's n, in shared
+//     memory;
 //  2. one block scan over the per-warp fork counts and one atomic on
 //     nextFreeCore for the whole chunk (Sec. 5.2.3's cooperative allocation:
 //     a scan, then a single atomic for the group);
 //  3. write: every warp writes its internal tasks' children (k-major, so a
-//     warp's children are contiguous) and rewrites those tasks as their join
-//     continuations, from shared memory alone (no loads, no block barrier).
+//     warp's children are contiguous) and the link row of its slots (zero for
+//     the leaves), from shared memory alone (no loads, no block barrier).
+// A row of a column written partly in one pass and partly much later leaves
+// partly written 32-byte sectors in L2; written whole (or by both passes of
+// one chunk) it does not: fib(34) at 512 x 2 went 0.427 -> 0.418 ms.
 // Returns whether this thread's tasks joined.
 constexpr uint32_t FIB_CHUNK_SLOTS = 16384;  // slots per chunk: their n fit a 16 KB byte array
 
@@ -947,7 +953,9 @@ __device__ __forceinline__ bool fib_fresh_tiles(const Conf &c, Ctl *ctl, Smem<BS
                         if (n < 2u || n <= c.rp.cutoff) {  // a leaf emits: fib(n) in its own slot, entry dead
                             c.result[s] = n < 2u ? (unsigned long long)n : fib_leaf(n);
                             c.code[s] = 0u;
-                        } else {
+                        } else {  // its continuation (its result is written by the join)
+                            c.result[s] = 0ull;
+                            c.code[s] = fj;
                             fork = true;
                         }
                     } else if (t) {  // not produced in a fresh range; run it as the general path would
@@ -1002,9 +1010,13 @@ __device__ __forceinline__ bool fib_fresh_tiles(const Conf &c, Ctl *ctl, Smem<BS
                 for (int k = 0; k < TPT; ++k) {
                     const uint32_t i = (j * TPT + k) * NW + wid;
                     const uint32_t m = fc.mask[i];
-                    if (!((m >> lane) & 1u)) continue;
-                    const uint32_t s = (uint32_t)(t0 + (unsigned long long)j * step + (unsigned long long)k * BS +
-                                                  threadIdx.x);
+                    const unsigned long long sl = t0 + (unsigned long long)j * step + (unsigned long long)k * BS +
+                                                  threadIdx.x;
+                    if (!((m >> lane) & 1u)) {
+                        if (sl < hi) c.link[(uint32_t)sl] = 0u;  // the link row is written whole
+                        continue;
+                    }
+                    const uint32_t s = (uint32_t)sl;
                     const uint32_t n = fc.n[j * TILE + k * BS + threadIdx.x];
                     const uint32_t child = cbase + fc.off[i] + 2u * (uint32_t)__popc(m & lt);
                     c.code[child] = fe;
@@ -1012,7 +1024,6 @@ __device__ __forceinline__ bool fib_fresh_tiles(const Conf &c, Ctl *ctl, Smem<BS
                     c.code[child + 1] = fe;
                     c.a0[child + 1] = n - 2u;
                     c.link[s] = child;
-                    c.code[s] = fj;
                     acc.joins++;
                     joined = true;
                 }
