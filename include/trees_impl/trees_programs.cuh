@@ -1110,8 +1110,13 @@ __device__ __forceinline__ void fib_join_tiles(const Conf &c, unsigned long long
             if (!t) continue;
             acc.valid++;
             if (t == TREES_TASK_FIB_SUM) {
+                // The sum schedules no join, so its range is not pushed again and no later epoch
+                // reaches this entry at its epoch number (a range is revisited only when one of
+                // its tasks joins; fresh ranges are written before they are read): the entry is
+                // already dead, and marking it invalid (as Sec. 5.3's finished tasks are) is a
+                // store per sum that changes nothing; leaving it out measured 0.4116 -> 0.4035 ms
+                // per fib(34).
                 c.result[s] = r[2 * k * BS] + r[2 * k * BS + 1];
-                c.code[s] = 0u;
             } else {  // not produced in a join range; run it as the general path would
                 Plan p;
                 p.s = s;
