@@ -210,7 +210,8 @@ struct Smem {
     unsigned long long w64a[NW];
     unsigned long long w64b[NW];
     unsigned int flags;
-    unsigned int bc32[4];
+    unsigned int bc32[8];                 // broadcast words (two per block part in the expansion tiles)
+    unsigned int pcnt[4];                 // BFS: claims waiting in each block part's buffer (claim_flush)
     unsigned long long bc64[4];
     int bar_ok;
     unsigned long long mbar[merge_nst(BS)];  // mbarriers of the merge stage buffers

@@ -1725,6 +1725,48 @@ __device__ __forceinline__ uint32_t load_tile_descriptors(const Conf &c, Smem<BS
     return nloc;
 }
 
+// The next tile's descriptors read ahead into registers (BFS): issued while
+// the current tile's chain runs, stored into the part's records once every
+// thread of the part has finished searching the current ones, so the next
+// tile starts without its two dependent round trips (the tile's first
+// descriptor, then the descriptors).  KD: the most a thread holds.
+template <int BS>
+struct DescAhead {
+    static constexpr uint32_t HB = BS / EXPAND_PARTS(BS), KD = (EXPAND_TILE + 2u + HB - 1u) / HB;
+    uint32_t n;  // descriptors of the next tile (0: no next tile)
+    uint32_t b[KD], v[KD];
+};
+
+template <int BS>
+__device__ __forceinline__ void desc_ahead_issue(const Conf &c, uint32_t tn, uint32_t nd, uint32_t nt, uint32_t lt,
+                                                 DescAhead<BS> &A) {
+    A.n = 0u;
+    if (tn < nt) {
+        const uint32_t df = c.me_tfd[tn], dl = tn + 1u < nt ? c.me_tfd[tn + 1u] : nd - 1u;
+        A.n = dl - df + 1u;
+#pragma unroll
+        for (uint32_t i = 0; i < DescAhead<BS>::KD; ++i) {
+            const uint32_t k = lt + i * DescAhead<BS>::HB;
+            if (k < A.n) {
+                A.b[i] = c.me_base[df + k];
+                A.v[i] = c.me_v[df + k];
+            }
+        }
+    }
+}
+
+template <int BS>
+__device__ __forceinline__ void desc_ahead_store(Smem<BS> &sm, uint32_t h, uint32_t lt, const DescAhead<BS> &A) {
+#pragma unroll
+    for (uint32_t i = 0; i < DescAhead<BS>::KD; ++i) {
+        const uint32_t k = lt + i * DescAhead<BS>::HB;
+        if (k < A.n) {
+            sm.u.ex.base[h][k] = A.b[i];
+            sm.u.ex.v[h][k] = A.v[i];
+        }
+    }
+}
+
 // Element g of the tile: its descriptor (load-balanced search over the
 // part's records in shared memory).
 template <int BS>
@@ -1755,18 +1797,58 @@ __device__ __forceinline__ bool part_reserve(const Conf &c, Ctl *ctl, Smem<BS> &
     return !sm.bc32[2u * h + 1u];
 }
 
-// One BFS expansion tile (EXPAND_TILE consecutive adjacency entries of the
-// epoch's frontier) on part h of the block.  Each entry's vertex is found by
-// a binary search over the tile's descriptors in shared memory
-// (load-balanced search); an unvisited neighbour is claimed with a CAS on its
-// level and forked as a visit task.
+// BFS claim buffers: the vertices an expansion tile claims wait in its block
+// part's buffer (the space of the distance records, which BFS does not use)
+// and are forked in bulk, one reservation on nextFreeCore for a buffer of
+// several tiles' claims (Sec. 5.2.3's single atomic for a group of forks,
+// the group made larger): a tile claims a dozen vertices on average, so a
+// reservation (and the scan that placed the claims) per tile cost more than
+// the claims' stores.  The fork range stays gap-free: each flush reserves
+// exactly its claims.
+constexpr uint32_t CLAIM_CAP = 2u * (EXPAND_TILE + 2u);  // u32 entries: the d records of one part
+
 template <int BS>
-__device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, uint32_t nd, uint32_t ne, uint32_t nt,
-                            uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, uint32_t h) {
+__device__ __forceinline__ uint32_t *claim_buf(Smem<BS> &sm, uint32_t h) {
+    static_assert(sizeof(sm.u.ex.d[0]) >= CLAIM_CAP * sizeof(uint32_t), "a part's buffer fits its d records");
+    return reinterpret_cast<uint32_t *>(sm.u.ex.d[h]);
+}
+
+// Forks the claims in part h's buffer (every thread of the part calls it,
+// after a barrier of the part that follows the appends): one reservation,
+// then the visit tasks, then the buffer is empty again.  Ends with a barrier
+// of the part.
+template <int BS>
+__device__ __forceinline__ void claim_flush(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t h, uint32_t lt,
+                                            uint32_t cen, uint32_t base, uint32_t ep, uint32_t e) {
+    constexpr uint32_t HB = BS / EXPAND_PARTS(BS);
+    const uint32_t n = sm.pcnt[h];
+    uint32_t b;
+    if (n && part_reserve<BS>(c, ctl, sm, h, lt, n, base, ep, e, &b)) {
+        const uint32_t code = enc(cen + 1u, TREES_TASK_BFS_VISIT);
+        const uint32_t *cb = claim_buf<BS>(sm, h);
+        for (uint32_t i = lt; i < n; i += HB) {
+            c.code[base + b + i] = code;
+            c.a0[base + b + i] = cb[i];
+        }
+    }
+    if (lt == 0u) sm.pcnt[h] = 0u;  // every thread read the count before part_reserve's barrier
+    bar_part<BS>(h);
+}
+
+// One BFS expansion tile (EXPAND_TILE consecutive adjacency entries of the
+// epoch's frontier) on part h of the block, whose nloc descriptors are in the
+// part's records.  Each entry's vertex is found by a binary search over the
+// tile's descriptors in shared memory (load-balanced search); an unvisited
+// neighbour is claimed with a CAS on its level and forked as a visit task.
+// The descriptors of the part's next tile tn are read meanwhile and are in
+// the records when it returns; it returns their count.
+template <int BS>
+__device__ uint32_t expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, uint32_t tn, uint32_t nloc,
+                                uint32_t nd, uint32_t ne, uint32_t nt, uint32_t cen, uint32_t base, uint32_t ep,
+                                uint32_t e, uint32_t h) {
     constexpr uint32_t HB = BS / EXPAND_PARTS(BS), EPT = EXPAND_TILE / HB;
     const uint32_t lt = threadIdx.x - h * HB;
     const uint32_t g0 = t * EXPAND_TILE, g1 = min(g0 + EXPAND_TILE, ne);
-    const uint32_t nloc = load_tile_descriptors<BS, false>(c, sm, t, nd, nt, h, lt);
     // stage 1: every element's adjacency index (load-balanced search in shared memory)
     uint32_t ed[EPT];
 #pragma unroll
@@ -1778,10 +1860,13 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
             ed[j] = sm.u.ex.v[h][k] + (g - sm.u.ex.base[h][k]);
         }
     }
-    // stage 2: all neighbour ids, then all their levels, in flight together
+    // stage 2: all neighbour ids, then all their levels, in flight together (and the next tile's
+    // descriptors behind them)
     int32_t uu[EPT], lv[EPT];
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j) uu[j] = ed[j] != 0xFFFFFFFFu ? __ldg(c.rp.col + ed[j]) : -1;
+    DescAhead<BS> A;
+    desc_ahead_issue<BS>(c, tn, nd, nt, lt, A);
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j) lv[j] = uu[j] >= 0 ? c.rp.level[uu[j]] : 0;
     // stage 3: claim unvisited neighbours (the CAS decides between competing visits); all of the
@@ -1794,22 +1879,20 @@ __device__ void expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, u
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j)
         if (uu[j] >= 0 && lv[j] < 0 && prev[j] == -1) cmask |= 1u << j;
-    uint32_t ftot;
-    const uint32_t off = part_scan_u32<BS>((uint32_t)__popc(cmask), h, &ftot, sm);
-    uint32_t b;
-    if (ftot && part_reserve<BS>(c, ctl, sm, h, lt, ftot, base, ep, e, &b)) {
-        const uint32_t code = enc(cen + 1u, TREES_TASK_BFS_VISIT);
-        uint32_t slot = base + b + off;
+    // the claimed vertices go to the part's buffer: one shared-memory atomic per warp, no barrier
+    const uint32_t lane = threadIdx.x & 31u, nc = (uint32_t)__popc(cmask), inc = warp_incl_u32(nc);
+    uint32_t wb = 0u;
+    if (lane == 31u && inc) wb = atomicAdd(&sm.pcnt[h], inc);
+    uint32_t pos = __shfl_sync(0xffffffffu, wb, 31) + inc - nc;
+    uint32_t *cb = claim_buf<BS>(sm, h);
 #pragma unroll
-        for (uint32_t j = 0; j < EPT; ++j) {
-            if ((cmask >> j) & 1u) {
-                c.code[slot] = code;
-                c.a0[slot] = (uint32_t)uu[j];
-                ++slot;
-            }
-        }
-    }
-    bar_part<BS>(h);  // the part's records are its next tile's
+    for (uint32_t j = 0; j < EPT; ++j)
+        if ((cmask >> j) & 1u) cb[pos++] = (uint32_t)uu[j];
+    bar_part<BS>(h);  // every thread of the part is past its search and its appends
+    desc_ahead_store<BS>(sm, h, lt, A);  // the records are free
+    if (sm.pcnt[h] > CLAIM_CAP - EXPAND_TILE) claim_flush<BS>(c, ctl, sm, h, lt, cen, base, ep, e);  // part-uniform
+    bar_part<BS>(h);  // the next tile's records are in place
+    return A.n;
 }
 
 // One SSSP relaxation tile (Sec. 6.3's worklist relaxation as a map) on part
@@ -1986,9 +2069,20 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
             const bool sssp = (PM & PM_BFS) == 0u || ((PM & PM_SSSP) != 0u && c.rp.program == TREES_PROG_SSSP);
             constexpr uint32_t P = EXPAND_PARTS(BS);
             const uint32_t h = threadIdx.x / (uint32_t)(BS / P);  // the parts take interleaved tiles
-            for (uint32_t t = P * blockIdx.x + h; t < nt2; t += P * gridDim.x) {
-                if (sssp) relax_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e, h);
-                else expand_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e, h);
+            const uint32_t lt = threadIdx.x - h * (uint32_t)(BS / P);
+            if (sssp) {
+                for (uint32_t t = P * blockIdx.x + h; t < nt2; t += P * gridDim.x)
+                    relax_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e, h);
+            } else {
+                uint32_t t = P * blockIdx.x + h;
+                if (t < nt2) {
+                    if (lt == 0u) sm.pcnt[h] = 0u;  // load_tile_descriptors ends with a barrier of the part
+                    uint32_t nloc = load_tile_descriptors<BS, false>(c, sm, t, nd2, nt2, h, lt);
+                    for (; t < nt2; t += P * gridDim.x)
+                        nloc = expand_tile<BS>(c, ctl, sm, t, t + P * gridDim.x, nloc, nd2, ne2, nt2, cen, base, ep,
+                                               e, h);
+                    claim_flush<BS>(c, ctl, sm, h, lt, cen, base, ep, e);  // the claims left in the buffer
+                }
             }
         }
     }
