@@ -120,7 +120,47 @@ __host__ __device__ constexpr size_t ring_bytes() {
 }
 
 // Dynamic shared memory bytes k_persistent<bs, tpt, program mask pm> is launched with.
+// SSSP's persistent kernels keep each block part's claim buffer (relax_tile)
+// in dynamic shared memory: CLAIM_CAP entries a part when that fits beside
+// the static shared memory at the kernel's residency, else none (the
+// per-tile reservation path).  A partial buffer is not worth it: at 256
+// threads it would take the SM's shared memory to 232 KB of its 256 KB and
+// leave the L1 cache the tiles' gathers use 24 KB (SSSP R-MAT 22 at 256 x 2:
+// 2.80 -> 4.65 ms with 636-entry buffers).
+template <int BS, int TPT>
+__host__ __device__ constexpr uint32_t sssp_claim_cap() {
+    return SMEM_PER_SM / persistent_min_blocks(BS, PM_SSSP, TPT) - SMEM_RESERVED_PER_BLOCK -
+                       ((int)sizeof(Smem<BS>) + 256) >=
+                   (int)(4u * EXPAND_PARTS(BS) * CLAIM_CAP)
+               ? CLAIM_CAP
+               : 0u;
+}
+
+template <int BS, int TPT, uint32_t PM>
+__host__ __device__ constexpr size_t dyn_smem_bytes() {
+    return PM == PM_FIB ? ring_bytes<BS, TPT, PM>()
+           : PM == PM_SSSP ? (size_t)4u * EXPAND_PARTS(BS) * sssp_claim_cap<BS, TPT>()
+                           : 0u;
+}
+
 inline size_t persistent_smem_bytes(uint32_t pm, int bs, int tpt) {
+    if (pm == PM_SSSP) {
+        switch (bs * 10 + tpt) {
+        case 1281: return dyn_smem_bytes<128, 1, PM_SSSP>();
+        case 1282: return dyn_smem_bytes<128, 2, PM_SSSP>();
+        case 1284: return dyn_smem_bytes<128, 4, PM_SSSP>();
+        case 2561: return dyn_smem_bytes<256, 1, PM_SSSP>();
+        case 2562: return dyn_smem_bytes<256, 2, PM_SSSP>();
+        case 2564: return dyn_smem_bytes<256, 4, PM_SSSP>();
+        case 5121: return dyn_smem_bytes<512, 1, PM_SSSP>();
+        case 5122: return dyn_smem_bytes<512, 2, PM_SSSP>();
+        case 5124: return dyn_smem_bytes<512, 4, PM_SSSP>();
+        case 10241: return dyn_smem_bytes<1024, 1, PM_SSSP>();
+        case 10242: return dyn_smem_bytes<1024, 2, PM_SSSP>();
+        case 10244: return dyn_smem_bytes<1024, 4, PM_SSSP>();
+        default: return 0;
+        }
+    }
     if (pm != PM_FIB) return 0;
     switch (bs * 10 + tpt) {
     case 1281: return ring_bytes<128, 1, PM_FIB>();
@@ -525,7 +565,7 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
     __shared__ Smem<BS> sm;
     __shared__ uint32_t sm_e;
     __shared__ SchedState st;
-    extern __shared__ __align__(16) uint32_t ring[];  // ring_bytes<BS, TPT, PM>() of dynamic shared memory
+    extern __shared__ __align__(16) uint32_t ring[];  // dyn_smem_bytes<BS, TPT, PM>() of dynamic shared memory
     Acc acc = {0u, 0u, 0u};
     if (threadIdx.x == 0) {
         st = SchedState{0ull, 1u, 0u, 0ull, 0ull, 0ull, 0ull, 0ull, 0u};
@@ -636,7 +676,12 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
                     if (stamp) st.t_pt = st.t_mp = globaltimer();
                 }
             }
-            map_phase<BS, PM, UP>(c, ctl, sm, ep, e, cen, base, mt, me);
+            if constexpr (PM == PM_SSSP) {  // the parts' claim buffers are in the dynamic shared memory
+                map_phase<BS, PM, UP>(c, ctl, sm, ep, e, cen, base, mt, me, nullptr, 0u, ring,
+                                      sssp_claim_cap<BS, TPT>());
+            } else {
+                map_phase<BS, PM, UP>(c, ctl, sm, ep, e, cen, base, mt, me);
+            }
             if (!grid_sync_ep<BS>(ctl, &st.bar, c.timeout_ns, sm, ep)) break;
             if (stamp) st.t_mp = globaltimer();
         }

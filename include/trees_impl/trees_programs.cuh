@@ -1813,19 +1813,17 @@ __device__ __forceinline__ uint32_t *claim_buf(Smem<BS> &sm, uint32_t h) {
     return reinterpret_cast<uint32_t *>(sm.u.ex.d[h]);
 }
 
-// Forks the claims in part h's buffer (every thread of the part calls it,
-// after a barrier of the part that follows the appends): one reservation,
-// then the visit tasks, then the buffer is empty again.  Ends with a barrier
-// of the part.
+// Forks the claims in part h's buffer cb as tasks `code` (every thread of
+// the part calls it, after a barrier of the part that follows the appends):
+// one reservation, then the tasks, then the buffer is empty again.  Ends with
+// a barrier of the part.
 template <int BS>
-__device__ __forceinline__ void claim_flush(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t h, uint32_t lt,
-                                            uint32_t cen, uint32_t base, uint32_t ep, uint32_t e) {
+__device__ __forceinline__ void claim_flush(const Conf &c, Ctl *ctl, Smem<BS> &sm, const uint32_t *cb, uint32_t h,
+                                            uint32_t lt, uint32_t code, uint32_t base, uint32_t ep, uint32_t e) {
     constexpr uint32_t HB = BS / EXPAND_PARTS(BS);
     const uint32_t n = sm.pcnt[h];
     uint32_t b;
     if (n && part_reserve<BS>(c, ctl, sm, h, lt, n, base, ep, e, &b)) {
-        const uint32_t code = enc(cen + 1u, TREES_TASK_BFS_VISIT);
-        const uint32_t *cb = claim_buf<BS>(sm, h);
         for (uint32_t i = lt; i < n; i += HB) {
             c.code[base + b + i] = code;
             c.a0[base + b + i] = cb[i];
@@ -1833,6 +1831,20 @@ __device__ __forceinline__ void claim_flush(const Conf &c, Ctl *ctl, Smem<BS> &s
     }
     if (lt == 0u) sm.pcnt[h] = 0u;  // every thread read the count before part_reserve's barrier
     bar_part<BS>(h);
+}
+
+// Appends this thread's claimed vertices (bits of cmask over uu) to part h's
+// buffer: one shared-memory atomic per warp, no barrier.
+template <int BS, int EPT>
+__device__ __forceinline__ void claim_append(Smem<BS> &sm, uint32_t *cb, uint32_t h, uint32_t cmask,
+                                             const int32_t (&uu)[EPT]) {
+    const uint32_t lane = threadIdx.x & 31u, nc = (uint32_t)__popc(cmask), inc = warp_incl_u32(nc);
+    uint32_t wb = 0u;
+    if (lane == 31u && inc) wb = atomicAdd(&sm.pcnt[h], inc);
+    uint32_t pos = __shfl_sync(0xffffffffu, wb, 31) + inc - nc;
+#pragma unroll
+    for (int j = 0; j < EPT; ++j)
+        if ((cmask >> j) & 1u) cb[pos++] = (uint32_t)uu[j];
 }
 
 // One BFS expansion tile (EXPAND_TILE consecutive adjacency entries of the
@@ -1879,18 +1891,12 @@ __device__ uint32_t expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t 
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j)
         if (uu[j] >= 0 && lv[j] < 0 && prev[j] == -1) cmask |= 1u << j;
-    // the claimed vertices go to the part's buffer: one shared-memory atomic per warp, no barrier
-    const uint32_t lane = threadIdx.x & 31u, nc = (uint32_t)__popc(cmask), inc = warp_incl_u32(nc);
-    uint32_t wb = 0u;
-    if (lane == 31u && inc) wb = atomicAdd(&sm.pcnt[h], inc);
-    uint32_t pos = __shfl_sync(0xffffffffu, wb, 31) + inc - nc;
-    uint32_t *cb = claim_buf<BS>(sm, h);
-#pragma unroll
-    for (uint32_t j = 0; j < EPT; ++j)
-        if ((cmask >> j) & 1u) cb[pos++] = (uint32_t)uu[j];
+    // the claimed vertices go to the part's buffer
+    claim_append<BS, (int)EPT>(sm, claim_buf<BS>(sm, h), h, cmask, uu);
     bar_part<BS>(h);  // every thread of the part is past its search and its appends
     desc_ahead_store<BS>(sm, h, lt, A);  // the records are free
-    if (sm.pcnt[h] > CLAIM_CAP - EXPAND_TILE) claim_flush<BS>(c, ctl, sm, h, lt, cen, base, ep, e);  // part-uniform
+    if (sm.pcnt[h] > CLAIM_CAP - EXPAND_TILE)  // part-uniform
+        claim_flush<BS>(c, ctl, sm, claim_buf<BS>(sm, h), h, lt, enc(cen + 1u, TREES_TASK_BFS_VISIT), base, ep, e);
     bar_part<BS>(h);  // the next tile's records are in place
     return A.n;
 }
@@ -1909,7 +1915,8 @@ __device__ uint32_t expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t 
 // is still the one every edge of v used in the previous epoch ends at once.
 template <int BS>
 __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, uint32_t nd, uint32_t ne, uint32_t nt,
-                           uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, uint32_t h) {
+                           uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, uint32_t h, uint32_t *cb,
+                           uint32_t cap) {
     constexpr uint32_t HB = BS / EXPAND_PARTS(BS), EPT = EXPAND_TILE / HB;
     const uint32_t lt = threadIdx.x - h * HB;
     const uint32_t g0 = t * EXPAND_TILE, g1 = min(g0 + EXPAND_TILE, ne);
@@ -1957,8 +1964,9 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j)
         if (prev[j] < cen + 1u) cmask |= 1u << j;
-    uint32_t ftot;
-    const uint32_t off = part_scan_u32<BS>((uint32_t)__popc(cmask), h, &ftot, sm);
+    if (cb) claim_append<BS, (int)EPT>(sm, cb, h, cmask, uu);  // forked in bulk (claim_flush)
+    uint32_t ftot = 0u, off = 0u;
+    if (!cb) off = part_scan_u32<BS>((uint32_t)__popc(cmask), h, &ftot, sm);
     uint32_t b;
     if (ftot && part_reserve<BS>(c, ctl, sm, h, lt, ftot, base, ep, e, &b)) {
         const uint32_t code = enc(cen + 1u, TREES_TASK_SSSP_RELAX);
@@ -1980,6 +1988,8 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
             atomicMax(c.rp.used + c.me_src[dfirst + k], (unsigned long long)(cen + 1u) << SSSP_USED_SHIFT | d);
     }
     bar_part<BS>(h);  // the part's records are its next tile's
+    if (cb && sm.pcnt[h] > cap - EXPAND_TILE)  // part-uniform
+        claim_flush<BS>(c, ctl, sm, cb, h, lt, enc(cen + 1u, TREES_TASK_SSSP_RELAX), base, ep, e);
 }
 
 // The combine maps of one FFT epoch as one flat array of butterflies.  The
@@ -2026,7 +2036,7 @@ __device__ void fft_combine_map(const Conf &c, uint32_t nd, uint32_t ne) {
 template <int BS, uint32_t PM, typename UP = NoUserProgram>
 __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, uint32_t e, uint32_t cen, uint32_t base,
                           unsigned long long mt, unsigned long long me, const RunParams *job_params = nullptr,
-                          uint32_t job_stride = 0) {
+                          uint32_t job_stride = 0, uint32_t *claims = nullptr, uint32_t claim_cap = 0u) {
     const uint32_t nt1 = (uint32_t)(mt & CTR_LOW_MASK), nd1 = (uint32_t)(mt >> 40);
     const uint32_t nd2 = (uint32_t)(me >> 40), ne2 = (uint32_t)(me & CTR_LOW_MASK);
     const uint32_t nt2 = (ne2 + EXPAND_TILE - 1u) / EXPAND_TILE;
@@ -2071,8 +2081,16 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
             const uint32_t h = threadIdx.x / (uint32_t)(BS / P);  // the parts take interleaved tiles
             const uint32_t lt = threadIdx.x - h * (uint32_t)(BS / P);
             if (sssp) {
-                for (uint32_t t = P * blockIdx.x + h; t < nt2; t += P * gridDim.x)
-                    relax_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e, h);
+                // a part's claim buffer: claim_cap entries of the caller's buffer, or none (per-tile forks)
+                uint32_t *cb = claims && claim_cap >= EXPAND_TILE + 32u ? claims + h * claim_cap : nullptr;
+                uint32_t t = P * blockIdx.x + h;
+                if (t < nt2) {
+                    if (cb && lt == 0u) sm.pcnt[h] = 0u;  // the tile's descriptor load ends with a barrier of the part
+                    for (; t < nt2; t += P * gridDim.x)
+                        relax_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e, h, cb, claim_cap);
+                    if (cb)  // the claims left in the buffer
+                        claim_flush<BS>(c, ctl, sm, cb, h, lt, enc(cen + 1u, TREES_TASK_SSSP_RELAX), base, ep, e);
+                }
             } else {
                 uint32_t t = P * blockIdx.x + h;
                 if (t < nt2) {
@@ -2081,7 +2099,8 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
                     for (; t < nt2; t += P * gridDim.x)
                         nloc = expand_tile<BS>(c, ctl, sm, t, t + P * gridDim.x, nloc, nd2, ne2, nt2, cen, base, ep,
                                                e, h);
-                    claim_flush<BS>(c, ctl, sm, h, lt, cen, base, ep, e);  // the claims left in the buffer
+                    claim_flush<BS>(c, ctl, sm, claim_buf<BS>(sm, h), h, lt, enc(cen + 1u, TREES_TASK_BFS_VISIT),
+                                    base, ep, e);  // the claims left in the buffer
                 }
             }
         }
