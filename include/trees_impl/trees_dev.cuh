@@ -38,9 +38,15 @@ __host__ __device__ constexpr uint32_t merge_stage(int bs) { return merge_tile(b
 // Merge tiles staged per block (a ring of TMA buffers): one merging while the
 // next streams in.
 __host__ __device__ constexpr int merge_nst(int) { return 2; }
-constexpr uint32_t EXPAND_TILE = 512;           // adjacency entries of one BFS / SSSP expansion tile (a block part's)
-// Parts of a block that run expansion tiles independently (8 entries per thread per tile).
-#define EXPAND_PARTS(BS) ((BS) >= 256 ? 4u : 2u)
+// Parts of a block that run BFS / SSSP expansion tiles independently, and the
+// adjacency entries of one tile (a part's): blocks of 512 or more threads run
+// eight parts of 256-entry tiles, smaller blocks four (two at 128 threads) of
+// 512 entries; either way a part's threads take 2-8 entries each, and the
+// parts' records fill the same shared union.  Measured (R-MAT 22, one call):
+// 8 parts x 256 at 512 x 2 BFS 0.918 -> 0.844 ms, SSSP 2.49 -> 2.43 ms; at
+// 256 threads 4 parts x 256 were slower (BFS 0.94 -> 0.98 ms).
+#define EXPAND_PARTS(BS) ((BS) >= 512 ? 8u : (BS) >= 256 ? 4u : 2u)
+__host__ __device__ constexpr uint32_t expand_tile_len(int bs) { return bs >= 512 ? 256u : 512u; }
 constexpr uint32_t JR_SLOTS = 1024;             // tile slots whose join operands can be prefetched
 constexpr uint32_t SMP_SHIFT = 6;               // mergesort splitter samples: every 64th key of a run
 constexpr int MCHUNK = 64;                      // merge tiles a block resolves at once
@@ -210,8 +216,8 @@ struct Smem {
     unsigned long long w64a[NW];
     unsigned long long w64b[NW];
     unsigned int flags;
-    unsigned int bc32[8];                 // broadcast words (two per block part in the expansion tiles)
-    unsigned int pcnt[4];                 // BFS: claims waiting in each block part's buffer (claim_flush)
+    unsigned int bc32[16];                // broadcast words (two per block part in the expansion tiles)
+    unsigned int pcnt[8];                 // claims waiting in each block part's buffer (claim_flush)
     unsigned long long bc64[4];
     int bar_ok;
     unsigned long long mbar[merge_nst(BS)];  // mbarriers of the merge stage buffers
@@ -228,9 +234,9 @@ struct Smem {
     union alignas(16) {
         uint32_t mg[merge_nst(BS)][merge_stage(BS)];  // staged merge tile inputs (TMA destinations)
         struct {  // one set of records per block part (its current expansion tile)
-            uint32_t base[4][EXPAND_TILE + 2];
-            uint32_t v[4][EXPAND_TILE + 2];
-            unsigned long long d[4][EXPAND_TILE + 2];  // SSSP: the source's distance, read once per tile
+            uint32_t base[EXPAND_PARTS(BS)][expand_tile_len(BS) + 2];
+            uint32_t v[EXPAND_PARTS(BS)][expand_tile_len(BS) + 2];
+            unsigned long long d[EXPAND_PARTS(BS)][expand_tile_len(BS) + 2];  // SSSP: the source's distance, read once per tile
         } ex;
         unsigned long long jr[2][JR_SLOTS][2];  // fib joins: the next tile's children's results, prefetched
     } u;

@@ -121,18 +121,18 @@ __host__ __device__ constexpr size_t ring_bytes() {
 
 // Dynamic shared memory bytes k_persistent<bs, tpt, program mask pm> is launched with.
 // SSSP's persistent kernels keep each block part's claim buffer (relax_tile)
-// in dynamic shared memory: CLAIM_CAP entries a part when that fits beside
-// the static shared memory at the kernel's residency, else none (the
-// per-tile reservation path).  A partial buffer is not worth it: at 256
-// threads it would take the SM's shared memory to 232 KB of its 256 KB and
-// leave the L1 cache the tiles' gathers use 24 KB (SSSP R-MAT 22 at 256 x 2:
-// 2.80 -> 4.65 ms with 636-entry buffers).
+// in dynamic shared memory: claim_cap_of(BS) entries a part, for blocks of
+// 512 threads or more when that fits beside the static shared memory at the
+// kernel's residency, else none (the per-tile reservation path).  Smaller
+// blocks run four or more per SM, and their buffers would take the SM's
+// shared memory to ~230 KB of its 256 KB, leaving the L1 cache the tiles'
+// gathers use ~25 KB (SSSP R-MAT 22 at 256 x 2: 2.80 -> 4.5-4.65 ms).
 template <int BS, int TPT>
 __host__ __device__ constexpr uint32_t sssp_claim_cap() {
-    return SMEM_PER_SM / persistent_min_blocks(BS, PM_SSSP, TPT) - SMEM_RESERVED_PER_BLOCK -
-                       ((int)sizeof(Smem<BS>) + 256) >=
-                   (int)(4u * EXPAND_PARTS(BS) * CLAIM_CAP)
-               ? CLAIM_CAP
+    return BS >= 512 && SMEM_PER_SM / persistent_min_blocks(BS, PM_SSSP, TPT) - SMEM_RESERVED_PER_BLOCK -
+                                ((int)sizeof(Smem<BS>) + 256) >=
+                            (int)(4u * EXPAND_PARTS(BS) * claim_cap_of(BS))
+               ? claim_cap_of(BS)
                : 0u;
 }
 

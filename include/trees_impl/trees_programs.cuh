@@ -574,7 +574,8 @@ __device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan (&p)
         const unsigned long long ebase = g & CTR_LOW_MASK;
         const uint32_t ndesc = (uint32_t)(tb >> 40);
         const unsigned long long nel = tb & CTR_LOW_MASK;
-        const unsigned long long tiles_end = (ebase + nel + EXPAND_TILE - 1) / EXPAND_TILE;
+        constexpr uint32_t ET = expand_tile_len(BS);
+        const unsigned long long tiles_end = (ebase + nel + ET - 1) / ET;
         const bool fits = (unsigned long long)dbase + ndesc <= c.mcap && ebase + nel < 0xFFFFFFFFull &&
                           tiles_end <= c.mcap;
         if (!fits) {
@@ -590,7 +591,7 @@ __device__ void map_alloc(const Conf &c, Ctl *ctl, Smem<BS> &sm, const Plan (&p)
                 c.me_base[di] = b;
                 c.me_job[di] = job;
                 c.me_src[di] = p[k].a1;  // the vertex (SSSP reads its distance)
-                for (uint32_t t = (b + EXPAND_TILE - 1u) / EXPAND_TILE; t * EXPAND_TILE < b + p[k].n; ++t)
+                for (uint32_t t = (b + ET - 1u) / ET; t * ET < b + p[k].n; ++t)
                     c.me_tfd[t] = di;
                 acc.maps++;
                 ++di;
@@ -1673,7 +1674,7 @@ __device__ void merge_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t nt1,
 }
 
 // The element maps (BFS expansion, SSSP relaxation) run as tiles of
-// EXPAND_TILE adjacency entries, each taken by one part of a block: the
+// expand_tile_len(BS) adjacency entries, each taken by one part of a block: the
 // EXPAND_PARTS(BS) parts of a block (BS / parts threads each, synchronised by
 // their own named barriers, with disjoint shared-memory records) run
 // independent tiles, so an SM has several tile chains in flight per block
@@ -1732,7 +1733,7 @@ __device__ __forceinline__ uint32_t load_tile_descriptors(const Conf &c, Smem<BS
 // descriptor, then the descriptors).  KD: the most a thread holds.
 template <int BS>
 struct DescAhead {
-    static constexpr uint32_t HB = BS / EXPAND_PARTS(BS), KD = (EXPAND_TILE + 2u + HB - 1u) / HB;
+    static constexpr uint32_t HB = BS / EXPAND_PARTS(BS), KD = (expand_tile_len(BS) + 2u + HB - 1u) / HB;
     uint32_t n;  // descriptors of the next tile (0: no next tile)
     uint32_t b[KD], v[KD];
 };
@@ -1805,11 +1806,11 @@ __device__ __forceinline__ bool part_reserve(const Conf &c, Ctl *ctl, Smem<BS> &
 // reservation (and the scan that placed the claims) per tile cost more than
 // the claims' stores.  The fork range stays gap-free: each flush reserves
 // exactly its claims.
-constexpr uint32_t CLAIM_CAP = 2u * (EXPAND_TILE + 2u);  // u32 entries: the d records of one part
+__host__ __device__ constexpr uint32_t claim_cap_of(int bs) { return 2u * (expand_tile_len(bs) + 2u); }  // the d records of one part, in u32
 
 template <int BS>
 __device__ __forceinline__ uint32_t *claim_buf(Smem<BS> &sm, uint32_t h) {
-    static_assert(sizeof(sm.u.ex.d[0]) >= CLAIM_CAP * sizeof(uint32_t), "a part's buffer fits its d records");
+    static_assert(sizeof(sm.u.ex.d[0]) >= claim_cap_of(BS) * sizeof(uint32_t), "a part's buffer fits its d records");
     return reinterpret_cast<uint32_t *>(sm.u.ex.d[h]);
 }
 
@@ -1847,7 +1848,7 @@ __device__ __forceinline__ void claim_append(Smem<BS> &sm, uint32_t *cb, uint32_
         if ((cmask >> j) & 1u) cb[pos++] = (uint32_t)uu[j];
 }
 
-// One BFS expansion tile (EXPAND_TILE consecutive adjacency entries of the
+// One BFS expansion tile (expand_tile_len(BS) consecutive adjacency entries of the
 // epoch's frontier) on part h of the block, whose nloc descriptors are in the
 // part's records.  Each entry's vertex is found by a binary search over the
 // tile's descriptors in shared memory (load-balanced search); an unvisited
@@ -1858,9 +1859,9 @@ template <int BS>
 __device__ uint32_t expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, uint32_t tn, uint32_t nloc,
                                 uint32_t nd, uint32_t ne, uint32_t nt, uint32_t cen, uint32_t base, uint32_t ep,
                                 uint32_t e, uint32_t h) {
-    constexpr uint32_t HB = BS / EXPAND_PARTS(BS), EPT = EXPAND_TILE / HB;
+    constexpr uint32_t ET = expand_tile_len(BS), HB = BS / EXPAND_PARTS(BS), EPT = ET / HB;
     const uint32_t lt = threadIdx.x - h * HB;
-    const uint32_t g0 = t * EXPAND_TILE, g1 = min(g0 + EXPAND_TILE, ne);
+    const uint32_t g0 = t * ET, g1 = min(g0 + ET, ne);
     // stage 1: every element's adjacency index (load-balanced search in shared memory)
     uint32_t ed[EPT];
 #pragma unroll
@@ -1895,7 +1896,7 @@ __device__ uint32_t expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t 
     claim_append<BS, (int)EPT>(sm, claim_buf<BS>(sm, h), h, cmask, uu);
     bar_part<BS>(h);  // every thread of the part is past its search and its appends
     desc_ahead_store<BS>(sm, h, lt, A);  // the records are free
-    if (sm.pcnt[h] > CLAIM_CAP - EXPAND_TILE)  // part-uniform
+    if (sm.pcnt[h] > claim_cap_of(BS) - ET)  // part-uniform
         claim_flush<BS>(c, ctl, sm, claim_buf<BS>(sm, h), h, lt, enc(cen + 1u, TREES_TASK_BFS_VISIT), base, ep, e);
     bar_part<BS>(h);  // the next tile's records are in place
     return A.n;
@@ -1917,9 +1918,9 @@ template <int BS>
 __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, uint32_t nd, uint32_t ne, uint32_t nt,
                            uint32_t cen, uint32_t base, uint32_t ep, uint32_t e, uint32_t h, uint32_t *cb,
                            uint32_t cap) {
-    constexpr uint32_t HB = BS / EXPAND_PARTS(BS), EPT = EXPAND_TILE / HB;
+    constexpr uint32_t ET = expand_tile_len(BS), HB = BS / EXPAND_PARTS(BS), EPT = ET / HB;
     const uint32_t lt = threadIdx.x - h * HB;
-    const uint32_t g0 = t * EXPAND_TILE, g1 = min(g0 + EXPAND_TILE, ne);
+    const uint32_t g0 = t * ET, g1 = min(g0 + ET, ne);
     const uint32_t dfirst = c.me_tfd[t];
     const uint32_t nloc = load_tile_descriptors<BS, true>(c, sm, t, nd, nt, h, lt);
     // stage 1: every element's adjacency index and its source's distance (load-balanced search)
@@ -1988,7 +1989,7 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
             atomicMax(c.rp.used + c.me_src[dfirst + k], (unsigned long long)(cen + 1u) << SSSP_USED_SHIFT | d);
     }
     bar_part<BS>(h);  // the part's records are its next tile's
-    if (cb && sm.pcnt[h] > cap - EXPAND_TILE)  // part-uniform
+    if (cb && sm.pcnt[h] > cap - ET)  // part-uniform
         claim_flush<BS>(c, ctl, sm, cb, h, lt, enc(cen + 1u, TREES_TASK_SSSP_RELAX), base, ep, e);
 }
 
@@ -2039,7 +2040,7 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
                           uint32_t job_stride = 0, uint32_t *claims = nullptr, uint32_t claim_cap = 0u) {
     const uint32_t nt1 = (uint32_t)(mt & CTR_LOW_MASK), nd1 = (uint32_t)(mt >> 40);
     const uint32_t nd2 = (uint32_t)(me >> 40), ne2 = (uint32_t)(me & CTR_LOW_MASK);
-    const uint32_t nt2 = (ne2 + EXPAND_TILE - 1u) / EXPAND_TILE;
+    const uint32_t nt2 = (ne2 + expand_tile_len(BS) - 1u) / expand_tile_len(BS);
     uint32_t *keys, *scratch;
     if constexpr ((PM & PM_USER) != 0u) {  // one block per unit, grid-stride over the epoch's units
         const trees_user_env env = user_env(c);
@@ -2082,7 +2083,7 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
             const uint32_t lt = threadIdx.x - h * (uint32_t)(BS / P);
             if (sssp) {
                 // a part's claim buffer: claim_cap entries of the caller's buffer, or none (per-tile forks)
-                uint32_t *cb = claims && claim_cap >= EXPAND_TILE + 32u ? claims + h * claim_cap : nullptr;
+                uint32_t *cb = claims && claim_cap >= expand_tile_len(BS) + 32u ? claims + h * claim_cap : nullptr;
                 uint32_t t = P * blockIdx.x + h;
                 if (t < nt2) {
                     if (cb && lt == 0u) sm.pcnt[h] = 0u;  // the tile's descriptor load ends with a barrier of the part
