@@ -39,14 +39,17 @@ __host__ __device__ constexpr uint32_t merge_stage(int bs) { return merge_tile(b
 // next streams in.
 __host__ __device__ constexpr int merge_nst(int) { return 2; }
 // Parts of a block that run BFS / SSSP expansion tiles independently, and the
-// adjacency entries of one tile (a part's): blocks of 512 or more threads run
-// eight parts of 256-entry tiles, smaller blocks four (two at 128 threads) of
-// 512 entries; either way a part's threads take 2-8 entries each, and the
-// parts' records fill the same shared union.  Measured (R-MAT 22, one call):
-// 8 parts x 256 at 512 x 2 BFS 0.918 -> 0.844 ms, SSSP 2.49 -> 2.43 ms; at
-// 256 threads 4 parts x 256 were slower (BFS 0.94 -> 0.98 ms).
-#define EXPAND_PARTS(BS) ((BS) >= 512 ? 8u : (BS) >= 256 ? 4u : 2u)
-__host__ __device__ constexpr uint32_t expand_tile_len(int bs) { return bs >= 512 ? 256u : 512u; }
+// adjacency entries of one tile (a part's): 512-thread blocks run sixteen
+// one-warp parts of 128-entry tiles, 1024-thread blocks eight parts of 256
+// (a part of several warps syncs on a named barrier, ids 1..15), smaller
+// blocks four (two at 128 threads) of 512; a part's threads take 2-8 entries
+// each and the parts' records fill the same shared union.  More parts are
+// more tile chains in flight per SM (R-MAT 22, one call each: at 512 x 2 BFS
+// 0.918 ms with 4 parts x 512, 0.844 with 8 x 256, 0.785 with 16 x 128; SSSP
+// 512 x 1 2.52, 2.38, 2.27 ms); at 256 threads 4 parts x 256 were slower than
+// 4 x 512 (BFS 0.94 -> 0.98 ms).
+#define EXPAND_PARTS(BS) ((BS) == 512 ? 16u : (BS) >= 1024 ? 8u : (BS) >= 256 ? 4u : 2u)
+__host__ __device__ constexpr uint32_t expand_tile_len(int bs) { return bs == 512 ? 128u : bs >= 1024 ? 256u : 512u; }
 constexpr uint32_t JR_SLOTS = 1024;             // tile slots whose join operands can be prefetched
 constexpr uint32_t SMP_SHIFT = 6;               // mergesort splitter samples: every 64th key of a run
 constexpr int MCHUNK = 64;                      // merge tiles a block resolves at once
@@ -216,8 +219,8 @@ struct Smem {
     unsigned long long w64a[NW];
     unsigned long long w64b[NW];
     unsigned int flags;
-    unsigned int bc32[16];                // broadcast words (two per block part in the expansion tiles)
-    unsigned int pcnt[8];                 // claims waiting in each block part's buffer (claim_flush)
+    unsigned int bc32[32];                // broadcast words (two per block part in the expansion tiles)
+    unsigned int pcnt[16];                // claims waiting in each block part's buffer (claim_flush)
     unsigned long long bc64[4];
     int bar_ok;
     unsigned long long mbar[merge_nst(BS)];  // mbarriers of the merge stage buffers

@@ -1679,10 +1679,15 @@ __device__ void merge_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t nt1,
 // their own named barriers, with disjoint shared-memory records) run
 // independent tiles, so an SM has several tile chains in flight per block
 // without more registers or shared memory.  bar_part(h): the barrier of part h
-// (ids 1..parts).
+// (ids 1..parts; a warp barrier for one-warp parts).
 template <int BS>
 __device__ __forceinline__ void bar_part(uint32_t h) {
-    asm volatile("bar.sync %0, %1;" ::"r"(1u + h), "r"((uint32_t)(BS / EXPAND_PARTS(BS))) : "memory");
+    static_assert(BS / EXPAND_PARTS(BS) == 32 || EXPAND_PARTS(BS) <= 15u, "named barrier ids 1..15");
+    if constexpr (BS / EXPAND_PARTS(BS) == 32) {
+        __syncwarp();  // a one-warp part
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(1u + h), "r"((uint32_t)(BS / EXPAND_PARTS(BS))) : "memory");
+    }
 }
 
 // Exclusive scan of v over the threads of block part h (thread order), with
