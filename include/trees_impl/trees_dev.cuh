@@ -83,6 +83,9 @@ struct RunParams {
     // SSSP: per vertex, (e + 1) << 40 | the largest distance of it that a relaxation of its
     // out-edges used in epoch e, e its last relax epoch (0 = never relaxed; context-owned)
     unsigned long long *used;
+    // BFS: one bit per vertex, set once the vertex is claimed (context-owned): the expansion
+    // probes it before the claim's CAS on `level`
+    uint32_t *visited;
     const float2 *fx;          // FFT input, N complex points
     float2 *fX;                // FFT output
     uint32_t lgn;              // FFT: log2 N

@@ -1878,25 +1878,37 @@ __device__ uint32_t expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t 
             ed[j] = sm.u.ex.v[h][k] + (g - sm.u.ex.base[h][k]);
         }
     }
-    // stage 2: all neighbour ids, then all their levels, in flight together (and the next tile's
-    // descriptors behind them)
-    int32_t uu[EPT], lv[EPT];
+    // stage 2: all neighbour ids, then all their visited bits, in flight together (and the next
+    // tile's descriptors behind them).  The bits are a hint: one is set only after its vertex's
+    // claim, so a clear bit may be stale (the CAS then fails) but a set bit never is; 32 vertices
+    // share a word, so the probes find them in L1 and L2 far more often than the levels (a 32-byte
+    // sector per probe of the 16 MB level array at R-MAT 22)
+    int32_t uu[EPT];
+    uint32_t vb[EPT];
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j) uu[j] = ed[j] != 0xFFFFFFFFu ? __ldg(c.rp.col + ed[j]) : -1;
     DescAhead<BS> A;
     desc_ahead_issue<BS>(c, tn, nd, nt, lt, A);
 #pragma unroll
-    for (uint32_t j = 0; j < EPT; ++j) lv[j] = uu[j] >= 0 ? c.rp.level[uu[j]] : 0;
-    // stage 3: claim unvisited neighbours (the CAS decides between competing visits); all of the
-    // thread's CASes are issued before any answer is examined, so their round trips overlap
+    for (uint32_t j = 0; j < EPT; ++j) vb[j] = uu[j] >= 0 ? __ldca(c.rp.visited + ((uint32_t)uu[j] >> 5)) : ~0u;
+    // stage 3: claim unvisited neighbours (the CAS on the level decides between competing visits);
+    // all of the thread's CASes are issued before any answer is examined, so their round trips overlap
     const int32_t nlev = (int32_t)(cen + 1u);
+    bool probe[EPT];
     int32_t prev[EPT];
 #pragma unroll
-    for (uint32_t j = 0; j < EPT; ++j) prev[j] = uu[j] >= 0 && lv[j] < 0 ? atomicCAS(c.rp.level + uu[j], -1, nlev) : 0;
+    for (uint32_t j = 0; j < EPT; ++j) {
+        probe[j] = uu[j] >= 0 && ((vb[j] >> ((uint32_t)uu[j] & 31u)) & 1u) == 0u;
+        prev[j] = probe[j] ? atomicCAS(c.rp.level + uu[j], -1, nlev) : 0;
+    }
     uint32_t cmask = 0u;
 #pragma unroll
-    for (uint32_t j = 0; j < EPT; ++j)
-        if (uu[j] >= 0 && lv[j] < 0 && prev[j] == -1) cmask |= 1u << j;
+    for (uint32_t j = 0; j < EPT; ++j) {
+        if (probe[j] && prev[j] == -1) {
+            cmask |= 1u << j;
+            atomicOr(c.rp.visited + ((uint32_t)uu[j] >> 5), 1u << ((uint32_t)uu[j] & 31u));
+        }
+    }
     // the claimed vertices go to the part's buffer
     claim_append<BS, (int)EPT>(sm, claim_buf<BS>(sm, h), h, cmask, uu);
     bar_part<BS>(h);  // every thread of the part is past its search and its appends

@@ -65,9 +65,14 @@ __global__ void k_setup(Ctl *ctl, Conf c, uint32_t type, uint32_t a0, uint32_t a
     }
 }
 
-__global__ void k_bfs_init(int32_t *level, int32_t nv, int32_t src) {
+// BFS start: every level unknown but the source's, and the visited bits
+// likewise.
+__global__ void k_bfs_init(int32_t *level, uint32_t *visited, int32_t nv, int32_t src) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x)
         level[v] = (v == src) ? 0 : -1;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < ((int64_t)nv + 31) / 32;
+         w += (int64_t)gridDim.x * blockDim.x)
+        visited[w] = w == src / 32 ? 1u << (src % 32) : 0u;
 }
 
 // SSSP start: every distance unknown but the source's; no vertex forked yet
@@ -796,6 +801,17 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
         rp.col = job->col;
         rp.level = job->level;
         rp.nv = job->nv;
+        {  // the visited bits: the context's per-vertex buffer, which BFS does not use otherwise
+            const size_t words = ((size_t)job->nv + 63) / 64;
+            if (x->own_used_n < words) {
+                if (x->own_used) cudaFree(x->own_used);
+                x->own_used = nullptr;
+                x->own_used_n = 0;
+                if (cudaMalloc(&x->own_used, words * 8) != cudaSuccess) return TREES_ERR_CUDA;
+                x->own_used_n = words;
+            }
+            rp.visited = reinterpret_cast<uint32_t *>(x->own_used);
+        }
         type = TREES_TASK_BFS_VISIT;
         a0 = job->n;
         break;
@@ -867,7 +883,7 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
     k_setup<<<1, 256, 0, st>>>(x->ctl, x->conf, type, a0, a1);
     if (job->program == TREES_PROG_BFS) {
         const int nb = std::min<int64_t>((job->nv + 255) / 256, 65536);
-        k_bfs_init<<<nb, 256, 0, st>>>(job->level, job->nv, (int32_t)job->n);
+        k_bfs_init<<<nb, 256, 0, st>>>(job->level, rp.visited, job->nv, (int32_t)job->n);
     }
     if (job->program == TREES_PROG_SSSP) {
         const int nb = std::min<int64_t>((job->nv + 255) / 256, 65536);
