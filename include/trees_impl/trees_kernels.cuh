@@ -620,6 +620,12 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
                 done = true;
             }
         }
+        if constexpr (PM == PM_FFT) {
+            if (mode == LOAD_FRESH && cen <= c.rp.lgn && c.rp.lgn - cen == 4u && c.rp.leaf >= 16u) {
+                fft_leaf_epoch<BS, TPT>(c, t0, step, hi, cen, acc);  // 16-point leaves only: no forks, no scan
+                done = true;
+            }
+        }
         if constexpr (PM == PM_FIB && ring_depths<BS, TPT, PM>() != 0) {
             if (mode == LOAD_JOIN) {  // sums through the ring of asynchronous copies
                 constexpr int RD = ring_depths<BS, TPT, PM>();

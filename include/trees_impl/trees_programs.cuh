@@ -412,6 +412,76 @@ __device__ __forceinline__ void fft_task_bodies(const RunParams &rp, const Plan 
             fft_combine_task(rp.fX, fft_block(p[k].a0, p[k].a1, rp.lgn), rp.lgn - p[k].a1);
 }
 
+// The FFT's leaf epoch (16-point leaves): every task of a fresh FFT range
+// has depth CEN (the root is task (0, 0) of epoch 0 and a fork's children
+// have the next depth in the next epoch), so when 2^(lgn - CEN) = 16 points
+// is the leaf size every task of the range is a leaf: it reads its entry,
+// transforms its 16 points and emits them into their output block, forks
+// nothing and joins nothing.  With no forks there is no scan and no block
+// barrier, so each thread streams through its slots of the block's tiles on
+// its own, its next entries in flight while a slot is transformed (the
+// generic tile path waits for each tile's loads after its block scan).  Slot order is point order (task o is at slot
+// lo + o), so a warp's loads stay coalesced.
+template <int BS, int TPT>
+__device__ __forceinline__ void fft_leaf_epoch(const Conf &c, unsigned long long t0, unsigned long long step,
+                                               uint32_t hi, uint32_t cen, Acc &acc) {
+    const float2 *__restrict__ x = c.rp.fx;
+    float2 *__restrict__ X = c.rp.fX;
+    const uint32_t lgn = c.rp.lgn, d = cen;
+    const uint32_t ntile = t0 < hi ? (uint32_t)((hi - t0 + step - 1ull) / step) : 0u, n = ntile * (uint32_t)TPT;
+    const auto slot = [&](uint32_t i) {
+        return t0 + (unsigned long long)(i / (uint32_t)TPT) * step + (unsigned long long)(i % (uint32_t)TPT) * BS +
+               threadIdx.x;
+    };
+    // slot i's task: its code (0: none or not this thread's) and offset o
+    const auto entry = [&](uint32_t i, uint32_t &cd, uint32_t &o) {
+        cd = 0u;
+        o = 0u;
+        if (i < n) {
+            const unsigned long long s = slot(i);
+            if (s < hi) {
+                cd = c.code[s];
+                o = c.a0[s];
+            }
+        }
+    };
+    const auto inputs = [&](uint32_t cd, uint32_t o, float2 (&a)[16]) {
+        if (task_type(cd, cen) == TREES_TASK_FFT) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) a[r] = x[o + ((uint32_t)fft_rev(r, 4) << d)];
+        }
+    };
+    uint32_t c0, o0, c1, o1, c2, o2;
+    entry(0u, c0, o0);
+    entry(1u, c1, o1);
+    for (uint32_t i = 0; i < n; ++i) {
+        entry(i + 2u, c2, o2);  // two ahead: the entry
+        if (task_type(c0, cen) == TREES_TASK_FFT) {
+            float2 a[16];
+            inputs(c0, o0, a);
+            acc.valid++;
+#pragma unroll
+            for (int lm = 1; lm <= 4; ++lm) {
+                const int h = 1 << (lm - 1);
+#pragma unroll
+                for (int k = 0; k < h; ++k) {
+                    const float2 w = fft_twiddle((uint32_t)k, (uint32_t)lm);
+#pragma unroll
+                    for (int q = 0; q < 16; q += 2 * h) fft_bfly(a[q + k], a[q + k + h], w);
+                }
+            }
+            const uint32_t dst = fft_block(o0, d, lgn);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) X[dst + k] = a[k];
+            c.code[(uint32_t)slot(i)] = 0u;  // emitted: the entry is dead
+        }
+        c0 = c1;
+        o0 = o1;
+        c1 = c2;
+        o1 = o2;
+    }
+}
+
 // Step 2: write the children into [child, child + n) for epoch CEN+1 and turn
 // the task into its join continuation.  Returns 1 if it joined.
 // fbase: the first slot of the epoch's fork range (the FFT places its
