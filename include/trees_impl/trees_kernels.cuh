@@ -620,9 +620,16 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
                 done = true;
             }
         }
-        if constexpr (PM == PM_FFT) {
-            if (mode == LOAD_FRESH && cen <= c.rp.lgn && c.rp.lgn - cen == 4u && c.rp.leaf >= 16u) {
+        if constexpr (PM == PM_FFT) {  // every task of an FFT epoch has depth CEN: the width fixes forks and maps
+            const uint32_t lgm = cen <= c.rp.lgn ? c.rp.lgn - cen : 0u;
+            if (mode == LOAD_FRESH && lgm == 4u && c.rp.leaf >= 16u) {
                 fft_leaf_epoch<BS, TPT>(c, t0, step, hi, cen, acc);  // 16-point leaves only: no forks, no scan
+                done = true;
+            } else if (mode == LOAD_FRESH && cen <= c.rp.lgn && (1u << lgm) > c.rp.leaf) {
+                jn = fft_fork_epoch<BS, TPT>(c, ctl, t0, step, lo, hi, cen, base, ep, e, acc);
+                done = true;
+            } else if (mode == LOAD_JOIN && lgm >= 1u && (1u << lgm) > c.rp.cutoff) {
+                fft_combine_epoch<BS, TPT>(c, ctl, t0, step, lo, hi, cen, ep, acc);
                 done = true;
             }
         }

@@ -482,6 +482,91 @@ __device__ __forceinline__ void fft_leaf_epoch(const Conf &c, unsigned long long
     }
 }
 
+// The FFT's other epochs above the leaves, for the same reason (every task
+// of an epoch has depth CEN, so the epoch's width fixes its forks and maps).
+// A fork epoch: each task (o, d) writes its two children at their point
+// offsets, fbase + o and fbase + o + 2^d (as commit_task places them), and
+// becomes its combine; the epoch's forks, two per task, are added to
+// nextFreeCore by one thread for the whole grid (Sec. 5.2.3's cooperative
+// allocation, the group being the epoch).  Returns whether this thread's
+// tasks joined.
+template <int BS, int TPT>
+__device__ __forceinline__ bool fft_fork_epoch(const Conf &c, Ctl *ctl, unsigned long long t0, unsigned long long step,
+                                               uint32_t lo, uint32_t hi, uint32_t cen, uint32_t base, uint32_t ep,
+                                               uint32_t e, Acc &acc) {
+    const uint32_t fe = enc(cen + 1u, TREES_TASK_FFT), fj = enc(cen, TREES_TASK_FFT_COMBINE);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicAdd(fork_ctr(ctl, ep), 2u * (hi - lo));
+        if ((unsigned long long)base + 2ull * (hi - lo) > c.cap) set_err(ctl, TREES_ERR_CAPACITY, e);
+    }
+    bool joined = false;
+    uint32_t cd[TPT], o[TPT], d[TPT];  // the current tile's entries; the next tile's load while it is written
+    const auto load = [&](unsigned long long tt) {
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            const unsigned long long s = tt + (unsigned long long)k * BS + threadIdx.x;
+            const bool in = tt < hi && s < hi;
+            cd[k] = in ? c.code[s] : 0u;
+            o[k] = in ? c.a0[s] : 0u;
+            d[k] = in ? c.a1[s] : 0u;
+        }
+    };
+    load(t0);
+    for (; t0 < hi; t0 += step) {
+        uint32_t pc[TPT], po[TPT], pd[TPT];
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            pc[k] = cd[k];
+            po[k] = o[k];
+            pd[k] = d[k];
+        }
+        load(t0 + step);
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            if (task_type(pc[k], cen) != TREES_TASK_FFT) continue;
+            const uint32_t s = (uint32_t)(t0 + (unsigned long long)k * BS + threadIdx.x);
+            const uint32_t c0 = base + po[k], c1 = c0 + (1u << pd[k]);
+            if ((unsigned long long)c1 >= c.cap) continue;  // the capacity error is set above
+            c.code[c0] = fe;
+            c.a0[c0] = po[k];
+            c.a1[c0] = pd[k] + 1u;
+            c.code[c1] = fe;
+            c.a0[c1] = po[k] + (1u << pd[k]);
+            c.a1[c1] = pd[k] + 1u;
+            c.code[s] = fj;
+            acc.valid++;
+            acc.joins++;
+            joined = true;
+        }
+    }
+    return joined;
+}
+
+// A combine epoch whose combines are maps: each task schedules the map over
+// its 2^(lgm-1) butterflies and is done; the epoch's maps (one descriptor
+// count per task, N/2 butterflies in all) are added to the map counter by one
+// thread for the whole grid (the combine maps need no descriptors).
+template <int BS, int TPT>
+__device__ __forceinline__ void fft_combine_epoch(const Conf &c, Ctl *ctl, unsigned long long t0,
+                                                  unsigned long long step, uint32_t lo, uint32_t hi, uint32_t cen,
+                                                  uint32_t ep, Acc &acc) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long nd = hi - lo;
+        atomicAdd(&ctl->me_ctr[ep], (nd << 40) | (nd << (c.rp.lgn - cen - 1u)));
+    }
+    for (; t0 < hi; t0 += step) {
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            const unsigned long long s = t0 + (unsigned long long)k * BS + threadIdx.x;
+            if (s < hi && task_type(c.code[s], cen) == TREES_TASK_FFT_COMBINE) {
+                c.code[s] = 0u;
+                acc.valid++;
+                acc.maps++;
+            }
+        }
+    }
+}
+
 // Step 2: write the children into [child, child + n) for epoch CEN+1 and turn
 // the task into its join continuation.  Returns 1 if it joined.
 // fbase: the first slot of the epoch's fork range (the FFT places its
