@@ -363,6 +363,13 @@ struct trees_ctx {
     int last_sched = TREES_SCHED_PERSISTENT;
     int host_status = TREES_OK;
     Ctl *pinned_ctl = nullptr;
+    // trees_sync's copies of the last run's status and root result (slot 0), in pinned host memory
+    struct SyncPin {
+        int err;
+        int pad;
+        unsigned long long res0;
+    } *pin_sync = nullptr;
+    bool res0_valid = false;  // pin_sync->res0 is slot 0's result of the last run
     // batched runs
     Job *d_jobs = nullptr;
     uint32_t *d_joff = nullptr;
@@ -443,6 +450,7 @@ static int finish_create(trees_ctx *x) {
     c.gstack_cap = STK_CAP;
     x->blk = reinterpret_cast<unsigned long long *>(m + L.off_blk);
     if (cudaMallocHost(&x->pinned_ctl, sizeof(Ctl)) != cudaSuccess) return TREES_ERR_CUDA;
+    if (cudaMallocHost(&x->pin_sync, sizeof(trees_ctx::SyncPin)) != cudaSuccess) return TREES_ERR_CUDA;
     if (cudaMemset(x->ctl, 0, sizeof(Ctl)) != cudaSuccess) return TREES_ERR_CUDA;
     return TREES_OK;
 }
@@ -558,6 +566,7 @@ void trees_destroy(trees_ctx *x) {
     if (x->own_used) cudaFree(x->own_used);
     if (x->own_smp) cudaFree(x->own_smp);
     if (x->pinned_ctl) cudaFreeHost(x->pinned_ctl);
+    if (x->pin_sync) cudaFreeHost(x->pin_sync);
     if (x->d_jobs) cudaFree(x->d_jobs);
     if (x->d_joff) cudaFree(x->d_joff);
     if (x->d_done) cudaFree(x->d_done);
@@ -876,6 +885,7 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
         return TREES_ERR_INVALID_ARG;
     }
     x->last_stream = st;
+    x->res0_valid = false;
     x->last_sched = x->cfg.scheduler;
     if (cudaMemsetAsync(x->blk, 0, (size_t)NBLK_STATS * 4 * 8, st) != cudaSuccess) return TREES_ERR_CUDA;
     if (x->cfg.trace && cudaMemsetAsync(x->conf.trace_valid, 0, (size_t)x->cfg.trace_cap * 4, st) != cudaSuccess)
@@ -939,16 +949,27 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
     return TREES_ERR_INVALID_ARG;
 }
 
+// The run's status and its root result (slot 0, where fib and N-Queens
+// leave theirs) follow the run on its stream into pinned host memory, so the
+// host waits once instead of once per synchronous copy; trees_result(x, 0)
+// then returns the copied value until the next run.
 int trees_sync(trees_ctx *x) {
     if (!x) return TREES_ERR_INVALID_ARG;
-    if (cudaStreamSynchronize(x->last_stream) != cudaSuccess) return TREES_ERR_CUDA;
-    int err = 0;
-    if (cudaMemcpy(&err, &x->ctl->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TREES_ERR_CUDA;
-    return err;
+    if (cudaMemcpyAsync(&x->pin_sync->err, &x->ctl->err, sizeof(int), cudaMemcpyDeviceToHost, x->last_stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&x->pin_sync->res0, x->conf.result, 8, cudaMemcpyDeviceToHost, x->last_stream) != cudaSuccess ||
+        cudaStreamSynchronize(x->last_stream) != cudaSuccess)
+        return TREES_ERR_CUDA;
+    x->res0_valid = true;
+    return x->pin_sync->err;
 }
 
 int trees_result(trees_ctx *x, uint32_t slot, uint64_t *out) {
     if (!x || !out || slot >= x->cap) return TREES_ERR_INVALID_ARG;
+    if (slot == 0u && x->res0_valid) {  // copied by trees_sync after the last run
+        *out = x->pin_sync->res0;
+        return TREES_OK;
+    }
     unsigned long long v = 0;
     if (cudaMemcpy(&v, x->conf.result + slot, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return TREES_ERR_CUDA;
     *out = v;
@@ -1451,6 +1472,7 @@ extern "C" int trees_batch_run(trees_ctx *x, const trees_job_t *jobs, const uint
         cudaMemcpyAsync(x->d_bc, &hb, sizeof(hb), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return TREES_ERR_CUDA;
     x->last_stream = st;
+    x->res0_valid = false;
     x->batch_n = njobs;
     // the host copies above read pageable/pinned host memory; keep hb alive until issued
     if (cudaStreamSynchronize(st) != cudaSuccess) return TREES_ERR_CUDA;
