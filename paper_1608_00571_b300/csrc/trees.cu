@@ -40,9 +40,14 @@ namespace {
 
 // ------------------------------------------------------------------ kernels
 
-// Zeroes the control block and writes the root task into TV entry 0 for
-// epoch 0 (Sec. 5.2.1).
-__global__ void k_setup(Ctl *ctl, Conf c, uint32_t type, uint32_t a0, uint32_t a1) {
+// Zeroes the control block and the run's per-block statistics and writes the
+// root task into TV entry 0 for epoch 0 (Sec. 5.2.1).
+constexpr int SETUP_BLOCKS = 32;  // k_setup's grid: the statistics' clearing spread over a few SMs
+__global__ void k_setup(Ctl *ctl, Conf c, uint32_t type, uint32_t a0, uint32_t a1, unsigned long long *blk) {
+    // every block clears its share of the per-block statistics; block 0 sets up the control block and the root
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (uint32_t)NBLK_STATS * 4u; i += gridDim.x * blockDim.x)
+        blk[i] = 0ull;
+    if (blockIdx.x != 0) return;
     unsigned int *w = reinterpret_cast<unsigned int *>(ctl);
     for (uint32_t i = threadIdx.x; i < sizeof(Ctl) / 4; i += blockDim.x) w[i] = 0u;
     __syncthreads();
@@ -887,10 +892,9 @@ int trees_run(trees_ctx *x, const trees_job_t *job, void *stream) {
     x->last_stream = st;
     x->res0_valid = false;
     x->last_sched = x->cfg.scheduler;
-    if (cudaMemsetAsync(x->blk, 0, (size_t)NBLK_STATS * 4 * 8, st) != cudaSuccess) return TREES_ERR_CUDA;
     if (x->cfg.trace && cudaMemsetAsync(x->conf.trace_valid, 0, (size_t)x->cfg.trace_cap * 4, st) != cudaSuccess)
         return TREES_ERR_CUDA;
-    k_setup<<<1, 256, 0, st>>>(x->ctl, x->conf, type, a0, a1);
+    k_setup<<<SETUP_BLOCKS, 256, 0, st>>>(x->ctl, x->conf, type, a0, a1, x->blk);
     if (job->program == TREES_PROG_BFS) {
         const int nb = std::min<int64_t>((job->nv + 255) / 256, 65536);
         k_bfs_init<<<nb, 256, 0, st>>>(job->level, rp.visited, job->nv, (int32_t)job->n);
@@ -1238,8 +1242,7 @@ extern "C" int trees_fib_noalloc(uint32_t n, uint32_t cutoff, uint64_t *dev_resu
     c.rp.cutoff = cutoff;
     c.rp.leaf = LEAF_MAX;
     unsigned long long *blk = reinterpret_cast<unsigned long long *>(m0 + L.off_blk);
-    if (cudaMemsetAsync(blk, 0, (size_t)NBLK_STATS * 4 * 8, st) != cudaSuccess) return TREES_ERR_CUDA;
-    k_setup<<<1, 256, 0, st>>>(ctl, c, TREES_TASK_FIB, n, 0u);
+    k_setup<<<SETUP_BLOCKS, 256, 0, st>>>(ctl, c, TREES_TASK_FIB, n, 0u, blk);
     if (cudaGetLastError() != cudaSuccess) return TREES_ERR_CUDA;
     void *args[] = {&ctl, &c, &blk};
     if (cudaLaunchCooperativeKernel(persistent_kernel_fib(1024, 2), dim3(d->grid), dim3(1024), args,
