@@ -1958,14 +1958,16 @@ __device__ __forceinline__ bool part_reserve(const Conf &c, Ctl *ctl, Smem<BS> &
     return !sm.bc32[2u * h + 1u];
 }
 
-// BFS claim buffers: the vertices an expansion tile claims wait in its block
-// part's buffer (the space of the distance records, which BFS does not use)
-// and are forked in bulk, one reservation on nextFreeCore for a buffer of
-// several tiles' claims (Sec. 5.2.3's single atomic for a group of forks,
-// the group made larger): a tile claims a dozen vertices on average, so a
-// reservation (and the scan that placed the claims) per tile cost more than
-// the claims' stores.  The fork range stays gap-free: each flush reserves
-// exactly its claims.
+// Claim buffers of the expansion tiles (block part h's buffer: the space of
+// its distance records, which BFS does not use; SSSP: dynamic shared memory).
+// SSSP's tiles append the vertices they claimed; BFS's tiles append their
+// candidates (neighbours whose visited bit was clear) and the flush claims
+// them.  Either way the forks of a buffer take one reservation on
+// nextFreeCore (Sec. 5.2.3's single atomic for a group of forks, the group
+// made larger): a tile claims a dozen vertices on average, so a reservation
+// (and the scan that placed the claims) per tile cost more than the claims'
+// stores.  The fork range stays gap-free: each flush reserves exactly its
+// claims.
 __host__ __device__ constexpr uint32_t claim_cap_of(int bs) { return 2u * (expand_tile_len(bs) + 2u); }  // the d records of one part, in u32
 
 template <int BS>
@@ -1994,7 +1996,63 @@ __device__ __forceinline__ void claim_flush(const Conf &c, Ctl *ctl, Smem<BS> &s
     bar_part<BS>(h);
 }
 
-// Appends this thread's claimed vertices (bits of cmask over uu) to part h's
+// BFS: claims the candidates in part h's buffer and forks the claimed ones as
+// visit tasks of epoch CEN+1 (every thread of the part calls it, after a
+// barrier of the part that follows the appends).  A CAS of each candidate's
+// level from -1 to CEN+1 decides between competing visits (the buffer may
+// hold a vertex several times, from several tiles or edges: one CAS wins),
+// the winner sets the vertex's visited bit, and one reservation places the
+// winners.  A thread's CASes are issued in groups of RC before any answer is
+// examined, so a buffer of ~30 tiles' candidates costs a few overlapped round
+// trips instead of one per tile (R-MAT 22, 512 x 1: 0.766 -> 0.668 ms; the
+// levels, and every epoch's task and fork counts, are unchanged: the same
+// vertices are claimed in the same epoch, by one candidate each).  Ends with
+// a barrier of the part.
+template <int BS>
+__device__ __forceinline__ void bfs_claim_flush(const Conf &c, Ctl *ctl, Smem<BS> &sm, const uint32_t *cb, uint32_t h,
+                                                uint32_t lt, uint32_t cen, uint32_t base, uint32_t ep, uint32_t e) {
+    constexpr uint32_t HB = BS / EXPAND_PARTS(BS), R = (claim_cap_of(BS) + HB - 1u) / HB, RC = 8u;
+    static_assert(R <= 32u, "one bit per candidate of a thread");
+    const uint32_t n = sm.pcnt[h];
+    const int32_t nlev = (int32_t)(cen + 1u);
+    uint32_t won = 0u;  // bit r: this thread's candidate r (buffer entry lt + r * HB) was claimed
+#pragma unroll
+    for (uint32_t r0 = 0; r0 < R; r0 += RC) {
+        int32_t prev[RC];
+#pragma unroll
+        for (uint32_t q = 0; q < RC; ++q) {
+            const uint32_t i = lt + (r0 + q) * HB;
+            prev[q] = r0 + q < R && i < n ? atomicCAS(c.rp.level + cb[i], -1, nlev) : 0;
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < RC; ++q) {
+            if (prev[q] == -1) {
+                const uint32_t u = cb[lt + (r0 + q) * HB];
+                won |= 1u << (r0 + q);
+                atomicOr(c.rp.visited + (u >> 5), 1u << (u & 31u));
+            }
+        }
+    }
+    uint32_t tot;
+    const uint32_t off = part_scan_u32<BS>((uint32_t)__popc(won), h, &tot, sm);
+    uint32_t b;
+    if (tot && part_reserve<BS>(c, ctl, sm, h, lt, tot, base, ep, e, &b)) {
+        const uint32_t code = enc(cen + 1u, TREES_TASK_BFS_VISIT);
+        uint32_t slot = base + b + off;
+#pragma unroll
+        for (uint32_t r = 0; r < R; ++r) {
+            if ((won >> r) & 1u) {
+                c.code[slot] = code;
+                c.a0[slot] = cb[lt + r * HB];
+                ++slot;
+            }
+        }
+    }
+    if (lt == 0u) sm.pcnt[h] = 0u;  // every thread read the count before part_scan's barrier
+    bar_part<BS>(h);
+}
+
+// Appends this thread's vertices (bits of cmask over uu) to part h's
 // buffer: one shared-memory atomic per warp, no barrier.
 template <int BS, int EPT>
 __device__ __forceinline__ void claim_append(Smem<BS> &sm, uint32_t *cb, uint32_t h, uint32_t cmask,
@@ -2011,8 +2069,9 @@ __device__ __forceinline__ void claim_append(Smem<BS> &sm, uint32_t *cb, uint32_
 // One BFS expansion tile (expand_tile_len(BS) consecutive adjacency entries of the
 // epoch's frontier) on part h of the block, whose nloc descriptors are in the
 // part's records.  Each entry's vertex is found by a binary search over the
-// tile's descriptors in shared memory (load-balanced search); an unvisited
-// neighbour is claimed with a CAS on its level and forked as a visit task.
+// tile's descriptors in shared memory (load-balanced search); a neighbour
+// whose visited bit is clear goes to the part's buffer, whose flush claims it
+// with a CAS on its level and forks it as a visit task (bfs_claim_flush).
 // The descriptors of the part's next tile tn are read meanwhile and are in
 // the records when it returns; it returns their count.
 template <int BS>
@@ -2037,39 +2096,32 @@ __device__ uint32_t expand_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t 
     // tile's descriptors behind them).  The bits are a hint: one is set only after its vertex's
     // claim, so a clear bit may be stale (the CAS then fails) but a set bit never is; 32 vertices
     // share a word, so the probes find them in L1 and L2 far more often than the levels (a 32-byte
-    // sector per probe of the 16 MB level array at R-MAT 22)
+    // sector per probe of the 16 MB level array at R-MAT 22).  The neighbour ids stream past once and
+    // are read without allocating in L1, which keeps the visited words there (R-MAT 22, 512 x 2:
+    // 0.768 -> 0.750 ms)
     int32_t uu[EPT];
     uint32_t vb[EPT];
 #pragma unroll
-    for (uint32_t j = 0; j < EPT; ++j) uu[j] = ed[j] != 0xFFFFFFFFu ? __ldg(c.rp.col + ed[j]) : -1;
+    for (uint32_t j = 0; j < EPT; ++j) {
+        uu[j] = -1;
+        if (ed[j] != 0xFFFFFFFFu)
+            asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(uu[j]) : "l"(c.rp.col + ed[j]));
+    }
     DescAhead<BS> A;
     desc_ahead_issue<BS>(c, tn, nd, nt, lt, A);
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j) vb[j] = uu[j] >= 0 ? __ldca(c.rp.visited + ((uint32_t)uu[j] >> 5)) : ~0u;
-    // stage 3: claim unvisited neighbours (the CAS on the level decides between competing visits);
-    // all of the thread's CASes are issued before any answer is examined, so their round trips overlap
-    const int32_t nlev = (int32_t)(cen + 1u);
-    bool probe[EPT];
-    int32_t prev[EPT];
-#pragma unroll
-    for (uint32_t j = 0; j < EPT; ++j) {
-        probe[j] = uu[j] >= 0 && ((vb[j] >> ((uint32_t)uu[j] & 31u)) & 1u) == 0u;
-        prev[j] = probe[j] ? atomicCAS(c.rp.level + uu[j], -1, nlev) : 0;
-    }
+    // stage 3: the neighbours whose visited bit is clear are candidates; they go to the part's
+    // buffer, and its flush claims them (the tile's chain ends without an atomic round trip)
     uint32_t cmask = 0u;
 #pragma unroll
-    for (uint32_t j = 0; j < EPT; ++j) {
-        if (probe[j] && prev[j] == -1) {
-            cmask |= 1u << j;
-            atomicOr(c.rp.visited + ((uint32_t)uu[j] >> 5), 1u << ((uint32_t)uu[j] & 31u));
-        }
-    }
-    // the claimed vertices go to the part's buffer
+    for (uint32_t j = 0; j < EPT; ++j)
+        if (uu[j] >= 0 && ((vb[j] >> ((uint32_t)uu[j] & 31u)) & 1u) == 0u) cmask |= 1u << j;
     claim_append<BS, (int)EPT>(sm, claim_buf<BS>(sm, h), h, cmask, uu);
     bar_part<BS>(h);  // every thread of the part is past its search and its appends
     desc_ahead_store<BS>(sm, h, lt, A);  // the records are free
     if (sm.pcnt[h] > claim_cap_of(BS) - ET)  // part-uniform
-        claim_flush<BS>(c, ctl, sm, claim_buf<BS>(sm, h), h, lt, enc(cen + 1u, TREES_TASK_BFS_VISIT), base, ep, e);
+        bfs_claim_flush<BS>(c, ctl, sm, claim_buf<BS>(sm, h), h, lt, cen, base, ep, e);
     bar_part<BS>(h);  // the next tile's records are in place
     return A.n;
 }
@@ -2109,17 +2161,25 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
             dv[j] = sm.u.ex.d[h][k];
         }
     }
-    // stage 2: neighbours, weights and the neighbours' distances in flight together
+    // stage 2: neighbours, weights and the neighbours' distances in flight together.  Neighbour ids
+    // and weights stream past once and are read without allocating in L1, which keeps the distances
+    // there (R-MAT 22, 512 x 1: 2.28 -> 2.14 ms)
     int32_t uu[EPT];
     unsigned long long cand[EPT], du[EPT];
 #pragma unroll
-    for (uint32_t j = 0; j < EPT; ++j) uu[j] = ed[j] != 0xFFFFFFFFu ? __ldg(c.rp.col + ed[j]) : -1;
+    for (uint32_t j = 0; j < EPT; ++j) {
+        uu[j] = -1;
+        if (ed[j] != 0xFFFFFFFFu)
+            asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(uu[j]) : "l"(c.rp.col + ed[j]));
+    }
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j) {
         cand[j] = ~0ull;
         du[j] = 0ull;
         if (uu[j] >= 0) {
-            cand[j] = dv[j] + (unsigned long long)__ldg(c.rp.weight + ed[j]);
+            uint32_t w;
+            asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(w) : "l"(c.rp.weight + ed[j]));
+            cand[j] = dv[j] + (unsigned long long)w;
             du[j] = c.rp.dist[uu[j]];
         }
     }
@@ -2272,8 +2332,7 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
                     for (; t < nt2; t += P * gridDim.x)
                         nloc = expand_tile<BS>(c, ctl, sm, t, t + P * gridDim.x, nloc, nd2, ne2, nt2, cen, base, ep,
                                                e, h);
-                    claim_flush<BS>(c, ctl, sm, claim_buf<BS>(sm, h), h, lt, enc(cen + 1u, TREES_TASK_BFS_VISIT),
-                                    base, ep, e);  // the claims left in the buffer
+                    bfs_claim_flush<BS>(c, ctl, sm, claim_buf<BS>(sm, h), h, lt, cen, base, ep, e);  // the candidates left
                 }
             }
         }
