@@ -877,7 +877,16 @@ __device__ __forceinline__ TileOut epoch_tile(const Conf &c, Ctl *ctl, Smem<BS> 
     }
     uint32_t ex[TPT], tot[TPT];
     int anymap;
-    block_scan_vec<BS, TPT>(nf, ex, tot, hasmap, &anymap, sm, par);
+    if constexpr ((PM & ~(PM_BFS | PM_SSSP)) == 0u) {
+        // a visit or relax task never forks itself (its map's tiles fork): no fork scan, and the
+        // map allocation's own scan sees whether the tile maps (R-MAT 22, BFS 512 x 1 0.665 ->
+        // 0.656 ms, SSSP 512 x 1 2.15 -> 2.13 ms)
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) ex[k] = tot[k] = 0u;
+        anymap = 1;
+    } else {
+        block_scan_vec<BS, TPT>(nf, ex, tot, hasmap, &anymap, sm, par);
+    }
     uint32_t all = 0;
 #pragma unroll
     for (int k = 0; k < TPT; ++k) all += tot[k];

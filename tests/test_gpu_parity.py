@@ -225,6 +225,34 @@ def test_bfs_rmat(scale):
         check_trace(ctx, sim)
 
 
+@pytest.mark.parametrize("bs,tpt,grid", [(512, 1, 0), (512, 1, 2), (256, 2, 3), (1024, 1, 2), (128, 2, 0)])
+def test_bfs_capacity_edge_and_buffer_flushes(bs, tpt, grid):
+    """BFS forks one visit task per reached vertex, from the flushes of the block parts' candidate
+    buffers (with two or three grid blocks every part flushes many times an epoch): a task vector
+    one slot short of the peak is a capacity error and the context stays usable; the peak itself
+    reproduces the oracle's levels and per-epoch trace."""
+    row_ptr, col, _ = gen.rmat(16, 16, seed=5)
+    sim = oracle.tvm_run(oracle.BFS, row_ptr=row_ptr, col=col, src=0)
+    peak = sim["stats"]["peak_slots"]
+    cfg = dict(block_size=bs, tasks_per_thread=tpt, trace=1)
+    if grid:
+        cfg["grid_blocks"] = grid
+    small_rp, small_col, _ = gen.rmat(10, 16, seed=6)
+    small = oracle.tvm_run(oracle.BFS, row_ptr=small_rp, col=small_col, src=0)
+    assert small["stats"]["peak_slots"] < peak - 1
+    with Ctx(peak - 1, **cfg) as ctx:
+        status, _ = bfs_gpu(ctx, row_ptr, col, 0)
+        assert status == T.TREES_ERR_CAPACITY
+        status, level = bfs_gpu(ctx, small_rp, small_col, 0)  # the next job on the same context
+        assert status == T.TREES_OK and np.array_equal(level, small["level"])
+    with Ctx(peak, **cfg) as ctx:
+        status, level = bfs_gpu(ctx, row_ptr, col, 0)
+        assert status == T.TREES_OK
+        assert np.array_equal(level, sim["level"])
+        assert T.trees_stats(ctx)["peak_slots"] == peak
+        check_trace(ctx, sim)
+
+
 @pytest.mark.parametrize("tpt", [1, 4])
 def test_all_programs_tasks_per_thread(tpt):
     cfg = dict(tasks_per_thread=tpt, block_size=256, trace=1)
