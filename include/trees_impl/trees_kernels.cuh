@@ -136,14 +136,51 @@ __host__ __device__ constexpr uint32_t sssp_claim_cap() {
                : 0u;
 }
 
+// The FFT leaf epoch's buffers (fft_leaf_epoch): the next slot's 16 input
+// points and a warp's 16 staged outputs per thread, 256 bytes a thread, in
+// dynamic shared memory for a kernel that runs one block per SM and has the
+// room beside its static shared memory; else the input buffer alone in the
+// shared union when it fits there (blocks of up to 256 threads), the output
+// buffer too when that fits (128 threads).  Two blocks per SM at 256 threads
+// with both buffers in dynamic shared memory left the L1 cache ~28 KB and
+// were slower (2^24 points, 256 x 1: 1.11 -> 1.25 ms); one block of 512
+// threads gained (1.198 -> 1.094 ms).
+template <int BS, int TPT, uint32_t PM>
+__host__ __device__ constexpr size_t fft_leaf_dyn_bytes() {
+    return PM == PM_FFT && persistent_min_blocks(BS, PM, TPT) == 1 && (size_t)BS * 32u * sizeof(float2) > sizeof(Smem<BS>::u) &&
+                   SMEM_PER_SM / persistent_min_blocks(BS, PM, TPT) - SMEM_RESERVED_PER_BLOCK -
+                           ((int)sizeof(Smem<BS>) + 256) >=
+                       (int)(BS * 32 * sizeof(float2))
+               ? (size_t)BS * 32u * sizeof(float2)
+               : 0u;
+}
+
 template <int BS, int TPT, uint32_t PM>
 __host__ __device__ constexpr size_t dyn_smem_bytes() {
     return PM == PM_FIB ? ring_bytes<BS, TPT, PM>()
+           : PM == PM_FFT ? fft_leaf_dyn_bytes<BS, TPT, PM>()
            : PM == PM_SSSP ? (size_t)4u * EXPAND_PARTS(BS) * sssp_claim_cap<BS, TPT>()
                            : 0u;
 }
 
 inline size_t persistent_smem_bytes(uint32_t pm, int bs, int tpt) {
+    if (pm == PM_FFT) {
+        switch (bs * 10 + tpt) {
+        case 1281: return dyn_smem_bytes<128, 1, PM_FFT>();
+        case 1282: return dyn_smem_bytes<128, 2, PM_FFT>();
+        case 1284: return dyn_smem_bytes<128, 4, PM_FFT>();
+        case 2561: return dyn_smem_bytes<256, 1, PM_FFT>();
+        case 2562: return dyn_smem_bytes<256, 2, PM_FFT>();
+        case 2564: return dyn_smem_bytes<256, 4, PM_FFT>();
+        case 5121: return dyn_smem_bytes<512, 1, PM_FFT>();
+        case 5122: return dyn_smem_bytes<512, 2, PM_FFT>();
+        case 5124: return dyn_smem_bytes<512, 4, PM_FFT>();
+        case 10241: return dyn_smem_bytes<1024, 1, PM_FFT>();
+        case 10242: return dyn_smem_bytes<1024, 2, PM_FFT>();
+        case 10244: return dyn_smem_bytes<1024, 4, PM_FFT>();
+        default: return 0;
+        }
+    }
     if (pm == PM_SSSP) {
         switch (bs * 10 + tpt) {
         case 1281: return dyn_smem_bytes<128, 1, PM_SSSP>();
@@ -623,7 +660,9 @@ __global__ void __launch_bounds__(BS, persistent_min_blocks(BS, PM, TPT)) k_pers
         if constexpr (PM == PM_FFT) {  // every task of an FFT epoch has depth CEN: the width fixes forks and maps
             const uint32_t lgm = cen <= c.rp.lgn ? c.rp.lgn - cen : 0u;
             if (mode == LOAD_FRESH && lgm == 4u && c.rp.leaf >= 16u) {
-                fft_leaf_epoch<BS, TPT>(c, t0, step, hi, cen, acc);  // 16-point leaves only: no forks, no scan
+                constexpr size_t FD = fft_leaf_dyn_bytes<BS, TPT, PM>();
+                fft_leaf_epoch<BS, TPT, FD ? FD : sizeof(sm.u)>(
+                    c, FD ? reinterpret_cast<float2 *>(ring) : reinterpret_cast<float2 *>(&sm.u), t0, step, hi, cen, acc);  // 16-point leaves only: no forks, no scan
                 done = true;
             } else if (mode == LOAD_FRESH && cen <= c.rp.lgn && (1u << lgm) > c.rp.leaf) {
                 jn = fft_fork_epoch<BS, TPT>(c, ctl, t0, step, lo, hi, cen, base, ep, e, acc);
