@@ -531,33 +531,33 @@ __device__ __forceinline__ void fft_leaf_epoch(const Conf &c, float2 *lb, unsign
             o1 = o2;
         }
         cp_async_wait_all();
-        return;
-    }
-    for (uint32_t i = 0; i < n; ++i) {
-        entry(i + 2u, c2, o2);  // two ahead: the entry
-        if (task_type(c0, cen) == TREES_TASK_FFT) {
-            float2 a[16];
-            inputs(c0, o0, a);
-            acc.valid++;
+    } else {  // no room for the buffer: each slot's points are loaded into registers when it runs
+        for (uint32_t i = 0; i < n; ++i) {
+            entry(i + 2u, c2, o2);  // two ahead: the entry
+            if (task_type(c0, cen) == TREES_TASK_FFT) {
+                float2 a[16];
+                inputs(c0, o0, a);
+                acc.valid++;
 #pragma unroll
-            for (int lm = 1; lm <= 4; ++lm) {
-                const int h = 1 << (lm - 1);
+                for (int lm = 1; lm <= 4; ++lm) {
+                    const int h = 1 << (lm - 1);
 #pragma unroll
-                for (int k = 0; k < h; ++k) {
-                    const float2 w = fft_twiddle((uint32_t)k, (uint32_t)lm);
+                    for (int k = 0; k < h; ++k) {
+                        const float2 w = fft_twiddle((uint32_t)k, (uint32_t)lm);
 #pragma unroll
-                    for (int q = 0; q < 16; q += 2 * h) fft_bfly(a[q + k], a[q + k + h], w);
+                        for (int q = 0; q < 16; q += 2 * h) fft_bfly(a[q + k], a[q + k + h], w);
+                    }
                 }
-            }
-            const uint32_t dst = fft_block(o0, d, lgn);
+                const uint32_t dst = fft_block(o0, d, lgn);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) X[dst + k] = a[k];
-            c.code[(uint32_t)slot(i)] = 0u;  // emitted: the entry is dead
+                for (int k = 0; k < 16; ++k) X[dst + k] = a[k];
+                c.code[(uint32_t)slot(i)] = 0u;  // emitted: the entry is dead
+            }
+            c0 = c1;
+            o0 = o1;
+            c1 = c2;
+            o1 = o2;
         }
-        c0 = c1;
-        o0 = o1;
-        c1 = c2;
-        o1 = o2;
     }
 }
 
