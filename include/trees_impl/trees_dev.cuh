@@ -223,7 +223,7 @@ struct Smem {
     unsigned long long w64b[NW];
     unsigned int flags;
     unsigned int bc32[32];                // broadcast words (two per block part in the expansion tiles)
-    unsigned int pcnt[16];                // claims waiting in each block part's buffer (claim_flush)
+    unsigned int pcnt[16];                // entries waiting in each block part's claim buffer (bfs_claim_flush, sssp_claim_flush)
     unsigned long long bc64[4];
     int bar_ok;
     unsigned long long mbar[merge_nst(BS)];  // mbarriers of the merge stage buffers

@@ -2048,9 +2048,11 @@ __device__ __forceinline__ bool part_reserve(const Conf &c, Ctl *ctl, Smem<BS> &
 
 // Claim buffers of the expansion tiles (block part h's buffer: the space of
 // its distance records, which BFS does not use; SSSP: dynamic shared memory).
-// SSSP's tiles append the vertices they claimed; BFS's tiles append their
-// candidates (neighbours whose visited bit was clear) and the flush claims
-// them.  Either way the forks of a buffer take one reservation on
+// SSSP's tiles append the neighbours whose distance their atomic minimum
+// shortened, and the flush's atomic maximum on sched decides which are
+// forked; BFS's tiles append their candidates (neighbours whose visited bit
+// was clear) and the flush claims them.  Either way the forks of a buffer take
+// one reservation on
 // nextFreeCore (Sec. 5.2.3's single atomic for a group of forks, the group
 // made larger): a tile claims a dozen vertices on average, so a reservation
 // (and the scan that placed the claims) per tile cost more than the claims'
@@ -2062,26 +2064,6 @@ template <int BS>
 __device__ __forceinline__ uint32_t *claim_buf(Smem<BS> &sm, uint32_t h) {
     static_assert(sizeof(sm.u.ex.d[0]) >= claim_cap_of(BS) * sizeof(uint32_t), "a part's buffer fits its d records");
     return reinterpret_cast<uint32_t *>(sm.u.ex.d[h]);
-}
-
-// Forks the claims in part h's buffer cb as tasks `code` (every thread of
-// the part calls it, after a barrier of the part that follows the appends):
-// one reservation, then the tasks, then the buffer is empty again.  Ends with
-// a barrier of the part.
-template <int BS>
-__device__ __forceinline__ void claim_flush(const Conf &c, Ctl *ctl, Smem<BS> &sm, const uint32_t *cb, uint32_t h,
-                                            uint32_t lt, uint32_t code, uint32_t base, uint32_t ep, uint32_t e) {
-    constexpr uint32_t HB = BS / EXPAND_PARTS(BS);
-    const uint32_t n = sm.pcnt[h];
-    uint32_t b;
-    if (n && part_reserve<BS>(c, ctl, sm, h, lt, n, base, ep, e, &b)) {
-        for (uint32_t i = lt; i < n; i += HB) {
-            c.code[base + b + i] = code;
-            c.a0[base + b + i] = cb[i];
-        }
-    }
-    if (lt == 0u) sm.pcnt[h] = 0u;  // every thread read the count before part_reserve's barrier
-    bar_part<BS>(h);
 }
 
 // BFS: claims the candidates in part h's buffer and forks the claimed ones as
@@ -2128,6 +2110,49 @@ __device__ __forceinline__ void bfs_claim_flush(const Conf &c, Ctl *ctl, Smem<BS
         const uint32_t code = enc(cen + 1u, TREES_TASK_BFS_VISIT);
         uint32_t slot = base + b + off;
 #pragma unroll
+        for (uint32_t r = 0; r < R; ++r) {
+            if ((won >> r) & 1u) {
+                c.code[slot] = code;
+                c.a0[slot] = cb[lt + r * HB];
+                ++slot;
+            }
+        }
+    }
+    if (lt == 0u) sm.pcnt[h] = 0u;  // every thread read the count before part_scan's barrier
+    bar_part<BS>(h);
+}
+
+// SSSP: forks relax(u) for epoch CEN+1 for each vertex u in part h's buffer
+// that no other thread has forked this epoch: an atomic maximum of sched[u]
+// to CEN+1 finds the first (a vertex shortened by several tiles or edges is
+// in the buffer several times; one maximum wins).  A thread's maxima are
+// issued in groups of RC before any answer is examined, so the tiles' chains
+// end after their atomic minima (R-MAT 22, 512 x 1: 2.13 -> 2.02 ms,
+// distances unchanged).  Ends with a barrier of the part.
+template <int BS>
+__device__ __forceinline__ void sssp_claim_flush(const Conf &c, Ctl *ctl, Smem<BS> &sm, const uint32_t *cb, uint32_t cap,
+                                                 uint32_t h, uint32_t lt, uint32_t cen, uint32_t base, uint32_t ep,
+                                                 uint32_t e) {
+    constexpr uint32_t HB = BS / EXPAND_PARTS(BS), RC = 8u;
+    const uint32_t n = sm.pcnt[h], R = (cap + HB - 1u) / HB;
+    uint32_t won = 0u;
+    for (uint32_t r0 = 0; r0 < R; r0 += RC) {
+        uint32_t prev[RC];
+#pragma unroll
+        for (uint32_t q = 0; q < RC; ++q) {
+            const uint32_t i = lt + (r0 + q) * HB;
+            prev[q] = r0 + q < R && i < n ? atomicMax(c.rp.sched + cb[i], cen + 1u) : ~0u;
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < RC; ++q)
+            if (prev[q] < cen + 1u) won |= 1u << (r0 + q);
+    }
+    uint32_t tot;
+    const uint32_t off = part_scan_u32<BS>((uint32_t)__popc(won), h, &tot, sm);
+    uint32_t b;
+    if (tot && part_reserve<BS>(c, ctl, sm, h, lt, tot, base, ep, e, &b)) {
+        const uint32_t code = enc(cen + 1u, TREES_TASK_SSSP_RELAX);
+        uint32_t slot = base + b + off;
         for (uint32_t r = 0; r < R; ++r) {
             if ((won >> r) & 1u) {
                 c.code[slot] = code;
@@ -2272,20 +2297,28 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
         }
     }
     // stage 3: shorten, and fork the neighbours this thread shortened first this epoch.  All of the
-    // thread's atomic minima are issued before any answer is examined, then all of its atomic maxima,
-    // so each stage costs one overlapped round trip instead of one per edge.
+    // thread's atomic minima are issued before any answer is examined, so they cost one overlapped
+    // round trip; with a claim buffer the shortened neighbours go there and its flush takes the
+    // atomic maxima that decide the forks, else the tile takes them here, all issued together.
     unsigned long long old[EPT];
 #pragma unroll
     for (uint32_t j = 0; j < EPT; ++j) old[j] = uu[j] >= 0 && cand[j] < du[j] ? atomicMin(c.rp.dist + uu[j], cand[j]) : 0ull;
-    uint32_t prev[EPT];
-#pragma unroll
-    for (uint32_t j = 0; j < EPT; ++j)
-        prev[j] = uu[j] >= 0 && cand[j] < du[j] && cand[j] < old[j] ? atomicMax(c.rp.sched + uu[j], cen + 1u) : ~0u;
     uint32_t cmask = 0u;
+    if (cb) {  // the shortened neighbours go to the buffer; its flush decides which are forked
 #pragma unroll
-    for (uint32_t j = 0; j < EPT; ++j)
-        if (prev[j] < cen + 1u) cmask |= 1u << j;
-    if (cb) claim_append<BS, (int)EPT>(sm, cb, h, cmask, uu);  // forked in bulk (claim_flush)
+        for (uint32_t j = 0; j < EPT; ++j)
+            if (uu[j] >= 0 && cand[j] < du[j] && cand[j] < old[j]) cmask |= 1u << j;
+        claim_append<BS, (int)EPT>(sm, cb, h, cmask, uu);
+        cmask = 0u;
+    } else {
+        uint32_t prev[EPT];
+#pragma unroll
+        for (uint32_t j = 0; j < EPT; ++j)
+            prev[j] = uu[j] >= 0 && cand[j] < du[j] && cand[j] < old[j] ? atomicMax(c.rp.sched + uu[j], cen + 1u) : ~0u;
+#pragma unroll
+        for (uint32_t j = 0; j < EPT; ++j)
+            if (prev[j] < cen + 1u) cmask |= 1u << j;
+    }
     uint32_t ftot = 0u, off = 0u;
     if (!cb) off = part_scan_u32<BS>((uint32_t)__popc(cmask), h, &ftot, sm);
     uint32_t b;
@@ -2310,7 +2343,7 @@ __device__ void relax_tile(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t t, ui
     }
     bar_part<BS>(h);  // the part's records are its next tile's
     if (cb && sm.pcnt[h] > cap - ET)  // part-uniform
-        claim_flush<BS>(c, ctl, sm, cb, h, lt, enc(cen + 1u, TREES_TASK_SSSP_RELAX), base, ep, e);
+        sssp_claim_flush<BS>(c, ctl, sm, cb, cap, h, lt, cen, base, ep, e);
 }
 
 // The combine maps of one FFT epoch as one flat array of butterflies.  The
@@ -2409,8 +2442,8 @@ __device__ void map_phase(const Conf &c, Ctl *ctl, Smem<BS> &sm, uint32_t ep, ui
                     if (cb && lt == 0u) sm.pcnt[h] = 0u;  // the tile's descriptor load ends with a barrier of the part
                     for (; t < nt2; t += P * gridDim.x)
                         relax_tile<BS>(c, ctl, sm, t, nd2, ne2, nt2, cen, base, ep, e, h, cb, claim_cap);
-                    if (cb)  // the claims left in the buffer
-                        claim_flush<BS>(c, ctl, sm, cb, h, lt, enc(cen + 1u, TREES_TASK_SSSP_RELAX), base, ep, e);
+                    if (cb)  // the candidates left in the buffer
+                        sssp_claim_flush<BS>(c, ctl, sm, cb, claim_cap, h, lt, cen, base, ep, e);
                 }
             } else {
                 uint32_t t = P * blockIdx.x + h;
