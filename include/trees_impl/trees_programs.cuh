@@ -624,7 +624,12 @@ __device__ __forceinline__ bool fft_fork_epoch(const Conf &c, Ctl *ctl, unsigned
 // A combine epoch whose combines are maps: each task schedules the map over
 // its 2^(lgm-1) butterflies and is done; the epoch's maps (one descriptor
 // count per task, N/2 butterflies in all) are added to the map counter by one
-// thread for the whole grid (the combine maps need no descriptors).
+// thread for the whole grid (the combine maps need no descriptors).  Every
+// entry of the range is a combine of this epoch (the fork epoch at depth CEN
+// made each task of its range its combine), so the count is the width and
+// no code is read; none is marked done either: a combine schedules no join,
+// so its range is never revisited (the reading taken for fib's sums).
+// Measured: 2^24 points, 512 x 1 1.082 -> 1.070 ms, 256 x 1 1.104 -> 1.092 ms.
 template <int BS, int TPT>
 __device__ __forceinline__ void fft_combine_epoch(const Conf &c, Ctl *ctl, unsigned long long t0,
                                                   unsigned long long step, uint32_t lo, uint32_t hi, uint32_t cen,
@@ -636,9 +641,7 @@ __device__ __forceinline__ void fft_combine_epoch(const Conf &c, Ctl *ctl, unsig
     for (; t0 < hi; t0 += step) {
 #pragma unroll
         for (int k = 0; k < TPT; ++k) {
-            const unsigned long long s = t0 + (unsigned long long)k * BS + threadIdx.x;
-            if (s < hi && task_type(c.code[s], cen) == TREES_TASK_FFT_COMBINE) {
-                c.code[s] = 0u;
+            if (t0 + (unsigned long long)k * BS + threadIdx.x < hi) {
                 acc.valid++;
                 acc.maps++;
             }
