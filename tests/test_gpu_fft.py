@@ -108,6 +108,34 @@ def test_fft_bit_identical_across_configurations():
         assert np.array_equal(o, outs[0])
 
 
+@pytest.mark.parametrize("lg", [14, 20])
+def test_fft_leaf_epoch_buffers_every_block_size(lg):
+    """The 16-point leaf epoch at every block size: its next slot's points in shared memory
+    (256 threads), its outputs staged too (128 threads; 512 threads, in dynamic shared memory)
+    or neither (1024 threads). 2^14 points leave most warps partly idle; 2^20 give every thread
+    several slots, the last one partial. The outputs are bit-identical across shapes, within the
+    radix-2 bound of the oracle's transform, and every epoch matches the oracle's task tree."""
+    n = 1 << lg
+    x = gen.signal(lg + 100, n)
+    want = oracle.tvm_run(oracle.FFT, x=x.astype(np.complex128), fft_leaf=16, fft_cutoff=0)["X"] if lg <= 14 else None
+    outs = []
+    for bs, tpt in [(128, 1), (128, 2), (256, 1), (512, 1), (512, 2), (1024, 1)]:
+        status, X, stats, trace = fft_gpu(x, 16, 0, block_size=bs, tasks_per_thread=tpt)
+        assert status == T.TREES_OK, (bs, tpt)
+        if want is not None:
+            check_close(X, want)
+            check_tree(n, 16, 0, stats, trace)
+        else:
+            assert stats["epochs"] == 2 * (lg - 4) + 1
+        outs.append(X.view(np.uint32))
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    if want is None:  # Parseval holds to the bound
+        x64 = x.astype(np.complex128)
+        norm_X = math.sqrt(n) * np.linalg.norm(x64)
+        assert abs(np.linalg.norm(outs[0].view(np.complex64).astype(np.complex128)) - norm_X) <= bound(n) * norm_X
+
+
 @pytest.mark.parametrize("lg", [16, 18])
 def test_fft_mid_sizes_against_oracle_tvm(lg):
     n = 1 << lg
