@@ -83,6 +83,26 @@ def test_sssp_rmat_block_sizes(bs, tpt, scale):
     check_counts(row_ptr, col, 0, dist, stats, trace)
 
 
+@pytest.mark.parametrize("bs,tpt,grid", [(512, 1, 2), (512, 2, 3), (1024, 1, 2), (512, 1, 0)])
+def test_sssp_claim_buffer_flushes_and_capacity(bs, tpt, grid):
+    """The shapes with claim buffers (the shortened neighbours wait in a block part's buffer; its
+    flush takes the atomic maxima that decide the forks): on two or three grid blocks every part
+    flushes many times an epoch. Distances equal Dijkstra's, and a task vector far too small is a
+    capacity error."""
+    row_ptr, col, info = gen.rmat(14, 16, seed=4)
+    weight = gen.weights(5, row_ptr, col)
+    want, _ = oracle.sssp_dijkstra(row_ptr, col, weight, 0)
+    cfg = dict(block_size=bs, tasks_per_thread=tpt)
+    if grid:
+        cfg["grid_blocks"] = grid
+    status, dist, stats, trace = run_sssp(row_ptr, col, weight, 0, 16 * info["nv"], **cfg)
+    assert status == T.TREES_OK
+    assert np.array_equal(dist, want)
+    check_counts(row_ptr, col, 0, dist, stats, trace)
+    status, _, _, _ = run_sssp(row_ptr, col, weight, 0, info["nv"] // 4, **cfg)
+    assert status == T.TREES_ERR_CAPACITY
+
+
 def test_sssp_unit_weights_equal_gpu_bfs_levels():
     row_ptr, col, info = gen.rmat(13, 8, seed=7)
     nv = info["nv"]
