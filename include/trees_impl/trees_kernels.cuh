@@ -119,7 +119,9 @@ __host__ __device__ constexpr size_t ring_bytes() {
     return join_ring_bytes<BS, TPT, PM>() + (size_t)SHADOW_BYTES_PER_SLOT * shadow_slots<BS, TPT, PM>();
 }
 
-// Dynamic shared memory bytes k_persistent<bs, tpt, program mask pm> is launched with.
+// Dynamic shared memory bytes k_persistent<bs, tpt, program mask pm> is launched with:
+// fib's join ring and solo shadow (ring_bytes), the FFT leaf epoch's buffers
+// (fft_leaf_dyn_bytes), SSSP's claim buffers (sssp_claim_cap), else none.
 // SSSP's persistent kernels keep each block part's claim buffer (relax_tile)
 // in dynamic shared memory: claim_cap_of(BS) entries a part, for blocks of
 // 512 threads or more when that fits beside the static shared memory at the
@@ -147,7 +149,8 @@ __host__ __device__ constexpr uint32_t sssp_claim_cap() {
 // threads gained (1.198 -> 1.094 ms).
 template <int BS, int TPT, uint32_t PM>
 __host__ __device__ constexpr size_t fft_leaf_dyn_bytes() {
-    return PM == PM_FFT && persistent_min_blocks(BS, PM, TPT) == 1 && (size_t)BS * 32u * sizeof(float2) > sizeof(Smem<BS>::u) &&
+    return PM == PM_FFT && persistent_min_blocks(BS, PM, TPT) == 1 &&
+                   (size_t)BS * 32u * sizeof(float2) > sizeof(Smem<BS>::u) &&
                    SMEM_PER_SM / persistent_min_blocks(BS, PM, TPT) - SMEM_RESERVED_PER_BLOCK -
                            ((int)sizeof(Smem<BS>) + 256) >=
                        (int)(BS * 32 * sizeof(float2))
