@@ -147,12 +147,13 @@ def test_fft_mid_sizes_against_oracle_tvm(lg):
     check_tree(n, 16, 64, stats, trace)
 
 
-def test_fft_full_size_sampled_outputs():
-    """2^24 points in the benchmark's configuration: every output is finite,
-    Parseval holds to the bound, and sampled outputs match the definition."""
+@pytest.mark.parametrize("bs,tpt", [(256, 1), (512, 1), (512, 2)])
+def test_fft_full_size_sampled_outputs(bs, tpt):
+    """2^24 points in the benchmark's configuration, at the shapes the autotuner picks from: every
+    output is finite, Parseval holds to the bound, and sampled outputs match the definition."""
     n, leaf, cutoff = 1 << 24, 16, 0
     x = gen.signal(1, n)
-    status, X, stats, _ = fft_gpu(x, leaf, cutoff, block_size=256, tasks_per_thread=1)
+    status, X, stats, _ = fft_gpu(x, leaf, cutoff, block_size=bs, tasks_per_thread=tpt)
     assert status == T.TREES_OK
     assert stats["epochs"] == 2 * 20 + 1
     x64 = x.astype(np.complex128)
