@@ -140,6 +140,8 @@ struct Ctl {
     unsigned long long me_ctr[3];    // element maps: (descriptors << 40) | elements
     int err;                         // first device-side error (sticky)
     unsigned int err_epoch;
+    unsigned long long res0;         // persistent scheduler: slot 0's result at the end of the run, beside
+                                     // err so that one 16-byte copy brings both to the host (trees_sync)
     unsigned long long tasks, joins, maps, forks;
     unsigned long long t_start, t_end;
     unsigned int epochs, peak, final_next, pad1;
